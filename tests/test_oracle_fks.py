@@ -162,6 +162,8 @@ def _closed_form_subtracted(xi, y, xc, dl):
     (x1^2+x2^2)/((1-x1)(1-x2)), in units of g^2 C_F B_avg (s = 1)."""
     x1 = 2 * (1 - xi) / (2 - xi * (1 - y))
     x2 = 2 - x1 - xi
+    if x1 >= 1.0 or x2 >= 1.0:  # measure-zero edge hit by the quadrature rule
+        return 0.0
     R = 2 * (x1 * x1 + x2 * x2) / ((1 - x1) * (1 - x2))
     d53 = 1 - y
     d54 = 2 * (1 - x1) / (x2 * xi)
