@@ -1,0 +1,221 @@
+/*
+ * me.h -- C ABI of the GB300 event-parallel NLO matrix-element library.
+ *
+ * The library evaluates, for a batch of independent phase-space points, the
+ * tree-level quantities that dominate fixed-order NLO run time (arXiv:2503.07439,
+ * Sec. 4.1 and Fig. 1: Born, real-emission and counterterm amplitudes; Sec. 4.2:
+ * all of them are tree-level amplitudes) behind the multi-event interface of
+ * Sec. 4.4 (step 1 of the work plan), with the branch-free per-point flow of
+ * Sec. 4.3, Algorithm 2.
+ *
+ * Conventions for every entry point:
+ *  - momenta: float64 structure-of-arrays, element [c][l][i] at
+ *    momenta[(c * n_ext + l) * n + i], c = 0..3 (E, px, py, pz) in GeV, l over the
+ *    process legs in the order of the process name (two incoming legs first), i over
+ *    the n points.  Points must be in the partonic centre-of-mass frame with the
+ *    beams along +z (leg 0) and -z (leg 1) for the FKS entry points.
+ *  - ps_weights: optional float64[n] (NULL = all 1) multiplied into each output.
+ *  - out: float64[n].
+ *  - pointers may be host (pageable or pinned) or device memory of the handle's
+ *    device; the kind is detected per pointer.  With any host pointer the call
+ *    copies through device scratch and returns after the results are in `out`.
+ *    With device pointers only, the work is enqueued on the handle's stream and the
+ *    call returns without synchronising (me_synchronize waits).
+ *  - ownership: the caller owns all input and output buffers and keeps them alive
+ *    until the results are ready; the library owns its handles, process tables and
+ *    scratch, freed by me_destroy.
+ *  - errors: every int-returning call returns ME_OK (0) or a negative ME_ERR_* code
+ *    and sets a thread-local message readable with me_last_error(); no exception
+ *    crosses the boundary.  A failed call leaves `out` unspecified.
+ */
+#ifndef ME_GB300_H
+#define ME_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ME_OK 0
+#define ME_ERR_ARG (-1)      /* invalid argument (NULL handle, n < 0, bad sizes, bad params) */
+#define ME_ERR_OOM (-2)      /* device or host allocation failed */
+#define ME_ERR_PROCESS (-3)  /* unknown process or entry point not defined for it */
+#define ME_ERR_TIMEOUT (-4)  /* a bounded wait ran out (me_poll) */
+#define ME_ERR_CUDA (-5)     /* a CUDA call failed; see me_last_error() */
+#define ME_ERR_BUSY (-6)     /* request rejected: queue full or over the memory budget */
+
+#define ME_PARAMS_VERSION 1u
+#define ME_PREC_FP64 0   /* every amplitude in float64 */
+#define ME_PREC_MIXED 1  /* float32 amplitudes; float64 FKS maps, combination and rescue */
+
+/*
+ * Run parameters.  Start from me_default_params(); `version` must equal
+ * ME_PARAMS_VERSION.
+ *   alpha, alpha_s   couplings (alpha_s fixed, renormalisation scale = sqrt(s))
+ *   mt               top-quark mass [GeV]
+ *   xi_cut, delta    FKS plus-distribution cut-offs xi_c in (0,1], delta in (0,2]
+ *   xi_thr, y_thr    mixed mode: points with xi < xi_thr or 1-y < y_thr in an active
+ *                    counterterm region are re-evaluated in float64
+ *   tol, me_eps      mixed mode: a point is re-evaluated in float64 when
+ *                    (|R S| + |CT|) * me_eps > tol/8 * |R S - CT|
+ *   device           CUDA device ordinal the handle runs on
+ *   lanes_per_event  lanes sharing one point (4, 8, 16 or 32; 0 = autotune)
+ */
+typedef struct me_params {
+  uint32_t version;
+  int32_t precision;
+  double alpha;
+  double alpha_s;
+  double mt;
+  double xi_cut;
+  double delta;
+  double xi_thr;
+  double y_thr;
+  double tol;
+  double me_eps;
+  int32_t device;
+  int32_t lanes_per_event;
+} me_params;
+
+typedef struct me_handle me_handle;
+
+/* Fill `p` with the defaults: FP64, alpha = 1/132.507, alpha_s = 0.118, mt = 173,
+ * xi_cut = 0.5, delta = 1, xi_thr = 1e-3, y_thr = 1e-3, tol = 1e-5, me_eps = 3e-6,
+ * device 0, lanes_per_event 0.  Never fails. */
+void me_default_params(me_params* p);
+
+/*
+ * Create a handle for one process.  `process` is one of
+ *   "ee_uu"   e+ e- -> u ubar          (legs e+, e-, u, ubar)
+ *   "ee_uug"  e+ e- -> u ubar g        (legs e+, e-, u, ubar, g)
+ *   "gg_tt"   g g -> t tbar            (legs g, g, t, tbar)
+ *   "gg_ttg"  g g -> t tbar g          (legs g, g, t, tbar, g)
+ *   "gg_ttgg" g g -> t tbar g g        (legs g, g, t, tbar, g, g)
+ *   "uu_tt"   u ubar -> t tbar         (legs u, ubar, t, tbar)
+ *   "uu_ttg"  u ubar -> t tbar g       (legs u, ubar, t, tbar, g)
+ * Sets up the device-resident process constants (colour matrices, colour
+ * correlators, couplings) on `params->device` on first use of that device.
+ * Returns ME_ERR_PROCESS for an unknown name, ME_ERR_ARG for bad params.
+ */
+int me_init(const char* process, const me_params* params, me_handle** out);
+
+/* Number of legs of the handle's process (for sizing momentum buffers). */
+int me_n_external(const me_handle* h);
+
+/*
+ * Tree-level squared matrix element (Sec. 2.1, Eq. (born); Sec. 2.2, Eq. (real)),
+ * summed over helicities and colours, averaged over initial spins and colours, with
+ * the identical-final-particle factor:  out[i] = ps_weights[i] * |M|^2(p_i).
+ * Defined for every process.  Adds (sum out, sum out^2, n) to the accumulators.
+ */
+int me_eval_born(me_handle* h, const double* momenta, const double* ps_weights, int64_t n, double* out);
+
+/*
+ * n-body NLO weight of e+e- -> u ubar: Born + virtual + integrated FKS
+ * counterterms, out[i] = ps_weights[i] * B_i * (1 + a_s (5 - 2 pi^2/3
+ * - (3 + 4 ln xi_cut) ln(delta/2))), a_s = alpha_s C_F / (2 pi).  Only "ee_uu".
+ */
+int me_eval_nbody_nlo(me_handle* h, const double* momenta, const double* ps_weights, int64_t n, double* out);
+
+/*
+ * Real-emission weight minus FKS soft and collinear counterterms, summed over the FKS
+ * sectors (Sec. 2.2: FKS subtraction; Sec. 4.2: one kinematic parametrisation per
+ * sector; Sec. 4.3, Algorithm 2: every term computed, then masked by the cut-offs):
+ *   out[i] = ps_weights[i] * sum_j [ R S_j - (Th_s G(0,y) + Th_c G(xi,1)
+ *                                    - Th_s Th_c G(0,1)) / (xi^2 (1-y) K) ].
+ * Defined for "ee_uug" (final-state sectors) and "gg_ttg", "uu_ttg" (initial-state
+ * sectors).  In ME_PREC_MIXED, points failing the stability test are recomputed in
+ * float64 before the call's results are complete.  Adds to the accumulators.
+ */
+int me_eval_real_subtracted(me_handle* h, const double* momenta, const double* ps_weights, int64_t n, double* out);
+
+/* Number of points re-evaluated in float64 by the last me_eval_real_subtracted call
+ * (synchronises the handle's stream). */
+int me_last_rescued(me_handle* h, int64_t* n_rescued);
+
+/* Monte-Carlo accumulators of all outputs since creation or the last set:
+ * out[0] = sum w, out[1] = sum w^2, out[2] = number of points (as double).
+ * Synchronises the handle's stream.  me_set_accumulators restores them (resume). */
+int me_get_accumulators(me_handle* h, double out[3]);
+int me_set_accumulators(me_handle* h, const double in[3]);
+
+/* Use an existing cudaStream_t (passed as void*) for the handle's work; NULL selects
+ * the handle's own stream.  The caller keeps the stream alive while it is in use. */
+int me_set_stream(me_handle* h, void* cuda_stream);
+
+/* Wait until all work enqueued on the handle's stream has finished. */
+int me_synchronize(me_handle* h);
+
+/* Release the handle and its device scratch (waits for its stream).  NULL is a no-op. */
+void me_destroy(me_handle* h);
+
+/* ---------------------------------------------------------------- request loop
+ * Continuous batching of phase-space batches from many integration channels
+ * (the multi-event interface of Sec. 4.4; points stay on the device for the whole
+ * evaluation, Sec. 4.3).  A server owns `n_slots` CUDA streams on one device; a
+ * scheduler thread admits queued requests, oldest first, whenever a slot is free
+ * and the sum of the in-flight requests' buffers (n * (4 n_ext + 2) * 8 bytes) stays
+ * within `mem_budget_bytes`, so requests that arrive while others run are admitted
+ * as slots and memory free up and their work overlaps on the GPU.  A request's
+ * result does not depend on what else is in flight.
+ */
+#define ME_KIND_BORN 0             /* me_eval_born */
+#define ME_KIND_REAL_SUBTRACTED 1  /* me_eval_real_subtracted */
+#define ME_KIND_NBODY_NLO 2        /* me_eval_nbody_nlo */
+
+typedef struct me_server me_server;
+typedef uint64_t me_ticket;
+
+typedef struct me_server_params {
+  uint32_t version;          /* ME_PARAMS_VERSION */
+  int32_t device;            /* CUDA device ordinal */
+  int32_t n_slots;           /* concurrent requests on the device, 1..64 */
+  int32_t max_queue;         /* pending requests beyond which me_submit returns ME_ERR_BUSY */
+  int64_t mem_budget_bytes;  /* admission budget for in-flight request buffers */
+  me_params params;          /* physics and precision, shared by all requests */
+} me_server_params;
+
+/* One batch: host buffers owned by the caller, kept alive until me_poll returns it. */
+typedef struct me_request {
+  const char* process;       /* process name as for me_init */
+  int32_t kind;              /* ME_KIND_* */
+  const double* momenta;     /* host, [4][n_ext][n] as above */
+  const double* ps_weights;  /* host float64[n] or NULL */
+  int64_t n;
+  double* out;               /* host float64[n], written before me_poll reports it */
+} me_request;
+
+typedef struct me_result {
+  int32_t status;            /* ME_OK or the ME_ERR_* code of the evaluation */
+  int64_t n;
+  int64_t n_rescued;         /* points re-evaluated in float64 (mixed precision) */
+  double sum_w, sum_w2;      /* of out[] */
+  double t_queue_us;         /* submit -> admission */
+  double t_device_us;        /* copies + kernels on the slot's stream (CUDA events) */
+  double t_total_us;         /* submit -> completion seen by the scheduler */
+} me_result;
+
+/* Defaults: device 0, 4 slots, queue 4096, 8 GiB budget, mixed precision. */
+void me_default_server_params(me_server_params* p);
+/* Start a server and its scheduler thread.  ME_ERR_ARG for bad parameters. */
+int me_server_create(const me_server_params* params, me_server** out);
+/* Queue a request; returns a ticket.  ME_ERR_BUSY when the queue is full or the
+ * request alone exceeds the memory budget; ME_ERR_PROCESS for an unknown process. */
+int me_submit(me_server* s, const me_request* req, me_ticket* out);
+/* Wait up to timeout_us (negative: no limit) for a ticket.  ME_OK: `out` filled and
+ * the ticket retired; ME_ERR_TIMEOUT: not finished yet (poll again); ME_ERR_ARG:
+ * unknown or already retired ticket.  The wait is on the host only. */
+int me_poll(me_server* s, me_ticket t, me_result* out, int64_t timeout_us);
+/* Stop the scheduler, wait for in-flight work, free everything.  NULL is a no-op. */
+void me_server_destroy(me_server* s);
+
+/* Message of the last failed call on this thread ("" if none).  Valid until the next
+ * call on the same thread. */
+const char* me_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ME_GB300_H */

@@ -242,5 +242,5 @@ def real_subtracted(real: str, k: np.ndarray, fp: FKSParams = FKSParams(),
         W = (G - th_s * G_soft - th_c * G_coll + th_s * th_c * G_sc) / (xi * xi * (1.0 - y) * kin.K)
         total += W
         parts.append(dict(xi=xi, y=y, G=G, G_soft=G_soft, G_coll=G_coll, G_sc=G_sc, W=W,
-                          S=S[isec], K=kin.K))
+                          S=S[isec], K=kin.K, RS=R * S[isec]))
     return (total, parts) if detail else total

@@ -1,0 +1,265 @@
+"""ctypes marshalling for the C ABI in include/me.h (no computation here)."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+ME_OK = 0
+ME_ERR_ARG = -1
+ME_ERR_OOM = -2
+ME_ERR_PROCESS = -3
+ME_ERR_TIMEOUT = -4
+ME_ERR_CUDA = -5
+ME_ERR_BUSY = -6
+ME_PREC_FP64 = 0
+ME_PREC_MIXED = 1
+ME_PARAMS_VERSION = 1
+ME_KIND_BORN = 0
+ME_KIND_REAL_SUBTRACTED = 1
+ME_KIND_NBODY_NLO = 2
+KINDS = {"born": ME_KIND_BORN, "real_subtracted": ME_KIND_REAL_SUBTRACTED, "nbody_nlo": ME_KIND_NBODY_NLO}
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libme_gb300.so")
+HEADER = os.path.join(os.path.dirname(PKG), "include", "me.h")
+
+
+class MEError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class MEParams(ctypes.Structure):
+    _fields_ = [("version", ctypes.c_uint32), ("precision", ctypes.c_int32), ("alpha", ctypes.c_double),
+                ("alpha_s", ctypes.c_double), ("mt", ctypes.c_double), ("xi_cut", ctypes.c_double),
+                ("delta", ctypes.c_double), ("xi_thr", ctypes.c_double), ("y_thr", ctypes.c_double),
+                ("tol", ctypes.c_double), ("me_eps", ctypes.c_double), ("device", ctypes.c_int32),
+                ("lanes_per_event", ctypes.c_int32)]
+
+
+class MEServerParams(ctypes.Structure):
+    _fields_ = [("version", ctypes.c_uint32), ("device", ctypes.c_int32), ("n_slots", ctypes.c_int32),
+                ("max_queue", ctypes.c_int32), ("mem_budget_bytes", ctypes.c_int64), ("params", MEParams)]
+
+
+class MERequest(ctypes.Structure):
+    _fields_ = [("process", ctypes.c_char_p), ("kind", ctypes.c_int32), ("momenta", ctypes.c_void_p),
+                ("ps_weights", ctypes.c_void_p), ("n", ctypes.c_int64), ("out", ctypes.c_void_p)]
+
+
+class MEResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("n", ctypes.c_int64), ("n_rescued", ctypes.c_int64),
+                ("sum_w", ctypes.c_double), ("sum_w2", ctypes.c_double), ("t_queue_us", ctypes.c_double),
+                ("t_device_us", ctypes.c_double), ("t_total_us", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load_library(path: str | None = None) -> ctypes.CDLL:
+    """Load the CUDA library (fails loudly if it has not been built)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"CUDA library {p} not found: build it with __graft_entry__.build()")
+    lib = ctypes.CDLL(p)
+    vp, i64, dp = ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "me_default_params": (None, [ctypes.POINTER(MEParams)]),
+        "me_init": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(MEParams), ctypes.POINTER(vp)]),
+        "me_n_external": (ctypes.c_int, [vp]),
+        "me_eval_born": (ctypes.c_int, [vp, vp, vp, i64, vp]),
+        "me_eval_nbody_nlo": (ctypes.c_int, [vp, vp, vp, i64, vp]),
+        "me_eval_real_subtracted": (ctypes.c_int, [vp, vp, vp, i64, vp]),
+        "me_last_rescued": (ctypes.c_int, [vp, ctypes.POINTER(i64)]),
+        "me_get_accumulators": (ctypes.c_int, [vp, dp]),
+        "me_set_accumulators": (ctypes.c_int, [vp, dp]),
+        "me_set_stream": (ctypes.c_int, [vp, vp]),
+        "me_synchronize": (ctypes.c_int, [vp]),
+        "me_destroy": (None, [vp]),
+        "me_last_error": (ctypes.c_char_p, []),
+        "me_default_server_params": (None, [ctypes.POINTER(MEServerParams)]),
+        "me_server_create": (ctypes.c_int, [ctypes.POINTER(MEServerParams), ctypes.POINTER(vp)]),
+        "me_submit": (ctypes.c_int, [vp, ctypes.POINTER(MERequest), ctypes.POINTER(ctypes.c_uint64)]),
+        "me_poll": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.POINTER(MEResult), i64]),
+        "me_server_destroy": (None, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def library() -> ctypes.CDLL:
+    return load_library()
+
+
+def declared_symbols(header: str = HEADER) -> list[str]:
+    """Function names declared in the C header."""
+    text = open(header).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(me_[a-z0-9_]+)\s*\(", text)))
+
+
+def _check(rc: int):
+    if rc != ME_OK:
+        raise MEError(rc, library().me_last_error().decode())
+
+
+def default_params(**kw) -> MEParams:
+    p = MEParams()
+    library().me_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def _ptr(x):
+    """(address, keepalive) of a numpy array or torch tensor (host or CUDA)."""
+    if x is None:
+        return None, None
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float64 or not x.flags["C_CONTIGUOUS"]:
+            x = np.ascontiguousarray(x, dtype=np.float64)
+        return x.ctypes.data, x
+    if hasattr(x, "data_ptr"):  # torch.Tensor
+        import torch
+        if x.dtype != torch.float64 or not x.is_contiguous():
+            raise ValueError("tensors must be contiguous float64")
+        return x.data_ptr(), x
+    raise TypeError(type(x))
+
+
+class Handle:
+    """One process on one device (me_init ... me_destroy)."""
+
+    def __init__(self, process: str, precision: int = ME_PREC_FP64, **params):
+        self.lib = library()
+        self.params = default_params(precision=precision, **params)
+        h = ctypes.c_void_p()
+        _check(self.lib.me_init(process.encode(), ctypes.byref(self.params), ctypes.byref(h)))
+        self.h = h
+        self.process = process
+        self.n_ext = self.lib.me_n_external(self.h)
+
+    def _call(self, fn, p, w, out):
+        n = p.shape[-1]
+        if p.shape[:2] != (4, self.n_ext):
+            raise ValueError(f"momenta must be [4][{self.n_ext}][n], got {tuple(p.shape)}")
+        if out is None:
+            if isinstance(p, np.ndarray):
+                out = np.empty(n)
+            else:
+                import torch
+                out = torch.empty(n, dtype=torch.float64, device=p.device)
+        pp, kp = _ptr(p)
+        wp, kw = _ptr(w)
+        op, ko = _ptr(out)
+        _check(fn(self.h, pp, wp, n, op))
+        if isinstance(out, np.ndarray) and ko is not out:
+            out[...] = ko
+        return out
+
+    def born(self, p, w=None, out=None):
+        return self._call(self.lib.me_eval_born, p, w, out)
+
+    def nbody_nlo(self, p, w=None, out=None):
+        return self._call(self.lib.me_eval_nbody_nlo, p, w, out)
+
+    def real_subtracted(self, p, w=None, out=None):
+        return self._call(self.lib.me_eval_real_subtracted, p, w, out)
+
+    def last_rescued(self) -> int:
+        v = ctypes.c_int64()
+        _check(self.lib.me_last_rescued(self.h, ctypes.byref(v)))
+        return v.value
+
+    def accumulators(self):
+        a = (ctypes.c_double * 3)()
+        _check(self.lib.me_get_accumulators(self.h, a))
+        return tuple(a)
+
+    def set_accumulators(self, vals):
+        a = (ctypes.c_double * 3)(*vals)
+        _check(self.lib.me_set_accumulators(self.h, a))
+
+    def set_stream(self, stream_ptr: int | None):
+        _check(self.lib.me_set_stream(self.h, stream_ptr))
+
+    def synchronize(self):
+        _check(self.lib.me_synchronize(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.me_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Request loop (me_server_create / me_submit / me_poll / me_server_destroy)."""
+
+    def __init__(self, device: int = 0, n_slots: int = 4, max_queue: int = 4096, mem_budget_bytes: int = 0,
+                 precision: int = ME_PREC_MIXED, **params):
+        self.lib = library()
+        sp = MEServerParams()
+        self.lib.me_default_server_params(ctypes.byref(sp))
+        sp.device = device
+        sp.n_slots = n_slots
+        sp.max_queue = max_queue
+        if mem_budget_bytes:
+            sp.mem_budget_bytes = mem_budget_bytes
+        sp.params = default_params(precision=precision, device=device, **params)
+        s = ctypes.c_void_p()
+        _check(self.lib.me_server_create(ctypes.byref(sp), ctypes.byref(s)))
+        self.s = s
+        self._keep = {}
+
+    def submit(self, process: str, kind: str, p: np.ndarray, w=None, out=None) -> int:
+        n = p.shape[-1]
+        out = np.empty(n) if out is None else out
+        pp, kp = _ptr(p)
+        wp, kw = _ptr(w)
+        op, ko = _ptr(out)
+        req = MERequest(process.encode(), KINDS[kind], pp, wp, n, op)
+        t = ctypes.c_uint64()
+        _check(self.lib.me_submit(self.s, ctypes.byref(req), ctypes.byref(t)))
+        self._keep[t.value] = (kp, kw, ko, req)
+        return t.value
+
+    def poll(self, ticket: int, timeout_us: int = -1) -> dict:
+        r = MEResult()
+        rc = self.lib.me_poll(self.s, ctypes.c_uint64(ticket), ctypes.byref(r), timeout_us)
+        if rc == ME_ERR_TIMEOUT:
+            return {"status": ME_ERR_TIMEOUT}
+        _check(rc)
+        kp, kw, ko, _ = self._keep.pop(ticket)
+        return {"status": r.status, "n": r.n, "n_rescued": r.n_rescued, "sum_w": r.sum_w, "sum_w2": r.sum_w2,
+                "t_queue_us": r.t_queue_us, "t_device_us": r.t_device_us, "t_total_us": r.t_total_us,
+                "out": ko}
+
+    def close(self):
+        if getattr(self, "s", None):
+            self.lib.me_server_destroy(self.s)
+            self.s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,691 @@
+// Host side of the C ABI: process set-up (colour algebra), handles, dispatch,
+// host<->device staging, FP64 rescue, accumulators, autotuning.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/me.h"
+#include "me_internal.h"
+#include "me_kernels.cuh"
+
+namespace me {
+
+// ---------------------------------------------------------------- errors
+static thread_local std::string g_err;
+static int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+#define ME_CUDA(call)                                                                          \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) return fail(ME_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+// ---------------------------------------------------------------- reductions
+__global__ void k_partials(const double* __restrict__ w, long n, double* __restrict__ part) {
+  __shared__ double s1[256], s2[256];
+  double a = 0.0, b = 0.0;
+  for (long i = (long)blockIdx.x * 256 + threadIdx.x; i < n; i += (long)gridDim.x * 256) {
+    const double x = w[i];
+    a += x;
+    b += x * x;
+  }
+  s1[threadIdx.x] = a;
+  s2[threadIdx.x] = b;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      s1[threadIdx.x] += s1[threadIdx.x + o];
+      s2[threadIdx.x] += s2[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = s1[0];
+    part[2 * blockIdx.x + 1] = s2[0];
+  }
+}
+
+__global__ void k_finish(const double* __restrict__ part, int nblk, double* __restrict__ acc, long n) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int i = 0; i < nblk; ++i) {
+      a += part[2 * i];
+      b += part[2 * i + 1];
+    }
+    acc[0] += a;
+    acc[1] += b;
+    acc[2] += (double)n;
+  }
+}
+constexpr int RED_BLOCKS = 304;  // 2 x 152 SMs
+
+// ---------------------------------------------------------------- colour algebra (host)
+using cd = std::complex<double>;
+struct Gen {
+  cd T[8][3][3];
+  double f[8][8][8];
+};
+static Gen make_generators() {
+  Gen g{};
+  const double r3 = 1.0 / std::sqrt(3.0);
+  cd l[8][3][3] = {};
+  l[0][0][1] = l[0][1][0] = 1.0;
+  l[1][0][1] = cd(0, -1);
+  l[1][1][0] = cd(0, 1);
+  l[2][0][0] = 1.0;
+  l[2][1][1] = -1.0;
+  l[3][0][2] = l[3][2][0] = 1.0;
+  l[4][0][2] = cd(0, -1);
+  l[4][2][0] = cd(0, 1);
+  l[5][1][2] = l[5][2][1] = 1.0;
+  l[6][1][2] = cd(0, -1);
+  l[6][2][1] = cd(0, 1);
+  l[7][0][0] = l[7][1][1] = r3;
+  l[7][2][2] = -2.0 * r3;
+  for (int a = 0; a < 8; ++a)
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) g.T[a][i][j] = 0.5 * l[a][i][j];
+  // f^abc = -2 i Tr([T^a, T^b] T^c)
+  for (int a = 0; a < 8; ++a)
+    for (int b = 0; b < 8; ++b)
+      for (int c = 0; c < 8; ++c) {
+        cd tr = 0.0;
+        for (int i = 0; i < 3; ++i)
+          for (int j = 0; j < 3; ++j)
+            for (int k = 0; k < 3; ++k)
+              tr += (g.T[a][i][j] * g.T[b][j][k] - g.T[b][i][j] * g.T[a][j][k]) * g.T[c][k][i];
+        g.f[a][b][c] = (cd(0, -2) * tr).real();
+      }
+  return g;
+}
+
+// A colour tensor over legs with dimensions dims[], stored dense.
+struct Tensor {
+  std::vector<int> dims;
+  std::vector<cd> v;
+  size_t size() const { return v.size(); }
+};
+enum Rep { ADJ, FUND, ANTI };
+
+// apply the colour-charge generator a of leg `axis` (representation rep) to t
+static Tensor charge(const Gen& G, const Tensor& t, int axis, Rep rep, int a) {
+  Tensor o = t;
+  std::fill(o.v.begin(), o.v.end(), cd(0));
+  size_t inner = 1;
+  for (size_t k = axis + 1; k < t.dims.size(); ++k) inner *= t.dims[k];
+  const int d = t.dims[axis];
+  const size_t outer = t.size() / (inner * d);
+  for (size_t o1 = 0; o1 < outer; ++o1)
+    for (int x = 0; x < d; ++x)
+      for (int y = 0; y < d; ++y) {
+        cd m;
+        if (rep == FUND) m = G.T[a][x][y];
+        else if (rep == ANTI) m = -G.T[a][y][x];
+        else m = cd(0, -1) * G.f[a][x][y];
+        if (m == cd(0)) continue;
+        for (size_t i = 0; i < inner; ++i) o.v[(o1 * d + x) * inner + i] += m * t.v[(o1 * d + y) * inner + i];
+      }
+  return o;
+}
+
+static cd inner(const Tensor& a, const Tensor& b) {
+  cd s = 0.0;
+  for (size_t i = 0; i < a.size(); ++i) s += std::conj(a.v[i]) * b.v[i];
+  return s;
+}
+
+struct ProcColour {
+  std::vector<Tensor> basis;
+  std::vector<Rep> reps;  // per axis
+};
+
+// string basis (T^{a_s0} ... T^{a_s(n-1)})_{ij} over axes (gluon_0..gluon_{n-1}, i, j)
+static ProcColour ttng_basis(const Gen& G, int ng) {
+  ProcColour pc;
+  std::vector<int> perm(ng);
+  for (int i = 0; i < ng; ++i) perm[i] = i;
+  std::vector<int> dims(ng, 8);
+  dims.push_back(3);
+  dims.push_back(3);
+  size_t ncol = 1;
+  for (int i = 0; i < ng; ++i) ncol *= 8;
+  do {
+    Tensor t;
+    t.dims = dims;
+    t.v.assign(ncol * 9, cd(0));
+    std::vector<int> a(ng);
+    for (size_t c = 0; c < ncol; ++c) {
+      size_t r = c;
+      for (int i = ng - 1; i >= 0; --i) {
+        a[i] = (int)(r % 8);
+        r /= 8;
+      }
+      cd m[3][3], tmp[3][3];
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) m[i][j] = (i == j) ? 1.0 : 0.0;
+      for (int q = 0; q < ng; ++q) {
+        const int ai = a[perm[q]];
+        for (int i = 0; i < 3; ++i)
+          for (int j = 0; j < 3; ++j) {
+            cd s = 0;
+            for (int k = 0; k < 3; ++k) s += m[i][k] * G.T[ai][k][j];
+            tmp[i][j] = s;
+          }
+        std::memcpy(m, tmp, sizeof(m));
+      }
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) t.v[c * 9 + i * 3 + j] = m[i][j];
+    }
+    pc.basis.push_back(std::move(t));
+  } while (std::next_permutation(perm.begin(), perm.end()));
+  for (int i = 0; i < ng; ++i) pc.reps.push_back(ADJ);
+  pc.reps.push_back(FUND);  // t  (outgoing quark)
+  pc.reps.push_back(ANTI);  // tbar (outgoing antiquark)
+  return pc;
+}
+
+static double delta(int a, int b) { return a == b ? 1.0 : 0.0; }
+
+// axes (k: incoming u, l: incoming ubar, i: t, j: tbar [, a: gluon])
+static ProcColour uu_basis(const Gen& G, bool gluon) {
+  ProcColour pc;
+  std::vector<int> dims = {3, 3, 3, 3};
+  if (gluon) dims.push_back(8);
+  const int na = gluon ? 8 : 1;
+  const int nb = gluon ? 4 : 2;
+  for (int e = 0; e < nb; ++e) {
+    Tensor t;
+    t.dims = dims;
+    t.v.assign(81 * na, cd(0));
+    for (int k = 0; k < 3; ++k)
+      for (int l = 0; l < 3; ++l)
+        for (int i = 0; i < 3; ++i)
+          for (int j = 0; j < 3; ++j)
+            for (int a = 0; a < na; ++a) {
+              cd v;
+              if (!gluon) {
+                v = e == 0 ? delta(i, k) * delta(l, j) : delta(i, j) * delta(l, k);
+              } else if (e == 0) v = G.T[a][i][k] * delta(l, j);
+              else if (e == 1) v = delta(i, k) * G.T[a][l][j];
+              else if (e == 2) v = G.T[a][i][j] * delta(l, k);
+              else v = delta(i, j) * G.T[a][l][k];
+              t.v[(((k * 3 + l) * 3 + i) * 3 + j) * na + a] = v;
+            }
+    pc.basis.push_back(std::move(t));
+  }
+  pc.reps = {ANTI, FUND, FUND, ANTI};
+  if (gluon) pc.reps.push_back(ADJ);
+  return pc;
+}
+
+// axes (i: u, j: ubar [, a])
+static ProcColour ee_basis(const Gen& G, bool gluon) {
+  ProcColour pc;
+  Tensor t;
+  const int na = gluon ? 8 : 1;
+  t.dims = {3, 3};
+  if (gluon) t.dims.push_back(8);
+  t.v.assign(9 * na, cd(0));
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      for (int a = 0; a < na; ++a) t.v[(i * 3 + j) * na + a] = gluon ? G.T[a][i][j] : cd(delta(i, j));
+  pc.basis.push_back(std::move(t));
+  pc.reps = {FUND, ANTI};
+  if (gluon) pc.reps.push_back(ADJ);
+  return pc;
+}
+
+// Build all tables; verifies colour conservation of every basis tensor and
+// that the Gram matrices are real.
+static int build_tables(ColourTables& tab) {
+  std::memset(&tab, 0, sizeof(tab));
+  const Gen G = make_generators();
+  struct Item {
+    int pid;
+    ProcColour pc;
+  };
+  std::vector<Item> items;
+  items.push_back({P_EE_UU, ee_basis(G, false)});
+  items.push_back({P_EE_UUG, ee_basis(G, true)});
+  items.push_back({P_GG_TT, ttng_basis(G, 2)});
+  items.push_back({P_GG_TTG, ttng_basis(G, 3)});
+  items.push_back({P_GG_TTGG, ttng_basis(G, 4)});
+  items.push_back({P_UU_TT, uu_basis(G, false)});
+  items.push_back({P_UU_TTG, uu_basis(G, true)});
+  for (auto& it : items) {
+    const auto& B = it.pc.basis;
+    const int nf = (int)B.size();
+    for (int x = 0; x < nf; ++x) {
+      // colour conservation: sum over legs of T_leg^a e_x = 0 for every a
+      for (int a = 0; a < 8; ++a) {
+        Tensor s = B[x];
+        std::fill(s.v.begin(), s.v.end(), cd(0));
+        for (size_t ax = 0; ax < B[x].dims.size(); ++ax) {
+          if (B[x].dims[ax] == 1) continue;
+          Tensor c = charge(G, B[x], (int)ax, it.pc.reps[ax], a);
+          for (size_t q = 0; q < s.size(); ++q) s.v[q] += c.v[q];
+        }
+        double mx = 0;
+        for (auto& v : s.v) mx = std::max(mx, std::abs(v));
+        if (mx > 1e-12) return fail(ME_ERR_PROCESS, "colour basis not invariant for process table");
+      }
+      for (int y = 0; y < nf; ++y) {
+        const cd c = inner(B[x], B[y]);
+        if (std::abs(c.imag()) > 1e-12) return fail(ME_ERR_PROCESS, "complex colour matrix");
+        tab.C[it.pid][x * nf + y] = c.real();
+        tab.Cf[it.pid][x * nf + y] = (float)c.real();
+      }
+    }
+    // Born colour correlators C^{kl}_{xy} = sum_a <T_k^a e_x | T_l^a e_y>
+    if (it.pid == P_GG_TT || it.pid == P_UU_TT) {
+      const int ci = it.pid == P_GG_TT ? 0 : 1;
+      int pr = 0;
+      for (int k = 0; k < 4; ++k)
+        for (int l = k; l < 4; ++l, ++pr)
+          for (int x = 0; x < 2; ++x)
+            for (int y = 0; y < 2; ++y) {
+              cd s = 0;
+              for (int a = 0; a < 8; ++a)
+                s += inner(charge(G, B[x], k, it.pc.reps[k], a), charge(G, B[y], l, it.pc.reps[l], a));
+              if (std::abs(s.imag()) > 1e-12) return fail(ME_ERR_PROCESS, "complex colour correlator");
+              tab.Ccorr[ci][pr][x * 2 + y] = s.real();
+            }
+    }
+  }
+  return ME_OK;
+}
+
+// ---------------------------------------------------------------- per-device state
+struct DeviceState {
+  bool ready = false;
+  ColourTables* d_tab = nullptr;
+};
+static std::mutex g_dev_mu;
+static DeviceState g_dev[64];
+static ColourTables* g_host_tab = nullptr;
+
+static int device_setup(int dev, ColourTables** d_tab) {
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  if (dev < 0 || dev >= 64) return fail(ME_ERR_ARG, "device ordinal out of range");
+  if (!g_host_tab) {
+    g_host_tab = new ColourTables;
+    int rc = build_tables(*g_host_tab);
+    if (rc != ME_OK) {
+      delete g_host_tab;
+      g_host_tab = nullptr;
+      return rc;
+    }
+  }
+  if (!g_dev[dev].ready) {
+    ME_CUDA(cudaSetDevice(dev));
+    ME_CUDA(cudaMalloc(&g_dev[dev].d_tab, sizeof(ColourTables)));
+    ME_CUDA(cudaMemcpy(g_dev[dev].d_tab, g_host_tab, sizeof(ColourTables), cudaMemcpyHostToDevice));
+    g_dev[dev].ready = true;
+  }
+  *d_tab = g_dev[dev].d_tab;
+  return ME_OK;
+}
+
+// ---------------------------------------------------------------- process registry
+struct ProcDesc {
+  const char* name;
+  int pid;
+  int n_ext;
+  int born_pid;   // underlying Born for the FKS entry (-1 if none)
+  double avg;     // initial spin x colour average / identical factor
+};
+static const ProcDesc kProcs[] = {
+    {"ee_uu", P_EE_UU, 4, -1, 4.0},
+    {"ee_uug", P_EE_UUG, 5, P_EE_UU, 4.0},
+    {"gg_tt", P_GG_TT, 4, -1, 256.0},
+    {"gg_ttg", P_GG_TTG, 5, P_GG_TT, 256.0},
+    {"gg_ttgg", P_GG_TTGG, 6, -1, 512.0},
+    {"uu_tt", P_UU_TT, 4, -1, 36.0},
+    {"uu_ttg", P_UU_TTG, 5, P_UU_TT, 36.0},
+};
+
+}  // namespace me
+
+using namespace me;
+
+struct me_handle {
+  const ProcDesc* proc;
+  me_params prm;
+  KParams kp;
+  int device;
+  cudaStream_t own_stream;
+  cudaStream_t stream;
+  // device scratch (grown on demand)
+  double* d_p = nullptr;
+  double* d_w = nullptr;
+  double* d_out = nullptr;
+  size_t cap = 0;
+  int* d_resc = nullptr;     // rescue index list (capacity cap)
+  int* d_nresc = nullptr;    // [0]: count
+  double* d_part = nullptr;  // reduction partials
+  double* d_acc = nullptr;   // accumulators (3)
+  int lpe[2][2] = {{0, 0}, {0, 0}};  // [kind][fp64] chosen lanes per event
+  int last_kind = K_TREE;
+};
+
+static int ensure_capacity(me_handle* h, size_t n) {
+  if (n <= h->cap) return ME_OK;
+  size_t c = std::max(n, (size_t)1024);
+  cudaFree(h->d_p);
+  cudaFree(h->d_w);
+  cudaFree(h->d_out);
+  cudaFree(h->d_resc);
+  h->d_p = h->d_w = h->d_out = nullptr;
+  h->d_resc = nullptr;
+  h->cap = 0;
+  if (cudaMalloc(&h->d_p, c * 4 * h->proc->n_ext * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&h->d_w, c * sizeof(double)) != cudaSuccess || cudaMalloc(&h->d_out, c * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&h->d_resc, c * sizeof(int)) != cudaSuccess)
+    return fail(ME_ERR_OOM, "device scratch allocation failed");
+  h->cap = c;
+  return ME_OK;
+}
+
+static bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+static cudaError_t dispatch(int pid, int kind, bool fp64, int lpe, const LaunchArgs& a, cudaStream_t st) {
+  switch (pid) {
+    case P_EE_UU:
+    case P_EE_UUG: return launch_ee(pid, kind, fp64, lpe, a, st);
+    case P_GG_TT:
+    case P_GG_TTG: return launch_gg(pid, kind, fp64, lpe, a, st);
+    case P_GG_TTGG: return launch_ggg(pid, kind, fp64, lpe, a, st);
+    case P_UU_TT:
+    case P_UU_TTG: return launch_uu(pid, kind, fp64, lpe, a, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// pick lanes-per-event by timing each candidate once on the caller's batch (first use)
+static int choose_lpe(me_handle* h, int kind, bool fp64, const LaunchArgs& a) {
+  int& slot = h->lpe[kind][fp64 ? 1 : 0];
+  if (h->prm.lanes_per_event) return slot = h->prm.lanes_per_event;
+  if (slot) return slot;
+  const int cands[4] = {4, 8, 16, 32};
+  LaunchArgs t = a;
+  t.groups = std::min<long>(a.groups, 1L << 15);
+  t.kp.flag_unstable = 0;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int pick = 8;
+  for (int c : cands) {
+    if (dispatch(h->proc->pid, kind, fp64, c, t, h->stream) != cudaSuccess) continue;  // warm-up
+    cudaEventRecord(e0, h->stream);
+    dispatch(h->proc->pid, kind, fp64, c, t, h->stream);
+    cudaEventRecord(e1, h->stream);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      pick = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaGetLastError();
+  return slot = pick;
+}
+
+extern "C" {
+
+void me_default_params(me_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->version = ME_PARAMS_VERSION;
+  p->precision = ME_PREC_FP64;
+  p->alpha = 1.0 / 132.507;
+  p->alpha_s = 0.118;
+  p->mt = 173.0;
+  p->xi_cut = 0.5;
+  p->delta = 1.0;
+  p->xi_thr = 1e-3;
+  p->y_thr = 1e-3;
+  p->tol = 1e-5;
+  p->me_eps = 3e-6;
+  p->device = 0;
+  p->lanes_per_event = 0;
+}
+
+const char* me_last_error(void) { return g_err.c_str(); }
+
+int me_init(const char* process, const me_params* params, me_handle** out) {
+  if (!process || !params || !out) return fail(ME_ERR_ARG, "me_init: NULL argument");
+  *out = nullptr;
+  if (params->version != ME_PARAMS_VERSION) return fail(ME_ERR_ARG, "me_init: params version mismatch");
+  if (params->precision != ME_PREC_FP64 && params->precision != ME_PREC_MIXED)
+    return fail(ME_ERR_ARG, "me_init: precision must be ME_PREC_FP64 or ME_PREC_MIXED");
+  if (!(params->xi_cut > 0 && params->xi_cut <= 1) || !(params->delta > 0 && params->delta <= 2) ||
+      !(params->alpha_s > 0) || !(params->alpha > 0) || !(params->mt > 0))
+    return fail(ME_ERR_ARG, "me_init: parameter out of range");
+  const int l = params->lanes_per_event;
+  if (l != 0 && l != 4 && l != 8 && l != 16 && l != 32) return fail(ME_ERR_ARG, "me_init: lanes_per_event");
+  const ProcDesc* pd = nullptr;
+  for (const auto& d : kProcs)
+    if (std::strcmp(d.name, process) == 0) pd = &d;
+  if (!pd) return fail(ME_ERR_PROCESS, std::string("me_init: unknown process ") + process);
+  ColourTables* d_tab = nullptr;
+  int rc = device_setup(params->device, &d_tab);
+  if (rc != ME_OK) return rc;
+  me_handle* h = new me_handle();
+  h->proc = pd;
+  h->prm = *params;
+  h->device = params->device;
+  if (cudaSetDevice(h->device) != cudaSuccess || cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    delete h;
+    return fail(ME_ERR_CUDA, "me_init: stream creation failed");
+  }
+  h->stream = h->own_stream;
+  if (cudaMalloc(&h->d_nresc, sizeof(int)) != cudaSuccess || cudaMalloc(&h->d_part, 2 * RED_BLOCKS * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&h->d_acc, 3 * sizeof(double)) != cudaSuccess) {
+    me_destroy(h);
+    return fail(ME_ERR_OOM, "me_init: allocation failed");
+  }
+  cudaMemset(h->d_acc, 0, 3 * sizeof(double));
+  cudaMemset(h->d_nresc, 0, sizeof(int));
+  KParams& kp = h->kp;
+  std::memset(&kp, 0, sizeof(kp));
+  kp.cp.gs = std::sqrt(4.0 * M_PI * params->alpha_s);
+  kp.cp.ee = std::sqrt(4.0 * M_PI * params->alpha);
+  kp.cp.mt = params->mt;
+  kp.avg_inv = 1.0 / pd->avg;
+  kp.born_avg_inv = pd->born_pid >= 0 ? 1.0 / kProcs[pd->born_pid].avg : 0.0;
+  kp.nlo_factor = 1.0;
+  kp.xi_cut = params->xi_cut;
+  kp.delta = params->delta;
+  kp.xi_thr = params->xi_thr;
+  kp.y_thr = params->y_thr;
+  kp.me_eps = params->me_eps;
+  kp.tol = params->tol;
+  kp.tab = d_tab;
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    me_destroy(h);
+    return fail(ME_ERR_CUDA, "me_init: device error");
+  }
+  *out = h;
+  return ME_OK;
+}
+
+int me_n_external(const me_handle* h) { return h ? h->proc->n_ext : 0; }
+
+static int run(me_handle* h, int kind, double nlo_factor, const double* momenta, const double* wgt, int64_t n,
+               double* out) {
+  if (!h) return fail(ME_ERR_ARG, "NULL handle");
+  if (n < 0 || n > (int64_t)INT32_MAX) return fail(ME_ERR_ARG, "n out of range [0, 2^31)");
+  if (n > 0 && (!momenta || !out)) return fail(ME_ERR_ARG, "NULL momenta/out");
+  ME_CUDA(cudaSetDevice(h->device));
+  h->last_kind = K_TREE;
+  if (n == 0) return ME_OK;
+  const int next = h->proc->n_ext;
+  const bool dp = is_device_ptr(momenta), dw = wgt ? is_device_ptr(wgt) : true, dout = is_device_ptr(out);
+  const bool staged = !(dp && dw && dout);
+  int rc = ensure_capacity(h, (size_t)n);
+  if (rc != ME_OK) return rc;
+  const double* P = momenta;
+  const double* Wt = wgt;
+  double* O = out;
+  if (!dp) {
+    ME_CUDA(cudaMemcpyAsync(h->d_p, momenta, (size_t)n * 4 * next * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    P = h->d_p;
+  }
+  if (wgt && !dw) {
+    ME_CUDA(cudaMemcpyAsync(h->d_w, wgt, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    Wt = h->d_w;
+  }
+  if (!dout) O = h->d_out;
+  const bool mixed = h->prm.precision == ME_PREC_MIXED;
+  LaunchArgs a{};
+  a.p = P;
+  a.wgt = Wt;
+  a.n = n;
+  a.out = O;
+  a.kp = h->kp;
+  a.kp.nlo_factor = nlo_factor;
+  a.groups = n;
+  a.resc_list = h->d_resc;
+  a.resc_count = h->d_nresc;
+  if (kind == K_REAL && mixed) {
+    a.kp.flag_unstable = 1;
+    ME_CUDA(cudaMemsetAsync(h->d_nresc, 0, sizeof(int), h->stream));
+    h->last_kind = K_REAL;
+  }
+  // the first call per (kind, precision) times the lane layouts (synchronising);
+  // both are chosen before the launches whose results are kept
+  const int lpe64 = (kind == K_REAL && mixed) ? choose_lpe(h, kind, true, a) : 0;
+  const int lpe = choose_lpe(h, kind, !mixed, a);
+  ME_CUDA(dispatch(h->proc->pid, kind, !mixed, lpe, a, h->stream));
+  if (kind == K_REAL && mixed) {
+    // FP64 re-evaluation of the flagged points (count read on the device)
+    LaunchArgs r = a;
+    r.kp.flag_unstable = 0;
+    r.idx = h->d_resc;
+    r.count = h->d_nresc;
+    ME_CUDA(dispatch(h->proc->pid, kind, true, lpe64, r, h->stream));
+  }
+  k_partials<<<RED_BLOCKS, 256, 0, h->stream>>>(O, n, h->d_part);
+  k_finish<<<1, 32, 0, h->stream>>>(h->d_part, RED_BLOCKS, h->d_acc, n);
+  ME_CUDA(cudaGetLastError());
+  if (!dout) ME_CUDA(cudaMemcpyAsync(out, O, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  if (staged) ME_CUDA(cudaStreamSynchronize(h->stream));
+  return ME_OK;
+}
+
+int me_eval_born(me_handle* h, const double* momenta, const double* ps_weights, int64_t n, double* out) {
+  return run(h, K_TREE, 1.0, momenta, ps_weights, n, out);
+}
+
+int me_eval_nbody_nlo(me_handle* h, const double* momenta, const double* ps_weights, int64_t n, double* out) {
+  if (!h) return fail(ME_ERR_ARG, "NULL handle");
+  if (h->proc->pid != P_EE_UU) return fail(ME_ERR_PROCESS, "me_eval_nbody_nlo: only defined for ee_uu");
+  const double a_s = h->prm.alpha_s * (4.0 / 3.0) / (2.0 * M_PI);
+  const double c = 5.0 - 2.0 * M_PI * M_PI / 3.0 - (3.0 + 4.0 * std::log(h->prm.xi_cut)) * std::log(0.5 * h->prm.delta);
+  return run(h, K_TREE, 1.0 + a_s * c, momenta, ps_weights, n, out);
+}
+
+int me_eval_real_subtracted(me_handle* h, const double* momenta, const double* ps_weights, int64_t n, double* out) {
+  if (!h) return fail(ME_ERR_ARG, "NULL handle");
+  if (h->proc->born_pid < 0) return fail(ME_ERR_PROCESS, "me_eval_real_subtracted: process has no FKS sectors");
+  return run(h, K_REAL, 1.0, momenta, ps_weights, n, out);
+}
+
+int me_last_rescued(me_handle* h, int64_t* n_rescued) {
+  if (!h || !n_rescued) return fail(ME_ERR_ARG, "NULL argument");
+  ME_CUDA(cudaSetDevice(h->device));
+  int c = 0;
+  if (h->prm.precision == ME_PREC_MIXED && h->last_kind == K_REAL) {
+    ME_CUDA(cudaMemcpyAsync(&c, h->d_nresc, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    ME_CUDA(cudaStreamSynchronize(h->stream));
+  }
+  *n_rescued = c;
+  return ME_OK;
+}
+
+int me_get_accumulators(me_handle* h, double out[3]) {
+  if (!h || !out) return fail(ME_ERR_ARG, "NULL argument");
+  ME_CUDA(cudaSetDevice(h->device));
+  ME_CUDA(cudaMemcpyAsync(out, h->d_acc, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  ME_CUDA(cudaStreamSynchronize(h->stream));
+  return ME_OK;
+}
+
+int me_set_accumulators(me_handle* h, const double in[3]) {
+  if (!h || !in) return fail(ME_ERR_ARG, "NULL argument");
+  ME_CUDA(cudaSetDevice(h->device));
+  ME_CUDA(cudaMemcpyAsync(h->d_acc, in, 3 * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  ME_CUDA(cudaStreamSynchronize(h->stream));
+  return ME_OK;
+}
+
+int me_set_stream(me_handle* h, void* s) {
+  if (!h) return fail(ME_ERR_ARG, "NULL handle");
+  h->stream = s ? (cudaStream_t)s : h->own_stream;
+  return ME_OK;
+}
+
+int me_synchronize(me_handle* h) {
+  if (!h) return fail(ME_ERR_ARG, "NULL handle");
+  ME_CUDA(cudaSetDevice(h->device));
+  ME_CUDA(cudaStreamSynchronize(h->stream));
+  return ME_OK;
+}
+
+void me_destroy(me_handle* h) {
+  if (!h) return;
+  cudaSetDevice(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  cudaFree(h->d_p);
+  cudaFree(h->d_w);
+  cudaFree(h->d_out);
+  cudaFree(h->d_resc);
+  cudaFree(h->d_nresc);
+  cudaFree(h->d_part);
+  cudaFree(h->d_acc);
+  if (h->own_stream) cudaStreamDestroy(h->own_stream);
+  delete h;
+}
+
+}  // extern "C"
+
+int me_internal_rescued_async(me_handle* h, int* dst) {
+  if (!h || !dst) return fail(ME_ERR_ARG, "NULL argument");
+  if (h->prm.precision != ME_PREC_MIXED || h->last_kind != K_REAL) {
+    *dst = 0;
+    return ME_OK;
+  }
+  ME_CUDA(cudaMemcpyAsync(dst, h->d_nresc, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  return ME_OK;
+}
+
+int me_internal_fail(int code, const char* msg) { return fail(code, msg ? msg : ""); }
+
+int me_internal_process_id(const char* name) {
+  if (!name) return -1;
+  for (const auto& d : kProcs)
+    if (std::strcmp(d.name, name) == 0) return d.pid;
+  return -1;
+}

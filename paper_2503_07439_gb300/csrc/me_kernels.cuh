@@ -1,0 +1,452 @@
+// Kernels of the event-parallel NLO hot path (templates; instantiated in me_inst_*.cu).
+//
+// Layout: momenta are structure-of-arrays float64 p[comp][leg][n] (comp = E,px,py,pz),
+// so that consecutive events are consecutive addresses; weights are float64 w[n].
+// A group of LPE consecutive lanes handles one event: the lanes split the helicity
+// sum (and, for the subtracted real, the Born-kinematics tasks) and reduce with warp
+// shuffles.  Born, real, soft and collinear terms are evaluated for every point and
+// masked afterwards (Sec. 4.3, Algorithm 2), so a warp never diverges on cuts.
+#pragma once
+#include "me_procs.cuh"
+
+namespace me {
+
+constexpr int MAX_FLOW = 24;
+constexpr int N_PAIRS = 10;  // unordered pairs (k<=l) of the 4 coloured legs of a 2->2 Born
+
+// Device-resident process constants (written once per device at set-up):
+// colour matrices (row-major NFLOW x NFLOW, in double and float) and the 2->2 Born
+// colour correlators C^{kl} (pair order (0,0),(0,1),..,(3,3); [0] gg->tt, [1] uu->tt).
+struct ColourTables {
+  double C[P_COUNT][MAX_FLOW * MAX_FLOW];
+  float Cf[P_COUNT][MAX_FLOW * MAX_FLOW];
+  double Ccorr[2][N_PAIRS][4];
+};
+
+struct KParams {
+  Couplings cp;
+  double avg_inv;       // 1 / (initial spin x colour average), x identical-particle factor
+  double born_avg_inv;  // same for the underlying Born of a real process
+  double nlo_factor;    // Born -> Born * factor (n-body NLO entry), else 1
+  double xi_cut, delta; // FKS plus-distribution cut-offs
+  double xi_thr, y_thr; // points with xi < xi_thr or 1-y < y_thr go to the FP64 path
+  double me_eps;        // assumed relative error of a bulk-precision matrix element
+  double tol;           // target relative accuracy of a weight
+  int flag_unstable;    // 1: append unstable points to the rescue list
+  const ColourTables* tab;
+};
+
+template <typename T> __device__ __forceinline__ const T* ctab(const ColourTables* t, int pid);
+template <> __device__ __forceinline__ const double* ctab<double>(const ColourTables* t, int pid) { return t->C[pid]; }
+template <> __device__ __forceinline__ const float* ctab<float>(const ColourTables* t, int pid) { return t->Cf[pid]; }
+
+template <int PID, typename T>
+__device__ __forceinline__ T colour_sum(const ColourTables* tab, const cx<T>* J) {
+  constexpr int NF = Proc<PID>::NFLOW;
+  const T* __restrict__ Cm = ctab<T>(tab, PID);
+  T s = T(0);
+#pragma unroll 4
+  for (int a = 0; a < NF; ++a) {
+    T zr = T(0), zi = T(0);
+#pragma unroll 8
+    for (int b = 0; b < NF; ++b) {
+      const T c = Cm[a * NF + b];
+      zr += c * J[b].re;
+      zi += c * J[b].im;
+    }
+    s += J[a].re * zr + J[a].im * zi;
+  }
+  return s;
+}
+
+// J^dagger M J for a real symmetric 2x2 matrix M (row-major)
+template <typename T>
+__device__ __forceinline__ T quad2(const T* M, const cx<T>* J) {
+  return M[0] * norm2(J[0]) + M[3] * norm2(J[1]) + T(2) * M[1] * (J[0].re * J[1].re + J[0].im * J[1].im);
+}
+
+template <int LPE, typename T>
+__device__ __forceinline__ T group_sum(T v, unsigned mask) {
+#pragma unroll
+  for (int o = LPE / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, LPE);
+  return v;
+}
+
+template <int LPE>
+__device__ __forceinline__ unsigned group_mask() {
+  if constexpr (LPE == 32) {
+    return 0xffffffffu;
+  } else {
+    const unsigned lane = threadIdx.x & 31u;
+    return ((1u << LPE) - 1u) << (lane & ~(unsigned)(LPE - 1));
+  }
+}
+
+template <int NEXT>
+__device__ __forceinline__ void load_event(const double* __restrict__ p, long n, long i, r4<double>* k) {
+#pragma unroll
+  for (int l = 0; l < NEXT; ++l) {
+    k[l].e = __ldg(p + (0L * NEXT + l) * n + i);
+    k[l].x = __ldg(p + (1L * NEXT + l) * n + i);
+    k[l].y = __ldg(p + (2L * NEXT + l) * n + i);
+    k[l].z = __ldg(p + (3L * NEXT + l) * n + i);
+  }
+}
+
+// ---------------------------------------------------------------- tree |M|^2
+// out[i] = wgt[i] * |M|^2(p_i) * nlo_factor.  `idx` (optional): event list to process
+// (the FP64 rescue of flagged points); `count` then holds its length on the device.
+template <int PID, typename T, int LPE>
+__global__ void __launch_bounds__(128) k_tree(const double* __restrict__ p, const double* __restrict__ wgt, long n,
+                                              double* __restrict__ out, KParams kp, const int* __restrict__ idx,
+                                              const int* __restrict__ count) {
+  constexpr int NEXT = Proc<PID>::NEXT, NHEL = Proc<PID>::NHEL, NF = Proc<PID>::NFLOW;
+  const long gid = ((long)blockIdx.x * blockDim.x + threadIdx.x) / LPE;
+  const int lane = threadIdx.x % LPE;
+  const long nev = idx ? (long)*count : n;
+  if (gid >= nev) return;
+  const long ev = idx ? (long)idx[gid] : gid;
+  r4<double> k[NEXT];
+  load_event<NEXT>(p, n, ev, k);
+  T acc = T(0);
+  for (int h = lane; h < NHEL; h += LPE) {
+    cx<T> J[NF];
+    amplitude<PID, T>(k, h, kp.cp, J);
+    acc += colour_sum<PID, T>(kp.tab, J);
+  }
+  double tot = (double)group_sum<LPE>(acc, group_mask<LPE>());
+  if (lane == 0) {
+    const double w = wgt ? wgt[ev] : 1.0;
+    out[ev] = w * tot * kp.avg_inv * kp.nlo_factor;
+  }
+}
+
+// ---------------------------------------------------------------- FKS kinematics (double)
+__device__ __forceinline__ r4<double> boost(const r4<double>& p, double bx, double by, double bz) {
+  const double b2 = bx * bx + by * by + bz * bz;
+  const double g = 1.0 / sqrt(1.0 - b2);
+  const double bp = bx * p.x + by * p.y + bz * p.z;
+  const double g2 = b2 > 0.0 ? (g - 1.0) / b2 : 0.0;
+  const double c = g2 * bp + g * p.e;
+  return r4<double>{g * (p.e + bp), p.x + c * bx, p.y + c * by, p.z + c * bz};
+}
+
+__device__ __forceinline__ void unit3(const r4<double>& p, double& x, double& y, double& z) {
+  const double a = 1.0 / sqrt(p.x * p.x + p.y * p.y + p.z * p.z);
+  x = p.x * a;
+  y = p.y * a;
+  z = p.z * a;
+}
+
+constexpr double PI = 3.14159265358979323846;
+constexpr double CF_ = 4.0 / 3.0;
+constexpr double CA_ = 3.0;
+
+// Initial-state FKS sectors (i = gluon leg 4, j = beam 0 or 1) of 2 -> Q Qbar g.
+struct IsrKin {
+  double xi, y[2], S[2], K, K0;
+  r4<double> soft[4];     // soft Born: beams, heavy pair at sqrt(s) along n*
+  r4<double> coll[2][4];  // collinear Born of sector j: beam j scaled by (1-xi)
+  double qdir[3];         // gluon direction
+  double cphi, sphi;      // gluon azimuth
+};
+
+__device__ __forceinline__ void isr_map(const r4<double>* k, double mass, IsrKin& o) {
+  const double rs = k[0].e + k[1].e, s = rs * rs;
+  o.xi = 2.0 * k[4].e / rs;
+  unit3(k[4], o.qdir[0], o.qdir[1], o.qdir[2]);
+  double b0[3], b1[3];
+  unit3(k[0], b0[0], b0[1], b0[2]);
+  unit3(k[1], b1[0], b1[1], b1[2]);
+  o.y[0] = o.qdir[0] * b0[0] + o.qdir[1] * b0[1] + o.qdir[2] * b0[2];
+  o.y[1] = o.qdir[0] * b1[0] + o.qdir[1] * b1[1] + o.qdir[2] * b1[2];
+  const double d0 = 1.0 - o.y[0], d1 = 1.0 - o.y[1];
+  o.S[0] = d1 / (d0 + d1);
+  o.S[1] = d0 / (d0 + d1);
+  const double pt = sqrt(o.qdir[0] * o.qdir[0] + o.qdir[1] * o.qdir[1]);
+  o.cphi = pt > 0.0 ? o.qdir[0] / pt : 1.0;
+  o.sphi = pt > 0.0 ? o.qdir[1] / pt : 0.0;
+  // heavy-pair rest-frame direction of the quark
+  const r4<double> Q = k[0] + k[1] - k[4];
+  const r4<double> ks = boost(k[2], -Q.x / Q.e, -Q.y / Q.e, -Q.z / Q.e);
+  double n[3];
+  unit3(ks, n[0], n[1], n[2]);
+  const double beta = sqrt(1.0 - 4.0 * mass * mass / s);
+  o.soft[0] = k[0];
+  o.soft[1] = k[1];
+  const double e = 0.5 * rs, pa = 0.5 * rs * beta;
+  o.soft[2] = r4<double>{e, pa * n[0], pa * n[1], pa * n[2]};
+  o.soft[3] = r4<double>{e, -pa * n[0], -pa * n[1], -pa * n[2]};
+  const double z = 1.0 - o.xi;
+  const double M = sqrt(s * z);
+  const double bQ = sqrt(fmax(0.0, 1.0 - 4.0 * mass * mass / (s * z)));
+  const double eQ = 0.5 * M, pQ = 0.5 * M * bQ;
+  const r4<double> tr{eQ, pQ * n[0], pQ * n[1], pQ * n[2]};
+  const r4<double> tbr{eQ, -pQ * n[0], -pQ * n[1], -pQ * n[2]};
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    o.coll[j][0] = j == 0 ? scale(z, k[0]) : k[0];
+    o.coll[j][1] = j == 1 ? scale(z, k[1]) : k[1];
+    const r4<double> Qc = o.coll[j][0] + o.coll[j][1];
+    const double bx = Qc.x / Qc.e, by = Qc.y / Qc.e, bz = Qc.z / Qc.e;
+    o.coll[j][2] = boost(tr, bx, by, bz);
+    o.coll[j][3] = boost(tbr, bx, by, bz);
+  }
+  o.K = s * bQ / (64.0 * PI * PI * PI * beta);
+  o.K0 = s / (64.0 * PI * PI * PI);
+}
+
+// Final-state FKS sectors (i = gluon leg 4, j = leg 2 or 3) of massless 2 -> 3.
+struct FsrKin {
+  double xi, y[2], S[2], K[2], K0, K1;
+  r4<double> born[2][4];
+  double qdir[3];
+};
+
+__device__ __forceinline__ void fsr_map(const r4<double>* k, FsrKin& o) {
+  const double rs = k[0].e + k[1].e, s = rs * rs;
+  o.xi = 2.0 * k[4].e / rs;
+  unit3(k[4], o.qdir[0], o.qdir[1], o.qdir[2]);
+  double nj[2][3];
+  unit3(k[2], nj[0][0], nj[0][1], nj[0][2]);
+  unit3(k[3], nj[1][0], nj[1][1], nj[1][2]);
+  double c[2];
+#pragma unroll
+  for (int j = 0; j < 2; ++j) c[j] = o.qdir[0] * nj[j][0] + o.qdir[1] * nj[j][1] + o.qdir[2] * nj[j][2];
+  const double d0 = 1.0 - c[0], d1 = 1.0 - c[1];
+  o.S[0] = d1 / (d0 + d1);
+  o.S[1] = d0 / (d0 + d1);
+  const double e = 0.5 * rs;
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    o.y[j] = c[j];
+    o.born[j][0] = k[0];
+    o.born[j][1] = k[1];
+    const r4<double> a{e, e * nj[j][0], e * nj[j][1], e * nj[j][2]};
+    const r4<double> b{e, -e * nj[j][0], -e * nj[j][1], -e * nj[j][2]};
+    o.born[j][2 + j] = a;
+    o.born[j][3 - j] = b;
+    const double den = 2.0 - o.xi * (1.0 - o.y[j]);
+    o.K[j] = s * (1.0 - o.xi) / (16.0 * PI * PI * PI * den * den);
+  }
+  o.K0 = s / (64.0 * PI * PI * PI);
+  o.K1 = s * (1.0 - o.xi) / (64.0 * PI * PI * PI);
+}
+
+__device__ __forceinline__ double eik(const r4<double>& a, const r4<double>& b, const double* q) {
+  const r4<double> qq{1.0, q[0], q[1], q[2]};
+  return mdot(a, b) / (mdot(a, qq) * mdot(b, qq));
+}
+
+// ---------------------------------------------------------------- real - counterterms
+// out[i] = wgt[i] * sum over FKS sectors of the subtracted real (ME units), see
+// the FKS formula: W_j = R S_j - [Th_s G(0,y) + Th_c G(xi,1) - Th_s Th_c G(0,1)] / (xi^2 (1-y) K).
+template <int PID, typename T, int LPE>
+__global__ void __launch_bounds__(128) k_real_sub(const double* __restrict__ p, const double* __restrict__ wgt,
+                                                  long n, double* __restrict__ out, KParams kp,
+                                                  const int* __restrict__ idx, const int* __restrict__ count,
+                                                  int* __restrict__ resc_list, int* __restrict__ resc_count) {
+  constexpr int NEXT = Proc<PID>::NEXT, NHEL = Proc<PID>::NHEL, NF = Proc<PID>::NFLOW;
+  constexpr int BPID = (PID == P_EE_UUG) ? P_EE_UU : (PID == P_GG_TTG ? P_GG_TT : P_UU_TT);
+  constexpr int BNF = Proc<BPID>::NFLOW;
+  const long gid = ((long)blockIdx.x * blockDim.x + threadIdx.x) / LPE;
+  const int lane = threadIdx.x % LPE;
+  const long nev = idx ? (long)*count : n;
+  if (gid >= nev) return;
+  const long ev = idx ? (long)idx[gid] : gid;
+  const unsigned mask = group_mask<LPE>();
+  r4<double> k[NEXT];
+  load_event<NEXT>(p, n, ev, k);
+  const double rs = k[0].e + k[1].e, s = rs * rs;
+  const double g2 = kp.cp.gs * kp.cp.gs;
+
+  // real matrix element
+  T accR = T(0);
+  for (int h = lane; h < NHEL; h += LPE) {
+    cx<T> J[NF];
+    amplitude<PID, T>(k, h, kp.cp, J);
+    accR += colour_sum<PID, T>(kp.tab, J);
+  }
+  const double R = (double)group_sum<LPE>(accR, mask) * kp.avg_inv;
+
+  double W = 0.0, mag = 0.0;
+  bool near = false;
+  if constexpr (PID == P_EE_UUG) {
+    FsrKin f;
+    fsr_map(k, f);
+    T aB[2] = {T(0), T(0)};
+    for (int t = lane; t < 32; t += LPE) {
+      const int j = t >> 4, h = t & 15;
+      cx<T> J[BNF];
+      amplitude<BPID, T>(f.born[j], h, kp.cp, J);
+      aB[j] += colour_sum<BPID, T>(kp.tab, J);
+    }
+    double B[2];
+    B[0] = (double)group_sum<LPE>(aB[0], mask) * kp.born_avg_inv;
+    B[1] = (double)group_sum<LPE>(aB[1], mask) * kp.born_avg_inv;
+    const double th_s = f.xi < kp.xi_cut ? 1.0 : 0.0;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      // soft: sum_{kl} w_kl B_kl with B_23 = B_32 = -C_F B (massless diagonal terms vanish)
+      const double x2R = -(4.0 * g2 / s) * 2.0 * eik(f.born[j][2], f.born[j][3], f.qdir) * (-CF_ * B[j]);
+      const double Gs = (1.0 - f.y[j]) * 0.5 * (1.0 + f.y[j]) * f.K0 * x2R;
+      const double Gc = f.K1 * (2.0 / (s * (1.0 - f.xi))) * 2.0 * g2 * CF_ * (1.0 + (1.0 - f.xi) * (1.0 - f.xi)) * B[j];
+      const double Gsc = f.K0 * (2.0 / s) * 2.0 * g2 * 2.0 * CF_ * B[j];
+      const double th_c = f.y[j] > 1.0 - kp.delta ? 1.0 : 0.0;
+      const double ct = (th_s * Gs + th_c * Gc - th_s * th_c * Gsc) / (f.xi * f.xi * (1.0 - f.y[j]) * f.K[j]);
+      const double rsj = R * f.S[j];
+      W += rsj - ct;
+      mag += fabs(rsj) + fabs(ct);
+      near |= (th_s > 0.0 && f.xi < kp.xi_thr) || (th_c > 0.0 && 1.0 - f.y[j] < kp.y_thr);
+    }
+  } else {
+    IsrKin f;
+    isr_map(k, kp.cp.mt, f);
+    // eikonal-weighted colour-correlation matrix E = sum_{k,l} w_kl C^{kl} (2x2)
+    const int ci = (BPID == P_GG_TT) ? 0 : 1;
+    double E[4] = {0.0, 0.0, 0.0, 0.0};
+    {
+      int pr = 0;
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = a; b < 4; ++b, ++pr) {
+          const double w = eik(f.soft[a], f.soft[b], f.qdir) * (a == b ? 1.0 : 2.0);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) E[q] += w * kp.tab->Ccorr[ci][pr][q];
+        }
+    }
+    const T Et[4] = {(T)E[0], (T)E[1], (T)E[2], (T)E[3]};
+    c4<T> eperp;
+    eperp.v[0] = cx<T>{T(0), T(0)};
+    eperp.v[1] = cx<T>{(T)f.cphi, T(0)};
+    eperp.v[2] = cx<T>{(T)f.sphi, T(0)};
+    eperp.v[3] = cx<T>{T(0), T(0)};
+    // Born tasks: [0,16) soft, [16,32) collinear, gg only: [32,40) perp leg 0, [40,48) perp leg 1
+    constexpr int NTASK = (BPID == P_GG_TT) ? 48 : 32;
+    T aE = T(0), aS = T(0), aC = T(0), aP[2] = {T(0), T(0)};
+    for (int t = lane; t < NTASK; t += LPE) {
+      cx<T> J[BNF];
+      if (t < 16) {
+        amplitude<BPID, T>(f.soft, t, kp.cp, J);
+        aE += quad2(Et, J);
+        aS += colour_sum<BPID, T>(kp.tab, J);
+      } else if (t < 32) {
+        amplitude<BPID, T>(f.coll[0], t - 16, kp.cp, J);
+        aC += colour_sum<BPID, T>(kp.tab, J);
+      } else {
+        const int j = (t - 32) >> 3;
+        const int r = (t - 32) & 7;
+        // helicities of the three other legs; the polarised gluon's bit is ignored
+        const int h = j == 0 ? (r << 1) : ((r & 1) | ((r >> 1) << 2));
+        amplitude<BPID, T>(f.coll[j], h, kp.cp, J, &eperp, j);
+        aP[j] += colour_sum<BPID, T>(kp.tab, J);
+      }
+    }
+    const double bav = kp.born_avg_inv;
+    const double x2R = -(4.0 * g2 / s) * (double)group_sum<LPE>(aE, mask) * bav;
+    const double Bs = (double)group_sum<LPE>(aS, mask) * bav;
+    const double Bc = (double)group_sum<LPE>(aC, mask) * bav;
+    double Bp[2] = {0.0, 0.0};
+    if constexpr (BPID == P_GG_TT) {
+      Bp[0] = (double)group_sum<LPE>(aP[0], mask) * bav;
+      Bp[1] = (double)group_sum<LPE>(aP[1], mask) * bav;
+    }
+    const double xi = f.xi, z = 1.0 - xi;
+    const double th_s = xi < kp.xi_cut ? 1.0 : 0.0;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const double Gs = (1.0 - f.y[j]) * f.S[j] * f.K0 * x2R;
+      double xiP, xiP0;
+      if constexpr (BPID == P_GG_TT) {
+        xiP = 2.0 * CA_ * ((z + xi * xi * z) * Bc + 2.0 * (xi * xi / z) * Bp[j]);
+        xiP0 = 2.0 * CA_ * Bs;
+      } else {
+        xiP = CF_ * (1.0 + z * z) * Bc;
+        xiP0 = 2.0 * CF_ * Bs;
+      }
+      const double Gc = f.K * (2.0 / s) * (1.0 / z) * 2.0 * g2 * xiP;
+      const double Gsc = f.K0 * (2.0 / s) * 2.0 * g2 * xiP0;
+      const double th_c = f.y[j] > 1.0 - kp.delta ? 1.0 : 0.0;
+      const double ct = (th_s * Gs + th_c * Gc - th_s * th_c * Gsc) / (xi * xi * (1.0 - f.y[j]) * f.K);
+      const double rsj = R * f.S[j];
+      W += rsj - ct;
+      mag += fabs(rsj) + fabs(ct);
+      near |= (th_s > 0.0 && xi < kp.xi_thr) || (th_c > 0.0 && 1.0 - f.y[j] < kp.y_thr);
+    }
+  }
+  if (lane == 0) {
+    const double w = wgt ? wgt[ev] : 1.0;
+    out[ev] = w * W;
+    if (kp.flag_unstable) {
+      // cancellation test: |R S| + |CT| relative to |W|, times the bulk-precision error
+      const bool unstable = near || !(mag * kp.me_eps <= 0.125 * kp.tol * fabs(W));
+      if (unstable) {
+        const int slot = atomicAdd(resc_count, 1);
+        resc_list[slot] = (int)ev;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- weight accumulation
+// Deterministic two-pass reduction: per-block partial (sum w, sum w^2) in a fixed tree
+// order, then one block adds the partials in block order.  No floating atomics.
+__global__ void k_partials(const double* __restrict__ w, long n, double* __restrict__ part);
+__global__ void k_finish(const double* __restrict__ part, int nblk, double* __restrict__ acc, long n);
+
+// ---------------------------------------------------------------- launch registry
+struct LaunchArgs {
+  const double* p;
+  const double* wgt;
+  long n;
+  double* out;
+  KParams kp;
+  const int* idx;    // optional event list (rescue), length *count on the device
+  const int* count;
+  int* resc_list;    // real kernel in bulk precision: unstable points are appended here
+  int* resc_count;
+  long groups;       // number of event groups to launch (n, or the list capacity)
+};
+enum KernelKind : int { K_TREE = 0, K_REAL = 1 };
+
+template <int PID, typename T, int LPE>
+cudaError_t launch_one(int kind, const LaunchArgs& a, cudaStream_t st) {
+  const int threads = 128;
+  const long total = a.groups * LPE;
+  const long blocks = (total + threads - 1) / threads;
+  if (blocks <= 0) return cudaSuccess;
+  if (kind == K_TREE) {
+    k_tree<PID, T, LPE><<<(unsigned)blocks, threads, 0, st>>>(a.p, a.wgt, a.n, a.out, a.kp, a.idx, a.count);
+  } else {
+    if constexpr (PID == P_EE_UUG || PID == P_GG_TTG || PID == P_UU_TTG)
+      k_real_sub<PID, T, LPE><<<(unsigned)blocks, threads, 0, st>>>(a.p, a.wgt, a.n, a.out, a.kp, a.idx, a.count,
+                                                                       a.resc_list, a.resc_count);
+    else
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// per-process launchers (one translation unit each); lpe in {4, 8, 16, 32}
+cudaError_t launch_ee(int pid, int kind, bool fp64, int lpe, const LaunchArgs& a, cudaStream_t st);
+cudaError_t launch_gg(int pid, int kind, bool fp64, int lpe, const LaunchArgs& a, cudaStream_t st);
+cudaError_t launch_ggg(int pid, int kind, bool fp64, int lpe, const LaunchArgs& a, cudaStream_t st);
+cudaError_t launch_uu(int pid, int kind, bool fp64, int lpe, const LaunchArgs& a, cudaStream_t st);
+
+}  // namespace me
+
+#define ME_LPE_SWITCH(PID, T)                                            \
+  switch (lpe) {                                                         \
+    case 4: return me::launch_one<PID, T, 4>(kind, a, st);               \
+    case 8: return me::launch_one<PID, T, 8>(kind, a, st);               \
+    case 16: return me::launch_one<PID, T, 16>(kind, a, st);             \
+    case 32: return me::launch_one<PID, T, 32>(kind, a, st);             \
+    default: return cudaErrorInvalidValue;                               \
+  }
+#define ME_PREC_SWITCH(PID)                      \
+  if (fp64) {                                    \
+    ME_LPE_SWITCH(PID, double)                   \
+  } else {                                       \
+    ME_LPE_SWITCH(PID, float)                    \
+  }

@@ -1,0 +1,274 @@
+// Device arithmetic for helicity amplitudes: complex numbers, four-vectors,
+// Dirac spinors in the chiral representation, colour-stripped vertex routines.
+//
+// Conventions (standard QFT; the paper fixes none): metric (+,-,-,-); chiral
+// gamma matrices gamma^0 = [[0,1],[1,0]], gamma^k = [[0,s^k],[-s^k,0]], so that
+//   Vslash = [[0, V0 - s.V], [V0 + s.V, 0]];
+// helicity spinors u(p,l) = (w_{-l} chi_l, w_{+l} chi_l),
+//   v(p,l) = (-l w_{+l} chi_{-l}, l w_{-l} chi_{-l}), w_+- = sqrt(E +- |p|);
+// polarisation vectors eps(k,l) = (-l e1 - i e2)/sqrt(2).
+// Everything is templated on the arithmetic type T (float for the bulk path,
+// double for the FP64 path and the rescue of unstable points).
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+
+namespace me {
+
+template <typename T>
+struct cx {
+  T re, im;
+};
+
+template <typename T> __device__ __forceinline__ cx<T> mk(T r, T i) { return cx<T>{r, i}; }
+template <typename T> __device__ __forceinline__ cx<T> operator+(cx<T> a, cx<T> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename T> __device__ __forceinline__ cx<T> operator-(cx<T> a, cx<T> b) { return {a.re - b.re, a.im - b.im}; }
+template <typename T> __device__ __forceinline__ cx<T> operator-(cx<T> a) { return {-a.re, -a.im}; }
+template <typename T> __device__ __forceinline__ cx<T> operator*(cx<T> a, cx<T> b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename T> __device__ __forceinline__ cx<T> operator*(T s, cx<T> a) { return {s * a.re, s * a.im}; }
+template <typename T> __device__ __forceinline__ cx<T> operator*(cx<T> a, T s) { return {s * a.re, s * a.im}; }
+template <typename T> __device__ __forceinline__ cx<T> conj(cx<T> a) { return {a.re, -a.im}; }
+template <typename T> __device__ __forceinline__ cx<T> times_i(cx<T> a) { return {-a.im, a.re}; }
+template <typename T> __device__ __forceinline__ T norm2(cx<T> a) { return a.re * a.re + a.im * a.im; }
+
+// complex four-component object: a Lorentz vector with upper index, or a Dirac spinor
+template <typename T>
+struct c4 {
+  cx<T> v[4];
+};
+
+template <typename T>
+struct r4 {  // real four-vector (E, px, py, pz)
+  T e, x, y, z;
+};
+
+template <typename T> __device__ __forceinline__ r4<T> operator+(r4<T> a, r4<T> b) { return {a.e + b.e, a.x + b.x, a.y + b.y, a.z + b.z}; }
+template <typename T> __device__ __forceinline__ r4<T> operator-(r4<T> a, r4<T> b) { return {a.e - b.e, a.x - b.x, a.y - b.y, a.z - b.z}; }
+template <typename T> __device__ __forceinline__ r4<T> operator-(r4<T> a) { return {-a.e, -a.x, -a.y, -a.z}; }
+template <typename T> __device__ __forceinline__ r4<T> scale(T s, r4<T> a) { return {s * a.e, s * a.x, s * a.y, s * a.z}; }
+template <typename T> __device__ __forceinline__ T mdot(r4<T> a, r4<T> b) { return a.e * b.e - a.x * b.x - a.y * b.y - a.z * b.z; }
+template <typename U, typename T> __device__ __forceinline__ r4<U> cast4(r4<T> a) { return {(U)a.e, (U)a.x, (U)a.y, (U)a.z}; }
+
+// complex-vector . complex-vector (Minkowski, no conjugation)
+template <typename T>
+__device__ __forceinline__ cx<T> cdot(const c4<T>& a, const c4<T>& b) {
+  return a.v[0] * b.v[0] - a.v[1] * b.v[1] - a.v[2] * b.v[2] - a.v[3] * b.v[3];
+}
+// real-vector . complex-vector
+template <typename T>
+__device__ __forceinline__ cx<T> rdot(const r4<T>& a, const c4<T>& b) {
+  return a.e * b.v[0] - a.x * b.v[1] - a.y * b.v[2] - a.z * b.v[3];
+}
+template <typename T>
+__device__ __forceinline__ void cadd(c4<T>& acc, const c4<T>& x) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) acc.v[i] = acc.v[i] + x.v[i];
+}
+template <typename T>
+__device__ __forceinline__ void caxpy(c4<T>& acc, cx<T> a, const c4<T>& x) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) acc.v[i] = acc.v[i] + a * x.v[i];
+}
+template <typename T>
+__device__ __forceinline__ void cscale(c4<T>& x, cx<T> a) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) x.v[i] = a * x.v[i];
+}
+template <typename T>
+__device__ __forceinline__ void cscale(c4<T>& x, T a) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) x.v[i] = a * x.v[i];
+}
+template <typename T>
+__device__ __forceinline__ c4<T> czero() {
+  c4<T> z;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) z.v[i] = cx<T>{T(0), T(0)};
+  return z;
+}
+
+// ---------------------------------------------------------------- wavefunctions
+// two-component helicity eigenstate chi_lam along p/|p|; |p|+pz is formed without
+// cancellation as pt^2/(|p|-pz) when pz < 0.
+template <typename T>
+__device__ __forceinline__ void chi(const r4<T>& p, int lam, cx<T>& c0, cx<T>& c1) {
+  T pt2 = p.x * p.x + p.y * p.y;
+  T pa = sqrt(pt2 + p.z * p.z);
+  T s = (p.z >= T(0)) ? pa + p.z : pt2 / (pa - p.z);
+  if (s > T(0)) {
+    T rden = T(1) / sqrt(T(2) * pa * s);
+    if (lam > 0) {
+      c0 = cx<T>{s * rden, T(0)};
+      c1 = cx<T>{p.x * rden, p.y * rden};
+    } else {
+      c0 = cx<T>{-p.x * rden, p.y * rden};
+      c1 = cx<T>{s * rden, T(0)};
+    }
+  } else {  // exactly along -z
+    if (lam > 0) {
+      c0 = cx<T>{T(0), T(0)};
+      c1 = cx<T>{T(1), T(0)};
+    } else {
+      c0 = cx<T>{T(-1), T(0)};
+      c1 = cx<T>{T(0), T(0)};
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void omegas(const r4<T>& p, T m, T& wp, T& wm) {
+  T pa = sqrt(p.x * p.x + p.y * p.y + p.z * p.z);
+  wp = sqrt(p.e + pa);
+  wm = (m == T(0)) ? T(0) : m / wp;
+}
+
+template <typename T>
+__device__ __forceinline__ c4<T> spinor_u(const r4<T>& p, T m, int lam) {
+  T wp, wm;
+  omegas(p, m, wp, wm);
+  cx<T> a, b;
+  chi(p, lam, a, b);
+  T top = lam > 0 ? wm : wp, bot = lam > 0 ? wp : wm;
+  return c4<T>{{top * a, top * b, bot * a, bot * b}};
+}
+
+template <typename T>
+__device__ __forceinline__ c4<T> spinor_v(const r4<T>& p, T m, int lam) {
+  T wp, wm;
+  omegas(p, m, wp, wm);
+  cx<T> a, b;
+  chi(p, -lam, a, b);
+  T top = lam > 0 ? -wp : wm;   // -lam * w_{+lam}
+  T bot = lam > 0 ? wm : -wp;   //  lam * w_{-lam}
+  return c4<T>{{top * a, top * b, bot * a, bot * b}};
+}
+
+// Dirac adjoint psi^dagger gamma^0 (chiral rep: swap blocks, conjugate)
+template <typename T>
+__device__ __forceinline__ c4<T> dbar(const c4<T>& s) {
+  return c4<T>{{conj(s.v[2]), conj(s.v[3]), conj(s.v[0]), conj(s.v[1])}};
+}
+
+template <typename T>
+__device__ __forceinline__ c4<T> polvec(const r4<T>& k, int lam, bool outgoing) {
+  T pt2 = k.x * k.x + k.y * k.y;
+  T pt = sqrt(pt2);
+  T ka = sqrt(pt2 + k.z * k.z);
+  T ct = k.z / ka, st = pt / ka;
+  T cp = T(1), sp = T(0);
+  if (pt > T(0)) {
+    cp = k.x / pt;
+    sp = k.y / pt;
+  }
+  const T r2 = T(0.70710678118654752440);
+  // eps = (-lam e1 - i e2)/sqrt(2), e1 = (0, ct cp, ct sp, -st), e2 = (0, -sp, cp, 0)
+  T l = (T)lam;
+  c4<T> e;
+  e.v[0] = cx<T>{T(0), T(0)};
+  e.v[1] = cx<T>{-l * ct * cp * r2, sp * r2};
+  e.v[2] = cx<T>{-l * ct * sp * r2, -cp * r2};
+  e.v[3] = cx<T>{l * st * r2, T(0)};
+  if (outgoing) {
+#pragma unroll
+    for (int i = 1; i < 4; ++i) e.v[i] = conj(e.v[i]);
+  }
+  return e;
+}
+
+// ---------------------------------------------------------------- Dirac algebra
+// row spinor times Vslash (V complex, upper index)
+template <typename T>
+__device__ __forceinline__ c4<T> row_slash(const c4<T>& r, const c4<T>& V) {
+  cx<T> a = V.v[0] - V.v[3], b = V.v[0] + V.v[3];
+  cx<T> c = V.v[1] - times_i(V.v[2]);  // V1 - i V2
+  cx<T> d = V.v[1] + times_i(V.v[2]);  // V1 + i V2
+  c4<T> o;
+  o.v[0] = r.v[2] * b + r.v[3] * d;
+  o.v[1] = r.v[2] * c + r.v[3] * a;
+  o.v[2] = r.v[0] * a - r.v[1] * d;
+  o.v[3] = -(r.v[0] * c) + r.v[1] * b;
+  return o;
+}
+// Vslash times column spinor
+template <typename T>
+__device__ __forceinline__ c4<T> slash_col(const c4<T>& V, const c4<T>& s) {
+  cx<T> a = V.v[0] - V.v[3], b = V.v[0] + V.v[3];
+  cx<T> c = V.v[1] - times_i(V.v[2]);
+  cx<T> d = V.v[1] + times_i(V.v[2]);
+  c4<T> o;
+  o.v[0] = a * s.v[2] - c * s.v[3];
+  o.v[1] = -(d * s.v[2]) + b * s.v[3];
+  o.v[2] = b * s.v[0] + c * s.v[1];
+  o.v[3] = d * s.v[0] + a * s.v[1];
+  return o;
+}
+// row spinor times (Qslash + m), Q real
+template <typename T>
+__device__ __forceinline__ c4<T> row_prop(const c4<T>& r, const r4<T>& Q, T m) {
+  T a = Q.e - Q.z, b = Q.e + Q.z;
+  cx<T> c = cx<T>{Q.x, -Q.y}, d = cx<T>{Q.x, Q.y};
+  c4<T> o;
+  o.v[0] = b * r.v[2] + r.v[3] * d + m * r.v[0];
+  o.v[1] = r.v[2] * c + a * r.v[3] + m * r.v[1];
+  o.v[2] = a * r.v[0] - r.v[1] * d + m * r.v[2];
+  o.v[3] = -(r.v[0] * c) + b * r.v[1] + m * r.v[3];
+  return o;
+}
+// (-Qslash + m) times column spinor, Q real
+template <typename T>
+__device__ __forceinline__ c4<T> col_prop(const r4<T>& Q, T m, const c4<T>& s) {
+  T a = Q.e - Q.z, b = Q.e + Q.z;
+  cx<T> c = cx<T>{Q.x, -Q.y}, d = cx<T>{Q.x, Q.y};
+  c4<T> o;
+  o.v[0] = m * s.v[0] - (a * s.v[2] - c * s.v[3]);
+  o.v[1] = m * s.v[1] - (-(d * s.v[2]) + b * s.v[3]);
+  o.v[2] = m * s.v[2] - (b * s.v[0] + c * s.v[1]);
+  o.v[3] = m * s.v[3] - (d * s.v[0] + a * s.v[1]);
+  return o;
+}
+// vector current J^mu = r gamma^mu s
+template <typename T>
+__device__ __forceinline__ c4<T> vcurrent(const c4<T>& r, const c4<T>& s) {
+  c4<T> J;
+  J.v[0] = r.v[0] * s.v[2] + r.v[1] * s.v[3] + r.v[2] * s.v[0] + r.v[3] * s.v[1];
+  J.v[1] = (r.v[0] * s.v[3] + r.v[1] * s.v[2]) - (r.v[2] * s.v[1] + r.v[3] * s.v[0]);
+  J.v[2] = times_i((r.v[1] * s.v[2] - r.v[0] * s.v[3]) - (r.v[3] * s.v[0] - r.v[2] * s.v[1]));
+  J.v[3] = (r.v[0] * s.v[2] - r.v[1] * s.v[3]) - (r.v[2] * s.v[0] - r.v[3] * s.v[1]);
+  return J;
+}
+template <typename T>
+__device__ __forceinline__ cx<T> spdot(const c4<T>& r, const c4<T>& s) {
+  return r.v[0] * s.v[0] + r.v[1] * s.v[1] + r.v[2] * s.v[2] + r.v[3] * s.v[3];
+}
+
+// ---------------------------------------------------------------- gluon vertices
+// three-gluon Lorentz structure contracted with J1_mu J2_nu, momenta k1,k2,k3 incoming:
+// W^rho = (J1.J2)(k1-k2)^rho + J2^rho (k2-k3).J1 + J1^rho (k3-k1).J2
+template <typename T>
+__device__ __forceinline__ c4<T> vvv(const c4<T>& J1, const c4<T>& J2, const r4<T>& k1, const r4<T>& k2) {
+  r4<T> k3 = -(k1 + k2);
+  cx<T> j12 = cdot(J1, J2);
+  cx<T> a = rdot(k2 - k3, J1);
+  cx<T> b = rdot(k3 - k1, J2);
+  r4<T> d = k1 - k2;
+  c4<T> W;
+  W.v[0] = d.e * j12 + a * J2.v[0] + b * J1.v[0];
+  W.v[1] = d.x * j12 + a * J2.v[1] + b * J1.v[1];
+  W.v[2] = d.y * j12 + a * J2.v[2] + b * J1.v[2];
+  W.v[3] = d.z * j12 + a * J2.v[3] + b * J1.v[3];
+  return W;
+}
+// colour-ordered four-gluon structure: 2(L.R) M - (L.M) R - (M.R) L
+template <typename T>
+__device__ __forceinline__ c4<T> vvvv_ordered(const c4<T>& L, const c4<T>& M, const c4<T>& R) {
+  cx<T> lr = cdot(L, R), lm = cdot(L, M), mr = cdot(M, R);
+  cx<T> two_lr = lr + lr;
+  c4<T> o;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) o.v[i] = two_lr * M.v[i] - lm * R.v[i] - mr * L.v[i];
+  return o;
+}
+
+}  // namespace me

@@ -1,0 +1,290 @@
+// Per-process colour-decomposed helicity amplitudes (device).
+//
+// Each routine returns, for one helicity configuration, the partial amplitudes
+// J_c of the process in its colour-flow basis, so that the colour-summed squared
+// amplitude is J^dagger C J (Sec. 2.1, Eq. (born): |sum of diagrams|^2; Sec. 4.2:
+// Born, real and counterterms are all tree-level amplitudes).
+//
+//  * t tbar + n gluons (gg->tt, gg->ttg, gg->ttgg): colour-ordered Berends-Giele
+//    recursion.  Full amplitude M = sum_sigma (T^{a_s1} ... T^{a_sn})_{i_t j_tbar} A(sigma);
+//    colour-ordered rules derived from the Feynman rules with [T^a,T^b] = i f^abc T^c:
+//      gluon current  J(LR)  = -(g/Q^2) V3(J_L, J_R; -Q_L, -Q_R)
+//                     J(LMR) = +(g^2/Q^2) [2(J_L.J_R) J_M - (J_L.J_M) J_R - (J_M.J_R) J_L]
+//      quark line     U(s_1..s_k) = sum_j U(s_1..s_j) (i g Jslash(s_{j+1}..s_k)) i(Qslash+m)/(Q^2-m^2)
+//      amplitude      A(s) = sum_j U(s_1..s_j) (i g Jslash(s_{j+1}..s_n)) v(tbar).
+//  * e+e- -> u ubar (g): photon current from the leptons inserted on the quark line.
+//  * u ubar -> t tbar (g): explicit diagrams, colour by Fierz onto a 2- (4-) element basis.
+// Momenta: all-outgoing (q = -p for incoming legs), kept in double for the
+// propagator denominators; spinors and currents are in T.
+#pragma once
+#include "me_math.cuh"
+
+namespace me {
+
+enum ProcId : int {
+  P_EE_UU = 0,
+  P_EE_UUG = 1,
+  P_GG_TT = 2,
+  P_GG_TTG = 3,
+  P_GG_TTGG = 4,
+  P_UU_TT = 5,
+  P_UU_TTG = 6,
+  P_COUNT = 7
+};
+
+template <int PID> struct Proc;
+template <> struct Proc<P_EE_UU> { static constexpr int NEXT = 4, NHEL = 16, NFLOW = 1; };
+template <> struct Proc<P_EE_UUG> { static constexpr int NEXT = 5, NHEL = 32, NFLOW = 1; };
+template <> struct Proc<P_GG_TT> { static constexpr int NEXT = 4, NHEL = 16, NFLOW = 2, NG = 2; };
+template <> struct Proc<P_GG_TTG> { static constexpr int NEXT = 5, NHEL = 32, NFLOW = 6, NG = 3; };
+template <> struct Proc<P_GG_TTGG> { static constexpr int NEXT = 6, NHEL = 64, NFLOW = 24, NG = 4; };
+template <> struct Proc<P_UU_TT> { static constexpr int NEXT = 4, NHEL = 16, NFLOW = 2; };
+template <> struct Proc<P_UU_TTG> { static constexpr int NEXT = 5, NHEL = 32, NFLOW = 4; };
+
+struct Couplings {
+  double gs;   // strong coupling g_s
+  double ee;   // electromagnetic coupling e
+  double mt;   // top mass
+};
+
+__host__ __device__ constexpr int factorial(int n) { return n <= 1 ? 1 : n * factorial(n - 1); }
+
+// permutation number `idx` (lexicographic) of {0..n-1}
+__device__ __forceinline__ void nth_perm(int n, int idx, int* out) {
+  int pool[4] = {0, 1, 2, 3};
+  int m = n;
+  for (int i = 0; i < n; ++i) {
+    int f = factorial(m - 1);
+    int k = idx / f;
+    idx -= k * f;
+    out[i] = pool[k];
+    for (int j = k; j < m - 1; ++j) pool[j] = pool[j + 1];
+    --m;
+  }
+}
+
+__device__ __forceinline__ int hel_of(int hel, int leg) { return ((hel >> leg) & 1) ? 1 : -1; }
+
+// ----------------------------------------------------------------------------
+// t tbar + NG gluons.  Gluon legs: the two incoming legs 0,1 and outgoing legs 4,5..
+// Leg 2 = t (ubar), leg 3 = tbar (v).  `eps_override`: replace gluon leg `ov_leg`'s
+// polarisation by a given vector (spin-correlated Born), else nullptr.
+template <typename T, int NG>
+__device__ void amp_ttng(const r4<double>* p, int hel, const Couplings& cp, const c4<T>* eps_override,
+                         int ov_leg, cx<T>* A) {
+  constexpr int NF = factorial(NG);
+  const T g = (T)cp.gs;
+  const T mt = (T)cp.mt;
+  int gleg[NG];
+  gleg[0] = 0;
+  gleg[1] = 1;
+#pragma unroll
+  for (int i = 2; i < NG; ++i) gleg[i] = 2 + i;
+  c4<T> eps[NG];
+  r4<double> qg[NG];
+#pragma unroll
+  for (int i = 0; i < NG; ++i) {
+    int l = gleg[i];
+    bool in = l < 2;
+    qg[i] = in ? -p[l] : p[l];
+    if (eps_override != nullptr && l == ov_leg)
+      eps[i] = *eps_override;
+    else
+      eps[i] = polvec(cast4<T>(p[l]), hel_of(hel, l), !in);
+  }
+  const c4<T> ub = dbar(spinor_u(cast4<T>(p[2]), mt, hel_of(hel, 2)));
+  const c4<T> vb = spinor_v(cast4<T>(p[3]), mt, hel_of(hel, 3));
+  const r4<double> qt = p[2];
+  const double mt2 = cp.mt * cp.mt;
+
+  for (int f = 0; f < NF; ++f) {
+    int s[NG];
+    nth_perm(NG, f, s);
+    // contiguous gluon currents J[i][j] of the ordering, momenta Q[i][j]
+    c4<T> J[NG][NG];
+    r4<double> Q[NG][NG];
+#pragma unroll
+    for (int i = 0; i < NG; ++i) {
+      J[i][i] = eps[s[i]];
+      Q[i][i] = qg[s[i]];
+    }
+#pragma unroll
+    for (int len = 2; len <= NG; ++len) {
+#pragma unroll
+      for (int i = 0; i + len - 1 < NG; ++i) {
+        const int j = i + len - 1;
+        Q[i][j] = Q[i][j - 1] + qg[s[j]];
+        const double q2 = mdot(Q[i][j], Q[i][j]);
+        const T c3 = (T)(-1.0 / q2) * g;
+        c4<T> acc = czero<T>();
+#pragma unroll
+        for (int k = i; k < j; ++k) {
+          c4<T> w = vvv(J[i][k], J[k + 1][j], cast4<T>(-Q[i][k]), cast4<T>(-Q[k + 1][j]));
+          cadd(acc, w);
+        }
+        cscale(acc, c3);
+        if (len >= 3) {
+          const T c4g = (T)(1.0 / q2) * g * g;
+          c4<T> acc4 = czero<T>();
+#pragma unroll
+          for (int k = i; k < j - 1; ++k)
+#pragma unroll
+            for (int l = k + 1; l < j; ++l) cadd(acc4, vvvv_ordered(J[i][k], J[k + 1][l], J[l + 1][j]));
+          caxpy(acc, cx<T>{c4g, T(0)}, acc4);
+        }
+        J[i][j] = acc;
+      }
+    }
+    // quark line from the top side: U[k] = top with the first k gluons attached
+    c4<T> U[NG];
+    U[0] = ub;
+    r4<double> Qu = qt;
+#pragma unroll
+    for (int k = 1; k < NG; ++k) {
+      Qu = Qu + qg[s[k - 1]];
+      c4<T> acc = czero<T>();
+#pragma unroll
+      for (int j = 0; j < k; ++j) cadd(acc, row_slash(U[j], J[j][k - 1]));
+      const double den = mdot(Qu, Qu) - mt2;
+      // (i g)(i)/den = -g/den
+      c4<T> pr = row_prop(acc, cast4<T>(Qu), mt);
+      cscale(pr, (T)(-1.0 / den) * g);
+      U[k] = pr;
+    }
+    cx<T> a = cx<T>{T(0), T(0)};
+#pragma unroll
+    for (int j = 0; j < NG; ++j) a = a + spdot(row_slash(U[j], J[j][NG - 1]), vb);
+    A[f] = times_i(a) * g;
+  }
+}
+
+// ----------------------------------------------------------------------------
+// e+(0) e-(1) -> u(2) ubar(3) [g(4)].  Photon exchange; charges Q_e = -1, Q_u = 2/3.
+template <typename T>
+__device__ __forceinline__ c4<T> lepton_current(const r4<double>* p, int hel, const Couplings& cp) {
+  // vbar(e+) gamma^mu u(e-) with the photon propagator: (e Q_e / s) vbar gamma u
+  c4<T> vb = dbar(spinor_v(cast4<T>(p[0]), T(0), hel_of(hel, 0)));
+  c4<T> u = spinor_u(cast4<T>(p[1]), T(0), hel_of(hel, 1));
+  r4<double> Q = p[0] + p[1];
+  c4<T> L = vcurrent(vb, u);
+  cscale(L, (T)(-cp.ee / mdot(Q, Q)));
+  return L;
+}
+
+template <typename T>
+__device__ void amp_ee_uu(const r4<double>* p, int hel, const Couplings& cp, cx<T>* A) {
+  c4<T> L = lepton_current<T>(p, hel, cp);
+  c4<T> ub = dbar(spinor_u(cast4<T>(p[2]), T(0), hel_of(hel, 2)));
+  c4<T> v = spinor_v(cast4<T>(p[3]), T(0), hel_of(hel, 3));
+  const T equ = (T)(cp.ee * (2.0 / 3.0));
+  A[0] = times_i(spdot(row_slash(ub, L), v)) * equ;
+}
+
+template <typename T>
+__device__ void amp_ee_uug(const r4<double>* p, int hel, const Couplings& cp, cx<T>* A) {
+  c4<T> L = lepton_current<T>(p, hel, cp);
+  c4<T> ub = dbar(spinor_u(cast4<T>(p[2]), T(0), hel_of(hel, 2)));
+  c4<T> v = spinor_v(cast4<T>(p[3]), T(0), hel_of(hel, 3));
+  c4<T> eps = polvec(cast4<T>(p[4]), hel_of(hel, 4), true);
+  const T g = (T)cp.gs;
+  const T equ = (T)(cp.ee * (2.0 / 3.0));
+  // gluon on the quark side: ubar (i g eps) i(Q1slash)/Q1^2, Q1 = p_u + p_g
+  r4<double> Q1 = p[2] + p[4];
+  c4<T> u1 = row_prop(row_slash(ub, eps), cast4<T>(Q1), T(0));
+  cscale(u1, (T)(-1.0 / mdot(Q1, Q1)) * g);
+  // gluon on the antiquark side: i(-Q2slash)/Q2^2 (i g eps) v, Q2 = p_ubar + p_g
+  r4<double> Q2 = p[3] + p[4];
+  c4<T> v1 = col_prop(cast4<T>(Q2), T(0), slash_col(eps, v));
+  cscale(v1, (T)(-1.0 / mdot(Q2, Q2)) * g);
+  cx<T> a = spdot(row_slash(u1, L), v) + spdot(row_slash(ub, L), v1);
+  A[0] = times_i(a) * equ;
+}
+
+// ----------------------------------------------------------------------------
+// u(0) ubar(1) -> t(2) tbar(3) [g(4)].  Colour basis (i=t, j=tbar, k=u, l=ubar):
+//   Born: e1 = d_ik d_lj, e2 = d_ij d_lk;  (T^b)_ij (T^b)_lk = (e1 - e2/N)/2.
+//   Real: e1 = T^a_ik d_lj, e2 = d_ik T^a_lj, e3 = T^a_ij d_lk, e4 = d_ij T^a_lk.
+template <typename T>
+__device__ __forceinline__ c4<T> light_current(const c4<T>& vbar_ub, const c4<T>& u_u, const r4<double>& Q, T g) {
+  // (g/Q^2) vbar gamma u  (vertex i g gamma, propagator -i/Q^2)
+  c4<T> J = vcurrent(vbar_ub, u_u);
+  cscale(J, (T)(1.0 / mdot(Q, Q)) * g);
+  return J;
+}
+
+template <typename T>
+__device__ void amp_uu_tt(const r4<double>* p, int hel, const Couplings& cp, cx<T>* A) {
+  const T g = (T)cp.gs, mt = (T)cp.mt;
+  c4<T> uu = spinor_u(cast4<T>(p[0]), T(0), hel_of(hel, 0));
+  c4<T> vbu = dbar(spinor_v(cast4<T>(p[1]), T(0), hel_of(hel, 1)));
+  c4<T> ub = dbar(spinor_u(cast4<T>(p[2]), mt, hel_of(hel, 2)));
+  c4<T> vt = spinor_v(cast4<T>(p[3]), mt, hel_of(hel, 3));
+  c4<T> Ju = light_current(vbu, uu, p[0] + p[1], g);
+  cx<T> d = times_i(spdot(row_slash(ub, Ju), vt)) * g;
+  A[0] = d * T(0.5);
+  A[1] = d * (T)(-1.0 / 6.0);
+}
+
+template <typename T>
+__device__ void amp_uu_ttg(const r4<double>* p, int hel, const Couplings& cp, cx<T>* A) {
+  const T g = (T)cp.gs, mt = (T)cp.mt;
+  const double mt2 = cp.mt * cp.mt;
+  c4<T> uu = spinor_u(cast4<T>(p[0]), T(0), hel_of(hel, 0));
+  c4<T> vbu = dbar(spinor_v(cast4<T>(p[1]), T(0), hel_of(hel, 1)));
+  c4<T> ub = dbar(spinor_u(cast4<T>(p[2]), mt, hel_of(hel, 2)));
+  c4<T> vt = spinor_v(cast4<T>(p[3]), mt, hel_of(hel, 3));
+  c4<T> eps = polvec(cast4<T>(p[4]), hel_of(hel, 4), true);
+  // outgoing momenta
+  const r4<double> q0 = -p[0], q1 = -p[1], q2 = p[2], q3 = p[3], q4 = p[4];
+  // u-line current without emission: momentum q0+q1
+  c4<T> Ju = light_current(vbu, uu, q0 + q1, g);
+  // D1: gluon off the top: ubar (ig eps) S_F(q2+q4) (ig Ju) v
+  r4<double> Qa = q2 + q4;
+  c4<T> r1 = row_prop(row_slash(ub, eps), cast4<T>(Qa), mt);
+  cscale(r1, (T)(-1.0 / (mdot(Qa, Qa) - mt2)) * g);
+  cx<T> D1 = times_i(spdot(row_slash(r1, Ju), vt)) * g;
+  // D2: gluon off the antitop: ubar (ig Ju) S_F(-(q3+q4)) (ig eps) v
+  r4<double> Qb = q3 + q4;
+  c4<T> c1 = col_prop(cast4<T>(Qb), mt, slash_col(eps, vt));
+  cscale(c1, (T)(-1.0 / (mdot(Qb, Qb) - mt2)) * g);
+  cx<T> D2 = times_i(spdot(row_slash(ub, Ju), c1)) * g;
+  // D3: gluon off the incoming antiquark (row side of the light line)
+  r4<double> Qc = q1 + q4;
+  c4<T> r3 = row_prop(row_slash(vbu, eps), cast4<T>(Qc), T(0));
+  cscale(r3, (T)(-1.0 / mdot(Qc, Qc)) * g);
+  c4<T> J3 = light_current(r3, uu, q0 + q1 + q4, g);
+  cx<T> D3 = times_i(spdot(row_slash(ub, J3), vt)) * g;
+  // D4: gluon off the incoming quark (column side)
+  r4<double> Qd = q0 + q4;
+  c4<T> c4u = col_prop(cast4<T>(Qd), T(0), slash_col(eps, uu));
+  cscale(c4u, (T)(-1.0 / mdot(Qd, Qd)) * g);
+  c4<T> J4 = light_current(vbu, c4u, q0 + q1 + q4, g);
+  cx<T> D4 = times_i(spdot(row_slash(ub, J4), vt)) * g;
+  // D5: three-gluon vertex joining the light current, the heavy current and the gluon
+  c4<T> Jt = vcurrent(ub, vt);
+  r4<double> Qt = q2 + q3;
+  cscale(Jt, (T)(1.0 / mdot(Qt, Qt)) * g);
+  c4<T> W = vvv(Ju, Jt, cast4<T>(-(q0 + q1)), cast4<T>(-Qt));
+  cx<T> D5 = cdot(W, eps) * g;
+  const T h = T(0.5), hn = (T)(-1.0 / 6.0);
+  cx<T> iD5 = times_i(D5);
+  A[0] = (D1 + D4) * h - iD5 * h;
+  A[1] = (D2 + D3) * h + iD5 * h;
+  A[2] = (D1 + D2) * hn;
+  A[3] = (D3 + D4) * hn;
+}
+
+// ----------------------------------------------------------------------------
+template <int PID, typename T>
+__device__ __forceinline__ void amplitude(const r4<double>* p, int hel, const Couplings& cp, cx<T>* A,
+                                          const c4<T>* eps_override = nullptr, int ov_leg = -1) {
+  if constexpr (PID == P_EE_UU) amp_ee_uu<T>(p, hel, cp, A);
+  else if constexpr (PID == P_EE_UUG) amp_ee_uug<T>(p, hel, cp, A);
+  else if constexpr (PID == P_GG_TT) amp_ttng<T, 2>(p, hel, cp, eps_override, ov_leg, A);
+  else if constexpr (PID == P_GG_TTG) amp_ttng<T, 3>(p, hel, cp, eps_override, ov_leg, A);
+  else if constexpr (PID == P_GG_TTGG) amp_ttng<T, 4>(p, hel, cp, eps_override, ov_leg, A);
+  else if constexpr (PID == P_UU_TT) amp_uu_tt<T>(p, hel, cp, A);
+  else if constexpr (PID == P_UU_TTG) amp_uu_ttg<T>(p, hel, cp, A);
+}
+
+}  // namespace me

@@ -1,0 +1,314 @@
+// Request loop: continuous batching of phase-space batches from many integration
+// channels (multi-event interface of Sec. 4.4, kept on the device between requests as
+// argued in Sec. 4.3).  A scheduler thread admits queued requests into free slots
+// while the device-memory budget allows; each slot owns a CUDA stream, pinned staging
+// buffers and one handle per process, so admitted requests of any process overlap on
+// the GPU.  Completion is detected by polling CUDA events (never a device-side wait).
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/me.h"
+#include "me_internal.h"
+
+namespace {
+
+using clk = std::chrono::steady_clock;
+
+struct Req {
+  uint64_t ticket;
+  int pid;
+  std::string process;
+  int kind;
+  const double* p;
+  const double* w;
+  int64_t n;
+  double* out;
+  int n_ext;
+  size_t bytes;
+  clk::time_point t_submit, t_admit;
+  me_result res;
+  bool done = false;
+};
+
+struct Slot {
+  cudaStream_t st = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  double *d_p = nullptr, *d_w = nullptr, *d_out = nullptr;
+  double *h_p = nullptr, *h_w = nullptr, *h_out = nullptr;
+  int* h_resc = nullptr;
+  size_t cap = 0;   // points
+  int cap_ext = 6;  // legs the buffers are sized for
+  me_handle* handles[16] = {};
+  Req* cur = nullptr;
+};
+
+}  // namespace
+
+struct me_server {
+  me_server_params prm;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<Req*> pending;
+  std::unordered_map<uint64_t, Req*> reqs;
+  std::vector<Slot> slots;
+  std::thread worker;
+  bool stop = false;
+  int64_t mem_in_use = 0;
+  uint64_t next_ticket = 1;
+};
+
+static int sfail(int code, const std::string& m) { return me_internal_fail(code, m.c_str()); }
+
+static int slot_reserve(Slot& s, int64_t n, int n_ext) {
+  if ((size_t)n <= s.cap && n_ext <= s.cap_ext) return ME_OK;
+  size_t c = std::max<size_t>((size_t)n, 4096);
+  cudaFree(s.d_p);
+  cudaFree(s.d_w);
+  cudaFree(s.d_out);
+  cudaFreeHost(s.h_p);
+  cudaFreeHost(s.h_w);
+  cudaFreeHost(s.h_out);
+  s.d_p = s.d_w = s.d_out = s.h_p = s.h_w = s.h_out = nullptr;
+  s.cap = 0;
+  const size_t pb = c * 4 * (size_t)s.cap_ext * sizeof(double);
+  if (cudaMalloc(&s.d_p, pb) != cudaSuccess || cudaMalloc(&s.d_w, c * 8) != cudaSuccess ||
+      cudaMalloc(&s.d_out, c * 8) != cudaSuccess || cudaMallocHost(&s.h_p, pb) != cudaSuccess ||
+      cudaMallocHost(&s.h_w, c * 8) != cudaSuccess || cudaMallocHost(&s.h_out, c * 8) != cudaSuccess)
+    return ME_ERR_OOM;
+  s.cap = c;
+  return ME_OK;
+}
+
+// launch one admitted request on its slot (called by the worker without the lock)
+static int start(me_server* sv, Slot& s, Req* r) {
+  cudaSetDevice(sv->prm.device);
+  int rc = slot_reserve(s, r->n, r->n_ext);
+  if (rc != ME_OK) return rc;
+  me_handle*& h = s.handles[r->pid];
+  if (!h) {
+    me_params p = sv->prm.params;
+    p.device = sv->prm.device;
+    if ((rc = me_init(r->process.c_str(), &p, &h)) != ME_OK) return rc;
+    if ((rc = me_set_stream(h, s.st)) != ME_OK) return rc;
+  }
+  const size_t pb = (size_t)r->n * 4 * r->n_ext * sizeof(double);
+  std::memcpy(s.h_p, r->p, pb);
+  if (r->w) std::memcpy(s.h_w, r->w, (size_t)r->n * 8);
+  cudaEventRecord(s.e0, s.st);
+  cudaMemcpyAsync(s.d_p, s.h_p, pb, cudaMemcpyHostToDevice, s.st);
+  if (r->w) cudaMemcpyAsync(s.d_w, s.h_w, (size_t)r->n * 8, cudaMemcpyHostToDevice, s.st);
+  const double* dw = r->w ? s.d_w : nullptr;
+  if (r->kind == ME_KIND_BORN) rc = me_eval_born(h, s.d_p, dw, r->n, s.d_out);
+  else if (r->kind == ME_KIND_REAL_SUBTRACTED) rc = me_eval_real_subtracted(h, s.d_p, dw, r->n, s.d_out);
+  else rc = me_eval_nbody_nlo(h, s.d_p, dw, r->n, s.d_out);
+  if (rc != ME_OK) return rc;
+  me_internal_rescued_async(h, s.h_resc);
+  cudaMemcpyAsync(s.h_out, s.d_out, (size_t)r->n * 8, cudaMemcpyDeviceToHost, s.st);
+  cudaEventRecord(s.e1, s.st);
+  if (cudaGetLastError() != cudaSuccess) return ME_ERR_CUDA;
+  return ME_OK;
+}
+
+static void finish(Req* r, Slot& s, int status) {
+  r->res.status = status;
+  r->res.n = r->n;
+  double a = 0, b = 0;
+  if (status == ME_OK) {
+    std::memcpy(r->out, s.h_out, (size_t)r->n * 8);
+    for (int64_t i = 0; i < r->n; ++i) {
+      a += r->out[i];
+      b += r->out[i] * r->out[i];
+    }
+    float ms = 0;
+    cudaEventElapsedTime(&ms, s.e0, s.e1);
+    r->res.t_device_us = 1e3 * ms;
+    r->res.n_rescued = *s.h_resc;
+  }
+  r->res.sum_w = a;
+  r->res.sum_w2 = b;
+  auto now = clk::now();
+  r->res.t_queue_us = std::chrono::duration<double, std::micro>(r->t_admit - r->t_submit).count();
+  r->res.t_total_us = std::chrono::duration<double, std::micro>(now - r->t_submit).count();
+}
+
+static void worker_loop(me_server* sv) {
+  cudaSetDevice(sv->prm.device);
+  std::unique_lock<std::mutex> lk(sv->mu);
+  while (!sv->stop) {
+    bool progress = false;
+    // completions
+    for (auto& s : sv->slots) {
+      if (!s.cur) continue;
+      cudaError_t q = cudaEventQuery(s.e1);
+      if (q == cudaErrorNotReady) continue;
+      Req* r = s.cur;
+      s.cur = nullptr;
+      finish(r, s, q == cudaSuccess ? ME_OK : ME_ERR_CUDA);
+      sv->mem_in_use -= (int64_t)r->bytes;
+      r->done = true;
+      progress = true;
+    }
+    if (progress) sv->cv_done.notify_all();
+    // admissions: FIFO while a slot and memory are free
+    while (!sv->pending.empty()) {
+      Req* r = sv->pending.front();
+      Slot* free_slot = nullptr;
+      for (auto& s : sv->slots)
+        if (!s.cur) {
+          free_slot = &s;
+          break;
+        }
+      if (!free_slot) break;
+      if (sv->mem_in_use + (int64_t)r->bytes > sv->prm.mem_budget_bytes && sv->mem_in_use > 0) break;
+      sv->pending.pop_front();
+      r->t_admit = clk::now();
+      sv->mem_in_use += (int64_t)r->bytes;
+      free_slot->cur = r;
+      lk.unlock();
+      int rc = start(sv, *free_slot, r);
+      lk.lock();
+      if (rc != ME_OK) {
+        free_slot->cur = nullptr;
+        finish(r, *free_slot, rc);
+        sv->mem_in_use -= (int64_t)r->bytes;
+        r->done = true;
+        sv->cv_done.notify_all();
+      }
+      progress = true;
+    }
+    if (!progress) {
+      bool busy = false;
+      for (auto& s : sv->slots) busy |= s.cur != nullptr;
+      // bounded host-side wait: short when work is in flight, longer when idle
+      sv->cv_work.wait_for(lk, busy ? std::chrono::microseconds(20) : std::chrono::milliseconds(5));
+    }
+  }
+}
+
+extern "C" {
+
+void me_default_server_params(me_server_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->version = ME_PARAMS_VERSION;
+  p->device = 0;
+  p->n_slots = 4;
+  p->max_queue = 4096;
+  p->mem_budget_bytes = (int64_t)8 << 30;
+  me_default_params(&p->params);
+  p->params.precision = ME_PREC_MIXED;
+}
+
+int me_server_create(const me_server_params* prm, me_server** out) {
+  if (!prm || !out) return sfail(ME_ERR_ARG, "me_server_create: NULL argument");
+  *out = nullptr;
+  if (prm->version != ME_PARAMS_VERSION || prm->n_slots < 1 || prm->n_slots > 64 || prm->max_queue < 1 ||
+      prm->mem_budget_bytes <= 0)
+    return sfail(ME_ERR_ARG, "me_server_create: bad parameters");
+  if (cudaSetDevice(prm->device) != cudaSuccess) return sfail(ME_ERR_CUDA, "me_server_create: bad device");
+  me_server* sv = new me_server();
+  sv->prm = *prm;
+  sv->slots.resize(prm->n_slots);
+  for (auto& s : sv->slots) {
+    if (cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&s.e0) != cudaSuccess || cudaEventCreate(&s.e1) != cudaSuccess ||
+        cudaMallocHost(&s.h_resc, sizeof(int)) != cudaSuccess) {
+      me_server_destroy(sv);
+      return sfail(ME_ERR_CUDA, "me_server_create: stream/event allocation failed");
+    }
+    *s.h_resc = 0;
+  }
+  sv->worker = std::thread(worker_loop, sv);
+  *out = sv;
+  return ME_OK;
+}
+
+int me_submit(me_server* sv, const me_request* rq, me_ticket* out) {
+  if (!sv || !rq || !out || !rq->process || !rq->momenta || !rq->out || rq->n < 0)
+    return sfail(ME_ERR_ARG, "me_submit: bad request");
+  const int pid = me_internal_process_id(rq->process);
+  if (pid < 0) return sfail(ME_ERR_PROCESS, std::string("me_submit: unknown process ") + rq->process);
+  if (rq->kind < ME_KIND_BORN || rq->kind > ME_KIND_NBODY_NLO) return sfail(ME_ERR_ARG, "me_submit: bad kind");
+  static const int next_of[] = {4, 5, 4, 5, 6, 4, 5};
+  Req* r = new Req();
+  r->pid = pid;
+  r->process = rq->process;
+  r->kind = rq->kind;
+  r->p = rq->momenta;
+  r->w = rq->ps_weights;
+  r->n = rq->n;
+  r->out = rq->out;
+  r->n_ext = next_of[pid];
+  r->bytes = (size_t)rq->n * (4 * r->n_ext + 2) * sizeof(double);
+  r->t_submit = clk::now();
+  std::memset(&r->res, 0, sizeof(r->res));
+  std::lock_guard<std::mutex> lk(sv->mu);
+  if ((int64_t)r->bytes > sv->prm.mem_budget_bytes) {
+    delete r;
+    return sfail(ME_ERR_BUSY, "me_submit: request larger than the memory budget");
+  }
+  if ((int)sv->pending.size() >= sv->prm.max_queue) {
+    delete r;
+    return sfail(ME_ERR_BUSY, "me_submit: queue full");
+  }
+  r->ticket = sv->next_ticket++;
+  sv->reqs[r->ticket] = r;
+  sv->pending.push_back(r);
+  *out = r->ticket;
+  sv->cv_work.notify_one();
+  return ME_OK;
+}
+
+int me_poll(me_server* sv, me_ticket t, me_result* out, int64_t timeout_us) {
+  if (!sv || !out) return sfail(ME_ERR_ARG, "me_poll: NULL argument");
+  std::unique_lock<std::mutex> lk(sv->mu);
+  auto it = sv->reqs.find(t);
+  if (it == sv->reqs.end()) return sfail(ME_ERR_ARG, "me_poll: unknown ticket");
+  Req* r = it->second;
+  auto ready = [&] { return r->done; };
+  if (timeout_us < 0) sv->cv_done.wait(lk, ready);
+  else if (!sv->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), ready))
+    return sfail(ME_ERR_TIMEOUT, "me_poll: not finished within the timeout");
+  *out = r->res;
+  sv->reqs.erase(it);
+  delete r;
+  return ME_OK;
+}
+
+void me_server_destroy(me_server* sv) {
+  if (!sv) return;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->stop = true;
+  }
+  sv->cv_work.notify_all();
+  if (sv->worker.joinable()) sv->worker.join();
+  cudaSetDevice(sv->prm.device);
+  for (auto& s : sv->slots) {
+    if (s.st) cudaStreamSynchronize(s.st);
+    for (auto* h : s.handles) me_destroy(h);
+    cudaFree(s.d_p);
+    cudaFree(s.d_w);
+    cudaFree(s.d_out);
+    cudaFreeHost(s.h_p);
+    cudaFreeHost(s.h_w);
+    cudaFreeHost(s.h_out);
+    cudaFreeHost(s.h_resc);
+    if (s.e0) cudaEventDestroy(s.e0);
+    if (s.e1) cudaEventDestroy(s.e1);
+    if (s.st) cudaStreamDestroy(s.st);
+  }
+  for (auto& kv : sv->reqs) delete kv.second;
+  delete sv;
+}
+
+}  // extern "C"
