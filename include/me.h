@@ -140,6 +140,14 @@ int me_last_rescued(me_handle* h, int64_t* n_rescued);
 int me_get_accumulators(me_handle* h, double out[3]);
 int me_set_accumulators(me_handle* h, const double in[3]);
 
+/* Stage timers (profiling, off by default).  When enabled, every evaluation records
+ * CUDA events on the handle's stream around its main kernel, its float64 rescue
+ * kernel and its weight reduction (at most 4096 calls are kept).  me_stage_times
+ * synchronises, returns the summed durations in milliseconds (out_ms[0] main kernel,
+ * [1] rescue, [2] reduction) and the number of timed calls, and clears them. */
+int me_enable_stage_timers(me_handle* h, int on);
+int me_stage_times(me_handle* h, double out_ms[3], int64_t* calls);
+
 /* Use an existing cudaStream_t (passed as void*) for the handle's work; NULL selects
  * the handle's own stream.  The caller keeps the stream alive while it is in use. */
 int me_set_stream(me_handle* h, void* cuda_stream);

@@ -81,6 +81,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "me_get_accumulators": (ctypes.c_int, [vp, dp]),
         "me_set_accumulators": (ctypes.c_int, [vp, dp]),
         "me_set_stream": (ctypes.c_int, [vp, vp]),
+        "me_enable_stage_timers": (ctypes.c_int, [vp, ctypes.c_int]),
+        "me_stage_times": (ctypes.c_int, [vp, dp, ctypes.POINTER(i64)]),
         "me_synchronize": (ctypes.c_int, [vp]),
         "me_destroy": (None, [vp]),
         "me_last_error": (ctypes.c_char_p, []),
@@ -151,6 +153,9 @@ class Handle:
         self.h = h
         self.process = process
         self.n_ext = self.lib.me_n_external(self.h)
+        # with device buffers the library returns once the work is enqueued on its
+        # stream; unless the caller hands in its own stream, wait for it here
+        self.sync = True
 
     def _call(self, fn, p, w, out):
         n = p.shape[-1]
@@ -166,6 +171,8 @@ class Handle:
         wp, kw = _ptr(w)
         op, ko = _ptr(out)
         _check(fn(self.h, pp, wp, n, op))
+        if self.sync:
+            _check(self.lib.me_synchronize(self.h))
         if isinstance(out, np.ndarray) and ko is not out:
             out[...] = ko
         return out
@@ -193,8 +200,21 @@ class Handle:
         a = (ctypes.c_double * 3)(*vals)
         _check(self.lib.me_set_accumulators(self.h, a))
 
+    def enable_stage_timers(self, on: bool = True):
+        _check(self.lib.me_enable_stage_timers(self.h, 1 if on else 0))
+
+    def stage_times(self):
+        """(main kernel ms, rescue ms, reduction ms, calls) summed since the last read."""
+        t = (ctypes.c_double * 3)()
+        c = ctypes.c_int64()
+        _check(self.lib.me_stage_times(self.h, t, ctypes.byref(c)))
+        return t[0], t[1], t[2], c.value
+
     def set_stream(self, stream_ptr: int | None):
+        """Run on the caller's CUDA stream (e.g. torch.cuda.Stream().cuda_stream); calls
+        then return without waiting and the caller orders work on that stream."""
         _check(self.lib.me_set_stream(self.h, stream_ptr))
+        self.sync = stream_ptr is None
 
     def synchronize(self):
         _check(self.lib.me_synchronize(self.h))

@@ -15,6 +15,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(os.path.dirname(PKG), "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libme_gb300.so")
+FLOPS_TOOL = os.path.join(BUILD, "me_flops")
 SOURCES = ["me_core.cu", "me_serve.cu", "me_inst_ee.cu", "me_inst_gg.cu", "me_inst_ggg.cu",
            "me_inst_uu.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -66,7 +67,21 @@ def build(verbose: bool = False, extra_flags=()) -> str:
         if verbose:
             print(" ".join(cmd), flush=True)
         subprocess.run(cmd, check=True)
+    src = os.path.join(CSRC, "me_flops.cu")
+    if not os.path.exists(FLOPS_TOOL) or os.path.getmtime(FLOPS_TOOL) < max(os.path.getmtime(src), newest_header):
+        r = subprocess.run([nvcc, "-O1", "-std=c++17", "-diag-suppress", "20014", "-x", "cu", src, "-o", FLOPS_TOOL],
+                           capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("op-count tool failed to build:\n" + r.stdout + r.stderr)
     return LIB
+
+
+def op_counts() -> dict:
+    """Algorithmic operation counts per helicity / event (see csrc/me_flops.cu)."""
+    import json
+    if not os.path.exists(FLOPS_TOOL):
+        build()
+    return json.loads(subprocess.run([FLOPS_TOOL], check=True, capture_output=True, text=True).stdout)
 
 
 if __name__ == "__main__":

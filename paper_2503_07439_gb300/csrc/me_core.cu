@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <cmath>
 #include <complex>
@@ -376,6 +377,11 @@ struct me_handle {
   double* d_acc = nullptr;   // accumulators (3)
   int lpe[2][2] = {{0, 0}, {0, 0}};  // [kind][fp64] chosen lanes per event
   int last_kind = K_TREE;
+  // stage timers: per timed call, events before the main kernel, after it, after the
+  // rescue kernel and after the reduction
+  bool timers = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::array<cudaEvent_t, 4>> ev_used;
 };
 
 static int ensure_capacity(me_handle* h, size_t n) {
@@ -578,7 +584,23 @@ static int run(me_handle* h, int kind, double nlo_factor, const double* momenta,
   // both are chosen before the launches whose results are kept
   const int lpe64 = (kind == K_REAL && mixed) ? choose_lpe(h, kind, true, a) : 0;
   const int lpe = choose_lpe(h, kind, !mixed, a);
+  std::array<cudaEvent_t, 4> ev{};
+  const bool timed = h->timers && h->ev_used.size() < 4096;
+  if (timed) {
+    for (auto& e : ev) {
+      if (h->ev_pool.empty()) {
+        cudaEvent_t x;
+        ME_CUDA(cudaEventCreate(&x));
+        h->ev_pool.push_back(x);
+      }
+      e = h->ev_pool.back();
+      h->ev_pool.pop_back();
+    }
+    h->ev_used.push_back(ev);
+    ME_CUDA(cudaEventRecord(ev[0], h->stream));
+  }
   ME_CUDA(dispatch(h->proc->pid, kind, !mixed, lpe, a, h->stream));
+  if (timed) ME_CUDA(cudaEventRecord(ev[1], h->stream));
   if (kind == K_REAL && mixed) {
     // FP64 re-evaluation of the flagged points (count read on the device)
     LaunchArgs r = a;
@@ -587,9 +609,11 @@ static int run(me_handle* h, int kind, double nlo_factor, const double* momenta,
     r.count = h->d_nresc;
     ME_CUDA(dispatch(h->proc->pid, kind, true, lpe64, r, h->stream));
   }
+  if (timed) ME_CUDA(cudaEventRecord(ev[2], h->stream));
   k_partials<<<RED_BLOCKS, 256, 0, h->stream>>>(O, n, h->d_part);
   k_finish<<<1, 32, 0, h->stream>>>(h->d_part, RED_BLOCKS, h->d_acc, n);
   ME_CUDA(cudaGetLastError());
+  if (timed) ME_CUDA(cudaEventRecord(ev[3], h->stream));
   if (!dout) ME_CUDA(cudaMemcpyAsync(out, O, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   if (staged) ME_CUDA(cudaStreamSynchronize(h->stream));
   return ME_OK;
@@ -641,6 +665,31 @@ int me_set_accumulators(me_handle* h, const double in[3]) {
   return ME_OK;
 }
 
+int me_enable_stage_timers(me_handle* h, int on) {
+  if (!h) return fail(ME_ERR_ARG, "NULL handle");
+  h->timers = on != 0;
+  return ME_OK;
+}
+
+int me_stage_times(me_handle* h, double out_ms[3], int64_t* calls) {
+  if (!h || !out_ms || !calls) return fail(ME_ERR_ARG, "NULL argument");
+  ME_CUDA(cudaSetDevice(h->device));
+  ME_CUDA(cudaStreamSynchronize(h->stream));
+  double t[3] = {0, 0, 0};
+  for (auto& ev : h->ev_used) {
+    for (int k = 0; k < 3; ++k) {
+      float ms = 0;
+      ME_CUDA(cudaEventElapsedTime(&ms, ev[k], ev[k + 1]));
+      t[k] += ms;
+    }
+    for (auto e : ev) h->ev_pool.push_back(e);
+  }
+  *calls = (int64_t)h->ev_used.size();
+  h->ev_used.clear();
+  for (int k = 0; k < 3; ++k) out_ms[k] = t[k];
+  return ME_OK;
+}
+
 int me_set_stream(me_handle* h, void* s) {
   if (!h) return fail(ME_ERR_ARG, "NULL handle");
   h->stream = s ? (cudaStream_t)s : h->own_stream;
@@ -665,6 +714,9 @@ void me_destroy(me_handle* h) {
   cudaFree(h->d_nresc);
   cudaFree(h->d_part);
   cudaFree(h->d_acc);
+  for (auto& ev : h->ev_used)
+    for (auto e : ev) cudaEventDestroy(e);
+  for (auto e : h->ev_pool) cudaEventDestroy(e);
   if (h->own_stream) cudaStreamDestroy(h->own_stream);
   delete h;
 }

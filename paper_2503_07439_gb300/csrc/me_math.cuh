@@ -13,6 +13,12 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+// Amplitude arithmetic compiles for the device and, for operation counting with a
+// counting scalar type, for the host.
+#ifndef ME_HD
+#define ME_HD __host__ __device__ __forceinline__
+#endif
+
 namespace me {
 
 template <typename T>
@@ -20,18 +26,18 @@ struct cx {
   T re, im;
 };
 
-template <typename T> __device__ __forceinline__ cx<T> mk(T r, T i) { return cx<T>{r, i}; }
-template <typename T> __device__ __forceinline__ cx<T> operator+(cx<T> a, cx<T> b) { return {a.re + b.re, a.im + b.im}; }
-template <typename T> __device__ __forceinline__ cx<T> operator-(cx<T> a, cx<T> b) { return {a.re - b.re, a.im - b.im}; }
-template <typename T> __device__ __forceinline__ cx<T> operator-(cx<T> a) { return {-a.re, -a.im}; }
-template <typename T> __device__ __forceinline__ cx<T> operator*(cx<T> a, cx<T> b) {
+template <typename T> ME_HD cx<T> mk(T r, T i) { return cx<T>{r, i}; }
+template <typename T> ME_HD cx<T> operator+(cx<T> a, cx<T> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename T> ME_HD cx<T> operator-(cx<T> a, cx<T> b) { return {a.re - b.re, a.im - b.im}; }
+template <typename T> ME_HD cx<T> operator-(cx<T> a) { return {-a.re, -a.im}; }
+template <typename T> ME_HD cx<T> operator*(cx<T> a, cx<T> b) {
   return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
 }
-template <typename T> __device__ __forceinline__ cx<T> operator*(T s, cx<T> a) { return {s * a.re, s * a.im}; }
-template <typename T> __device__ __forceinline__ cx<T> operator*(cx<T> a, T s) { return {s * a.re, s * a.im}; }
-template <typename T> __device__ __forceinline__ cx<T> conj(cx<T> a) { return {a.re, -a.im}; }
-template <typename T> __device__ __forceinline__ cx<T> times_i(cx<T> a) { return {-a.im, a.re}; }
-template <typename T> __device__ __forceinline__ T norm2(cx<T> a) { return a.re * a.re + a.im * a.im; }
+template <typename T> ME_HD cx<T> operator*(T s, cx<T> a) { return {s * a.re, s * a.im}; }
+template <typename T> ME_HD cx<T> operator*(cx<T> a, T s) { return {s * a.re, s * a.im}; }
+template <typename T> ME_HD cx<T> conj(cx<T> a) { return {a.re, -a.im}; }
+template <typename T> ME_HD cx<T> times_i(cx<T> a) { return {-a.im, a.re}; }
+template <typename T> ME_HD T norm2(cx<T> a) { return a.re * a.re + a.im * a.im; }
 
 // complex four-component object: a Lorentz vector with upper index, or a Dirac spinor
 template <typename T>
@@ -44,45 +50,45 @@ struct r4 {  // real four-vector (E, px, py, pz)
   T e, x, y, z;
 };
 
-template <typename T> __device__ __forceinline__ r4<T> operator+(r4<T> a, r4<T> b) { return {a.e + b.e, a.x + b.x, a.y + b.y, a.z + b.z}; }
-template <typename T> __device__ __forceinline__ r4<T> operator-(r4<T> a, r4<T> b) { return {a.e - b.e, a.x - b.x, a.y - b.y, a.z - b.z}; }
-template <typename T> __device__ __forceinline__ r4<T> operator-(r4<T> a) { return {-a.e, -a.x, -a.y, -a.z}; }
-template <typename T> __device__ __forceinline__ r4<T> scale(T s, r4<T> a) { return {s * a.e, s * a.x, s * a.y, s * a.z}; }
-template <typename T> __device__ __forceinline__ T mdot(r4<T> a, r4<T> b) { return a.e * b.e - a.x * b.x - a.y * b.y - a.z * b.z; }
-template <typename U, typename T> __device__ __forceinline__ r4<U> cast4(r4<T> a) { return {(U)a.e, (U)a.x, (U)a.y, (U)a.z}; }
+template <typename T> ME_HD r4<T> operator+(r4<T> a, r4<T> b) { return {a.e + b.e, a.x + b.x, a.y + b.y, a.z + b.z}; }
+template <typename T> ME_HD r4<T> operator-(r4<T> a, r4<T> b) { return {a.e - b.e, a.x - b.x, a.y - b.y, a.z - b.z}; }
+template <typename T> ME_HD r4<T> operator-(r4<T> a) { return {-a.e, -a.x, -a.y, -a.z}; }
+template <typename T> ME_HD r4<T> scale(T s, r4<T> a) { return {s * a.e, s * a.x, s * a.y, s * a.z}; }
+template <typename T> ME_HD T mdot(r4<T> a, r4<T> b) { return a.e * b.e - a.x * b.x - a.y * b.y - a.z * b.z; }
+template <typename U, typename T> ME_HD r4<U> cast4(r4<T> a) { return {(U)a.e, (U)a.x, (U)a.y, (U)a.z}; }
 
 // complex-vector . complex-vector (Minkowski, no conjugation)
 template <typename T>
-__device__ __forceinline__ cx<T> cdot(const c4<T>& a, const c4<T>& b) {
+ME_HD cx<T> cdot(const c4<T>& a, const c4<T>& b) {
   return a.v[0] * b.v[0] - a.v[1] * b.v[1] - a.v[2] * b.v[2] - a.v[3] * b.v[3];
 }
 // real-vector . complex-vector
 template <typename T>
-__device__ __forceinline__ cx<T> rdot(const r4<T>& a, const c4<T>& b) {
+ME_HD cx<T> rdot(const r4<T>& a, const c4<T>& b) {
   return a.e * b.v[0] - a.x * b.v[1] - a.y * b.v[2] - a.z * b.v[3];
 }
 template <typename T>
-__device__ __forceinline__ void cadd(c4<T>& acc, const c4<T>& x) {
+ME_HD void cadd(c4<T>& acc, const c4<T>& x) {
 #pragma unroll
   for (int i = 0; i < 4; ++i) acc.v[i] = acc.v[i] + x.v[i];
 }
 template <typename T>
-__device__ __forceinline__ void caxpy(c4<T>& acc, cx<T> a, const c4<T>& x) {
+ME_HD void caxpy(c4<T>& acc, cx<T> a, const c4<T>& x) {
 #pragma unroll
   for (int i = 0; i < 4; ++i) acc.v[i] = acc.v[i] + a * x.v[i];
 }
 template <typename T>
-__device__ __forceinline__ void cscale(c4<T>& x, cx<T> a) {
+ME_HD void cscale(c4<T>& x, cx<T> a) {
 #pragma unroll
   for (int i = 0; i < 4; ++i) x.v[i] = a * x.v[i];
 }
 template <typename T>
-__device__ __forceinline__ void cscale(c4<T>& x, T a) {
+ME_HD void cscale(c4<T>& x, T a) {
 #pragma unroll
   for (int i = 0; i < 4; ++i) x.v[i] = a * x.v[i];
 }
 template <typename T>
-__device__ __forceinline__ c4<T> czero() {
+ME_HD c4<T> czero() {
   c4<T> z;
 #pragma unroll
   for (int i = 0; i < 4; ++i) z.v[i] = cx<T>{T(0), T(0)};
@@ -93,7 +99,7 @@ __device__ __forceinline__ c4<T> czero() {
 // two-component helicity eigenstate chi_lam along p/|p|; |p|+pz is formed without
 // cancellation as pt^2/(|p|-pz) when pz < 0.
 template <typename T>
-__device__ __forceinline__ void chi(const r4<T>& p, int lam, cx<T>& c0, cx<T>& c1) {
+ME_HD void chi(const r4<T>& p, int lam, cx<T>& c0, cx<T>& c1) {
   T pt2 = p.x * p.x + p.y * p.y;
   T pa = sqrt(pt2 + p.z * p.z);
   T s = (p.z >= T(0)) ? pa + p.z : pt2 / (pa - p.z);
@@ -118,14 +124,14 @@ __device__ __forceinline__ void chi(const r4<T>& p, int lam, cx<T>& c0, cx<T>& c
 }
 
 template <typename T>
-__device__ __forceinline__ void omegas(const r4<T>& p, T m, T& wp, T& wm) {
+ME_HD void omegas(const r4<T>& p, T m, T& wp, T& wm) {
   T pa = sqrt(p.x * p.x + p.y * p.y + p.z * p.z);
   wp = sqrt(p.e + pa);
   wm = (m == T(0)) ? T(0) : m / wp;
 }
 
 template <typename T>
-__device__ __forceinline__ c4<T> spinor_u(const r4<T>& p, T m, int lam) {
+ME_HD c4<T> spinor_u(const r4<T>& p, T m, int lam) {
   T wp, wm;
   omegas(p, m, wp, wm);
   cx<T> a, b;
@@ -135,7 +141,7 @@ __device__ __forceinline__ c4<T> spinor_u(const r4<T>& p, T m, int lam) {
 }
 
 template <typename T>
-__device__ __forceinline__ c4<T> spinor_v(const r4<T>& p, T m, int lam) {
+ME_HD c4<T> spinor_v(const r4<T>& p, T m, int lam) {
   T wp, wm;
   omegas(p, m, wp, wm);
   cx<T> a, b;
@@ -147,12 +153,12 @@ __device__ __forceinline__ c4<T> spinor_v(const r4<T>& p, T m, int lam) {
 
 // Dirac adjoint psi^dagger gamma^0 (chiral rep: swap blocks, conjugate)
 template <typename T>
-__device__ __forceinline__ c4<T> dbar(const c4<T>& s) {
+ME_HD c4<T> dbar(const c4<T>& s) {
   return c4<T>{{conj(s.v[2]), conj(s.v[3]), conj(s.v[0]), conj(s.v[1])}};
 }
 
 template <typename T>
-__device__ __forceinline__ c4<T> polvec(const r4<T>& k, int lam, bool outgoing) {
+ME_HD c4<T> polvec(const r4<T>& k, int lam, bool outgoing) {
   T pt2 = k.x * k.x + k.y * k.y;
   T pt = sqrt(pt2);
   T ka = sqrt(pt2 + k.z * k.z);
@@ -180,7 +186,7 @@ __device__ __forceinline__ c4<T> polvec(const r4<T>& k, int lam, bool outgoing) 
 // ---------------------------------------------------------------- Dirac algebra
 // row spinor times Vslash (V complex, upper index)
 template <typename T>
-__device__ __forceinline__ c4<T> row_slash(const c4<T>& r, const c4<T>& V) {
+ME_HD c4<T> row_slash(const c4<T>& r, const c4<T>& V) {
   cx<T> a = V.v[0] - V.v[3], b = V.v[0] + V.v[3];
   cx<T> c = V.v[1] - times_i(V.v[2]);  // V1 - i V2
   cx<T> d = V.v[1] + times_i(V.v[2]);  // V1 + i V2
@@ -193,7 +199,7 @@ __device__ __forceinline__ c4<T> row_slash(const c4<T>& r, const c4<T>& V) {
 }
 // Vslash times column spinor
 template <typename T>
-__device__ __forceinline__ c4<T> slash_col(const c4<T>& V, const c4<T>& s) {
+ME_HD c4<T> slash_col(const c4<T>& V, const c4<T>& s) {
   cx<T> a = V.v[0] - V.v[3], b = V.v[0] + V.v[3];
   cx<T> c = V.v[1] - times_i(V.v[2]);
   cx<T> d = V.v[1] + times_i(V.v[2]);
@@ -206,7 +212,7 @@ __device__ __forceinline__ c4<T> slash_col(const c4<T>& V, const c4<T>& s) {
 }
 // row spinor times (Qslash + m), Q real
 template <typename T>
-__device__ __forceinline__ c4<T> row_prop(const c4<T>& r, const r4<T>& Q, T m) {
+ME_HD c4<T> row_prop(const c4<T>& r, const r4<T>& Q, T m) {
   T a = Q.e - Q.z, b = Q.e + Q.z;
   cx<T> c = cx<T>{Q.x, -Q.y}, d = cx<T>{Q.x, Q.y};
   c4<T> o;
@@ -218,7 +224,7 @@ __device__ __forceinline__ c4<T> row_prop(const c4<T>& r, const r4<T>& Q, T m) {
 }
 // (-Qslash + m) times column spinor, Q real
 template <typename T>
-__device__ __forceinline__ c4<T> col_prop(const r4<T>& Q, T m, const c4<T>& s) {
+ME_HD c4<T> col_prop(const r4<T>& Q, T m, const c4<T>& s) {
   T a = Q.e - Q.z, b = Q.e + Q.z;
   cx<T> c = cx<T>{Q.x, -Q.y}, d = cx<T>{Q.x, Q.y};
   c4<T> o;
@@ -230,7 +236,7 @@ __device__ __forceinline__ c4<T> col_prop(const r4<T>& Q, T m, const c4<T>& s) {
 }
 // vector current J^mu = r gamma^mu s
 template <typename T>
-__device__ __forceinline__ c4<T> vcurrent(const c4<T>& r, const c4<T>& s) {
+ME_HD c4<T> vcurrent(const c4<T>& r, const c4<T>& s) {
   c4<T> J;
   J.v[0] = r.v[0] * s.v[2] + r.v[1] * s.v[3] + r.v[2] * s.v[0] + r.v[3] * s.v[1];
   J.v[1] = (r.v[0] * s.v[3] + r.v[1] * s.v[2]) - (r.v[2] * s.v[1] + r.v[3] * s.v[0]);
@@ -239,7 +245,7 @@ __device__ __forceinline__ c4<T> vcurrent(const c4<T>& r, const c4<T>& s) {
   return J;
 }
 template <typename T>
-__device__ __forceinline__ cx<T> spdot(const c4<T>& r, const c4<T>& s) {
+ME_HD cx<T> spdot(const c4<T>& r, const c4<T>& s) {
   return r.v[0] * s.v[0] + r.v[1] * s.v[1] + r.v[2] * s.v[2] + r.v[3] * s.v[3];
 }
 
@@ -247,7 +253,7 @@ __device__ __forceinline__ cx<T> spdot(const c4<T>& r, const c4<T>& s) {
 // three-gluon Lorentz structure contracted with J1_mu J2_nu, momenta k1,k2,k3 incoming:
 // W^rho = (J1.J2)(k1-k2)^rho + J2^rho (k2-k3).J1 + J1^rho (k3-k1).J2
 template <typename T>
-__device__ __forceinline__ c4<T> vvv(const c4<T>& J1, const c4<T>& J2, const r4<T>& k1, const r4<T>& k2) {
+ME_HD c4<T> vvv(const c4<T>& J1, const c4<T>& J2, const r4<T>& k1, const r4<T>& k2) {
   r4<T> k3 = -(k1 + k2);
   cx<T> j12 = cdot(J1, J2);
   cx<T> a = rdot(k2 - k3, J1);
@@ -262,7 +268,7 @@ __device__ __forceinline__ c4<T> vvv(const c4<T>& J1, const c4<T>& J2, const r4<
 }
 // colour-ordered four-gluon structure: 2(L.R) M - (L.M) R - (M.R) L
 template <typename T>
-__device__ __forceinline__ c4<T> vvvv_ordered(const c4<T>& L, const c4<T>& M, const c4<T>& R) {
+ME_HD c4<T> vvvv_ordered(const c4<T>& L, const c4<T>& M, const c4<T>& R) {
   cx<T> lr = cdot(L, R), lm = cdot(L, M), mr = cdot(M, R);
   cx<T> two_lr = lr + lr;
   c4<T> o;

@@ -50,7 +50,7 @@ struct Couplings {
 __host__ __device__ constexpr int factorial(int n) { return n <= 1 ? 1 : n * factorial(n - 1); }
 
 // permutation number `idx` (lexicographic) of {0..n-1}
-__device__ __forceinline__ void nth_perm(int n, int idx, int* out) {
+ME_HD void nth_perm(int n, int idx, int* out) {
   int pool[4] = {0, 1, 2, 3};
   int m = n;
   for (int i = 0; i < n; ++i) {
@@ -63,14 +63,14 @@ __device__ __forceinline__ void nth_perm(int n, int idx, int* out) {
   }
 }
 
-__device__ __forceinline__ int hel_of(int hel, int leg) { return ((hel >> leg) & 1) ? 1 : -1; }
+ME_HD int hel_of(int hel, int leg) { return ((hel >> leg) & 1) ? 1 : -1; }
 
 // ----------------------------------------------------------------------------
 // t tbar + NG gluons.  Gluon legs: the two incoming legs 0,1 and outgoing legs 4,5..
 // Leg 2 = t (ubar), leg 3 = tbar (v).  `eps_override`: replace gluon leg `ov_leg`'s
 // polarisation by a given vector (spin-correlated Born), else nullptr.
 template <typename T, int NG>
-__device__ void amp_ttng(const r4<double>* p, int hel, const Couplings& cp, const c4<T>* eps_override,
+ME_HD void amp_ttng(const r4<double>* p, int hel, const Couplings& cp, const c4<T>* eps_override,
                          int ov_leg, cx<T>* A) {
   constexpr int NF = factorial(NG);
   const T g = (T)cp.gs;
@@ -161,7 +161,7 @@ __device__ void amp_ttng(const r4<double>* p, int hel, const Couplings& cp, cons
 // ----------------------------------------------------------------------------
 // e+(0) e-(1) -> u(2) ubar(3) [g(4)].  Photon exchange; charges Q_e = -1, Q_u = 2/3.
 template <typename T>
-__device__ __forceinline__ c4<T> lepton_current(const r4<double>* p, int hel, const Couplings& cp) {
+ME_HD c4<T> lepton_current(const r4<double>* p, int hel, const Couplings& cp) {
   // vbar(e+) gamma^mu u(e-) with the photon propagator: (e Q_e / s) vbar gamma u
   c4<T> vb = dbar(spinor_v(cast4<T>(p[0]), T(0), hel_of(hel, 0)));
   c4<T> u = spinor_u(cast4<T>(p[1]), T(0), hel_of(hel, 1));
@@ -172,7 +172,7 @@ __device__ __forceinline__ c4<T> lepton_current(const r4<double>* p, int hel, co
 }
 
 template <typename T>
-__device__ void amp_ee_uu(const r4<double>* p, int hel, const Couplings& cp, cx<T>* A) {
+ME_HD void amp_ee_uu(const r4<double>* p, int hel, const Couplings& cp, cx<T>* A) {
   c4<T> L = lepton_current<T>(p, hel, cp);
   c4<T> ub = dbar(spinor_u(cast4<T>(p[2]), T(0), hel_of(hel, 2)));
   c4<T> v = spinor_v(cast4<T>(p[3]), T(0), hel_of(hel, 3));
@@ -181,7 +181,7 @@ __device__ void amp_ee_uu(const r4<double>* p, int hel, const Couplings& cp, cx<
 }
 
 template <typename T>
-__device__ void amp_ee_uug(const r4<double>* p, int hel, const Couplings& cp, cx<T>* A) {
+ME_HD void amp_ee_uug(const r4<double>* p, int hel, const Couplings& cp, cx<T>* A) {
   c4<T> L = lepton_current<T>(p, hel, cp);
   c4<T> ub = dbar(spinor_u(cast4<T>(p[2]), T(0), hel_of(hel, 2)));
   c4<T> v = spinor_v(cast4<T>(p[3]), T(0), hel_of(hel, 3));
@@ -205,7 +205,7 @@ __device__ void amp_ee_uug(const r4<double>* p, int hel, const Couplings& cp, cx
 //   Born: e1 = d_ik d_lj, e2 = d_ij d_lk;  (T^b)_ij (T^b)_lk = (e1 - e2/N)/2.
 //   Real: e1 = T^a_ik d_lj, e2 = d_ik T^a_lj, e3 = T^a_ij d_lk, e4 = d_ij T^a_lk.
 template <typename T>
-__device__ __forceinline__ c4<T> light_current(const c4<T>& vbar_ub, const c4<T>& u_u, const r4<double>& Q, T g) {
+ME_HD c4<T> light_current(const c4<T>& vbar_ub, const c4<T>& u_u, const r4<double>& Q, T g) {
   // (g/Q^2) vbar gamma u  (vertex i g gamma, propagator -i/Q^2)
   c4<T> J = vcurrent(vbar_ub, u_u);
   cscale(J, (T)(1.0 / mdot(Q, Q)) * g);
@@ -213,7 +213,7 @@ __device__ __forceinline__ c4<T> light_current(const c4<T>& vbar_ub, const c4<T>
 }
 
 template <typename T>
-__device__ void amp_uu_tt(const r4<double>* p, int hel, const Couplings& cp, cx<T>* A) {
+ME_HD void amp_uu_tt(const r4<double>* p, int hel, const Couplings& cp, cx<T>* A) {
   const T g = (T)cp.gs, mt = (T)cp.mt;
   c4<T> uu = spinor_u(cast4<T>(p[0]), T(0), hel_of(hel, 0));
   c4<T> vbu = dbar(spinor_v(cast4<T>(p[1]), T(0), hel_of(hel, 1)));
@@ -226,7 +226,7 @@ __device__ void amp_uu_tt(const r4<double>* p, int hel, const Couplings& cp, cx<
 }
 
 template <typename T>
-__device__ void amp_uu_ttg(const r4<double>* p, int hel, const Couplings& cp, cx<T>* A) {
+ME_HD void amp_uu_ttg(const r4<double>* p, int hel, const Couplings& cp, cx<T>* A) {
   const T g = (T)cp.gs, mt = (T)cp.mt;
   const double mt2 = cp.mt * cp.mt;
   c4<T> uu = spinor_u(cast4<T>(p[0]), T(0), hel_of(hel, 0));
@@ -276,7 +276,7 @@ __device__ void amp_uu_ttg(const r4<double>* p, int hel, const Couplings& cp, cx
 
 // ----------------------------------------------------------------------------
 template <int PID, typename T>
-__device__ __forceinline__ void amplitude(const r4<double>* p, int hel, const Couplings& cp, cx<T>* A,
+ME_HD void amplitude(const r4<double>* p, int hel, const Couplings& cp, cx<T>* A,
                                           const c4<T>* eps_override = nullptr, int ov_leg = -1) {
   if constexpr (PID == P_EE_UU) amp_ee_uu<T>(p, hel, cp, A);
   else if constexpr (PID == P_EE_UUG) amp_ee_uug<T>(p, hel, cp, A);
