@@ -58,9 +58,11 @@ extern "C" {
  *   xi_thr, y_thr    mixed mode: points with xi < xi_thr or 1-y < y_thr in an active
  *                    counterterm region are re-evaluated in float64
  *   tol, me_eps      mixed mode: a point is re-evaluated in float64 when
- *                    (|R S| + |CT|) * me_eps > tol/8 * |R S - CT|
+ *                    (|R S| + |CT|) * me_eps > tol * |R S - CT|; me_eps is the
+ *                    measured float32 error per unit of (|R S| + |CT|) (99.9th
+ *                    percentile on flat points of the three real processes)
  *   device           CUDA device ordinal the handle runs on
- *   lanes_per_event  lanes sharing one point (4, 8, 16 or 32; 0 = autotune)
+ *   lanes_per_event  lanes sharing one point (1, 2, 4, 8 or 16; 0 = autotune)
  */
 typedef struct me_params {
   uint32_t version;
@@ -81,7 +83,7 @@ typedef struct me_params {
 typedef struct me_handle me_handle;
 
 /* Fill `p` with the defaults: FP64, alpha = 1/132.507, alpha_s = 0.118, mt = 173,
- * xi_cut = 0.5, delta = 1, xi_thr = 1e-3, y_thr = 1e-3, tol = 1e-5, me_eps = 3e-6,
+ * xi_cut = 0.5, delta = 1, xi_thr = 1e-3, y_thr = 1e-3, tol = 1e-5, me_eps = 8e-7,
  * device 0, lanes_per_event 0.  Never fails. */
 void me_default_params(me_params* p);
 

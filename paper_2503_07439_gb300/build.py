@@ -36,6 +36,7 @@ def _headers():
 
 
 def build(verbose: bool = False, extra_flags=()) -> str:
+    extra_flags = tuple(extra_flags) + tuple(os.environ.get("ME_NVCC_FLAGS", "").split())
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
     newest_header = max(os.path.getmtime(h) for h in _headers())

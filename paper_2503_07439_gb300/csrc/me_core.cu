@@ -430,7 +430,7 @@ static int choose_lpe(me_handle* h, int kind, bool fp64, const LaunchArgs& a) {
   int& slot = h->lpe[kind][fp64 ? 1 : 0];
   if (h->prm.lanes_per_event) return slot = h->prm.lanes_per_event;
   if (slot) return slot;
-  const int cands[4] = {4, 8, 16, 32};
+  const int cands[5] = {1, 2, 4, 8, 16};
   LaunchArgs t = a;
   t.groups = std::min<long>(a.groups, 1L << 15);
   t.kp.flag_unstable = 0;
@@ -473,7 +473,7 @@ void me_default_params(me_params* p) {
   p->xi_thr = 1e-3;
   p->y_thr = 1e-3;
   p->tol = 1e-5;
-  p->me_eps = 3e-6;
+  p->me_eps = 8e-7;
   p->device = 0;
   p->lanes_per_event = 0;
 }
@@ -490,7 +490,7 @@ int me_init(const char* process, const me_params* params, me_handle** out) {
       !(params->alpha_s > 0) || !(params->alpha > 0) || !(params->mt > 0))
     return fail(ME_ERR_ARG, "me_init: parameter out of range");
   const int l = params->lanes_per_event;
-  if (l != 0 && l != 4 && l != 8 && l != 16 && l != 32) return fail(ME_ERR_ARG, "me_init: lanes_per_event");
+  if (l != 0 && l != 1 && l != 2 && l != 4 && l != 8 && l != 16) return fail(ME_ERR_ARG, "me_init: lanes_per_event");
   const ProcDesc* pd = nullptr;
   for (const auto& d : kProcs)
     if (std::strcmp(d.name, process) == 0) pd = &d;

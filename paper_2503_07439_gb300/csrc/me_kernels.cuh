@@ -9,6 +9,11 @@
 #pragma once
 #include "me_procs.cuh"
 
+// minimum resident 128-thread blocks per SM requested from the register allocator
+#ifndef ME_MINB
+#define ME_MINB 3
+#endif
+
 namespace me {
 
 constexpr int MAX_FLOW = 24;
@@ -97,7 +102,7 @@ __device__ __forceinline__ void load_event(const double* __restrict__ p, long n,
 // out[i] = wgt[i] * |M|^2(p_i) * nlo_factor.  `idx` (optional): event list to process
 // (the FP64 rescue of flagged points); `count` then holds its length on the device.
 template <int PID, typename T, int LPE>
-__global__ void __launch_bounds__(128) k_tree(const double* __restrict__ p, const double* __restrict__ wgt, long n,
+__global__ void __launch_bounds__(128, ME_MINB) k_tree(const double* __restrict__ p, const double* __restrict__ wgt, long n,
                                               double* __restrict__ out, KParams kp, const int* __restrict__ idx,
                                               const int* __restrict__ count) {
   constexpr int NEXT = Proc<PID>::NEXT, NHEL = Proc<PID>::NHEL, NF = Proc<PID>::NFLOW;
@@ -242,7 +247,7 @@ __device__ __forceinline__ double eik(const r4<double>& a, const r4<double>& b, 
 // out[i] = wgt[i] * sum over FKS sectors of the subtracted real (ME units), see
 // the FKS formula: W_j = R S_j - [Th_s G(0,y) + Th_c G(xi,1) - Th_s Th_c G(0,1)] / (xi^2 (1-y) K).
 template <int PID, typename T, int LPE>
-__global__ void __launch_bounds__(128) k_real_sub(const double* __restrict__ p, const double* __restrict__ wgt,
+__global__ void __launch_bounds__(128, ME_MINB) k_real_sub(const double* __restrict__ p, const double* __restrict__ wgt,
                                                   long n, double* __restrict__ out, KParams kp,
                                                   const int* __restrict__ idx, const int* __restrict__ count,
                                                   int* __restrict__ resc_list, int* __restrict__ resc_count) {
@@ -379,8 +384,8 @@ __global__ void __launch_bounds__(128) k_real_sub(const double* __restrict__ p, 
     const double w = wgt ? wgt[ev] : 1.0;
     out[ev] = w * W;
     if (kp.flag_unstable) {
-      // cancellation test: |R S| + |CT| relative to |W|, times the bulk-precision error
-      const bool unstable = near || !(mag * kp.me_eps <= 0.125 * kp.tol * fabs(W));
+      // cancellation test: the bulk-precision error of W is ~ me_eps (|R S| + |CT|)
+      const bool unstable = near || !(mag * kp.me_eps <= kp.tol * fabs(W));
       if (unstable) {
         const int slot = atomicAdd(resc_count, 1);
         resc_list[slot] = (int)ev;
@@ -428,7 +433,7 @@ cudaError_t launch_one(int kind, const LaunchArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// per-process launchers (one translation unit each); lpe in {4, 8, 16, 32}
+// per-process launchers (one translation unit each); lpe in {1, 2, 4, 8, 16}
 cudaError_t launch_ee(int pid, int kind, bool fp64, int lpe, const LaunchArgs& a, cudaStream_t st);
 cudaError_t launch_gg(int pid, int kind, bool fp64, int lpe, const LaunchArgs& a, cudaStream_t st);
 cudaError_t launch_ggg(int pid, int kind, bool fp64, int lpe, const LaunchArgs& a, cudaStream_t st);
@@ -438,10 +443,11 @@ cudaError_t launch_uu(int pid, int kind, bool fp64, int lpe, const LaunchArgs& a
 
 #define ME_LPE_SWITCH(PID, T)                                            \
   switch (lpe) {                                                         \
+    case 1: return me::launch_one<PID, T, 1>(kind, a, st);               \
+    case 2: return me::launch_one<PID, T, 2>(kind, a, st);               \
     case 4: return me::launch_one<PID, T, 4>(kind, a, st);               \
     case 8: return me::launch_one<PID, T, 8>(kind, a, st);               \
     case 16: return me::launch_one<PID, T, 16>(kind, a, st);             \
-    case 32: return me::launch_one<PID, T, 32>(kind, a, st);             \
     default: return cudaErrorInvalidValue;                               \
   }
 #define ME_PREC_SWITCH(PID)                      \

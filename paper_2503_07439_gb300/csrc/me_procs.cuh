@@ -159,6 +159,158 @@ ME_HD void amp_ttng(const r4<double>* p, int hel, const Couplings& cp, const c4<
 }
 
 // ----------------------------------------------------------------------------
+// t tbar + 2 or 3 gluons with every sub-current computed once per helicity.
+// Colour-ordered currents obey the reflection identity J(s reversed) = (-1)^(k+1) J(s)
+// for k gluons (V3 is antisymmetric in its two legs, the ordered V4 symmetric in its
+// outer legs), so J(yx) = -J(xy) and J(zyx) = J(xyz); the quark currents U(x), U(xy)
+// and the amplitudes of all orderings then reuse them.  Orderings are numbered
+// lexicographically as in amp_ttng, so the colour basis is the same.
+template <typename T>
+ME_HD void amp_tt2_fast(const r4<double>* p, int hel, const Couplings& cp, const c4<T>* ov, int ov_leg, cx<T>* A) {
+  const T g = (T)cp.gs, mt = (T)cp.mt;
+  const double m2 = cp.mt * cp.mt;
+  const r4<double> Q0 = -p[0], Q1 = -p[1], Pt = p[2];
+  // inverse propagator denominators from float64 momentum sums
+  const T i01 = (T)(1.0 / mdot(Q0 + Q1, Q0 + Q1));
+  const T u0 = (T)(1.0 / (mdot(Pt + Q0, Pt + Q0) - m2));
+  const T u1 = (T)(1.0 / (mdot(Pt + Q1, Pt + Q1) - m2));
+  const r4<T> k0 = cast4<T>(Q0), k1 = cast4<T>(Q1), kt = cast4<T>(Pt);
+  const c4<T> e0 = (ov != nullptr && ov_leg == 0) ? *ov : polvec(cast4<T>(p[0]), hel_of(hel, 0), false);
+  const c4<T> e1 = (ov != nullptr && ov_leg == 1) ? *ov : polvec(cast4<T>(p[1]), hel_of(hel, 1), false);
+  const c4<T> ub = dbar(spinor_u(kt, mt, hel_of(hel, 2)));
+  const c4<T> vb = spinor_v(cast4<T>(p[3]), mt, hel_of(hel, 3));
+  c4<T> J01 = vvv(e0, e1, -k0, -k1);
+  cscale(J01, -g * i01);
+  const cx<T> s01 = spdot(row_slash(ub, J01), vb);
+  c4<T> U0 = row_prop(row_slash(ub, e0), kt + k0, mt);
+  cscale(U0, -g * u0);
+  c4<T> U1 = row_prop(row_slash(ub, e1), kt + k1, mt);
+  cscale(U1, -g * u1);
+  // A(01) = ig[ub J01 v + U0 e1 v],  A(10) = ig[-ub J01 v + U1 e0 v]
+  A[0] = times_i(s01 + spdot(row_slash(U0, e1), vb)) * g;
+  A[1] = times_i(spdot(row_slash(U1, e0), vb) - s01) * g;
+}
+
+template <typename T>
+ME_HD void amp_tt3_fast(const r4<double>* p, int hel, const Couplings& cp, cx<T>* A) {
+  const T g = (T)cp.gs, mt = (T)cp.mt;
+  const double m2 = cp.mt * cp.mt;
+  const r4<double> Q0 = -p[0], Q1 = -p[1], Q2 = p[4], Pt = p[2];
+  const T i01 = (T)(1.0 / mdot(Q0 + Q1, Q0 + Q1));
+  const T i02 = (T)(1.0 / mdot(Q0 + Q2, Q0 + Q2));
+  const T i12 = (T)(1.0 / mdot(Q1 + Q2, Q1 + Q2));
+  const r4<double> Qa = Q0 + Q1 + Q2;
+  const T i012 = (T)(1.0 / mdot(Qa, Qa));
+  const T u0 = (T)(1.0 / (mdot(Pt + Q0, Pt + Q0) - m2));
+  const T u1 = (T)(1.0 / (mdot(Pt + Q1, Pt + Q1) - m2));
+  const T u2 = (T)(1.0 / (mdot(Pt + Q2, Pt + Q2) - m2));
+  const T u01 = (T)(1.0 / (mdot(Pt + Q0 + Q1, Pt + Q0 + Q1) - m2));
+  const T u02 = (T)(1.0 / (mdot(Pt + Q0 + Q2, Pt + Q0 + Q2) - m2));
+  const T u12 = (T)(1.0 / (mdot(Pt + Q1 + Q2, Pt + Q1 + Q2) - m2));
+  const r4<T> k0 = cast4<T>(Q0), k1 = cast4<T>(Q1), k2 = cast4<T>(Q2), kt = cast4<T>(Pt);
+  const c4<T> e0 = polvec(cast4<T>(p[0]), hel_of(hel, 0), false);
+  const c4<T> e1 = polvec(cast4<T>(p[1]), hel_of(hel, 1), false);
+  const c4<T> e2 = polvec(k2, hel_of(hel, 4), true);
+  const c4<T> ub = dbar(spinor_u(kt, mt, hel_of(hel, 2)));
+  const c4<T> vb = spinor_v(cast4<T>(p[3]), mt, hel_of(hel, 3));
+  // pair currents J(xy), x<y; J(yx) = -J(xy)
+  c4<T> J01 = vvv(e0, e1, -k0, -k1);
+  cscale(J01, -g * i01);
+  c4<T> J02 = vvv(e0, e2, -k0, -k2);
+  cscale(J02, -g * i02);
+  c4<T> J12 = vvv(e1, e2, -k1, -k2);
+  cscale(J12, -g * i12);
+  // three-gluon currents F(abc) = F(cba): -(g/Q^2)[V3(a, bc) + V3(ab, c)] + (g^2/Q^2) V4(a,b,c)
+  const T c3 = -g * i012, c4g = g * g * i012;
+  cx<T> a[6];
+  {
+    c4<T> F = vvv(e0, J12, -k0, -(k1 + k2));
+    cadd(F, vvv(J01, e2, -(k0 + k1), -k2));
+    cscale(F, c3);
+    caxpy(F, cx<T>{c4g, T(0)}, vvvv_ordered(e0, e1, e2));
+    a[0] = a[5] = spdot(row_slash(ub, F), vb);  // 012, 210
+  }
+  {
+    c4<T> mJ12 = J12;
+    cscale(mJ12, T(-1));
+    c4<T> F = vvv(e0, mJ12, -k0, -(k1 + k2));
+    cadd(F, vvv(J02, e1, -(k0 + k2), -k1));
+    cscale(F, c3);
+    caxpy(F, cx<T>{c4g, T(0)}, vvvv_ordered(e0, e2, e1));
+    a[1] = a[3] = spdot(row_slash(ub, F), vb);  // 021, 120
+  }
+  {
+    c4<T> mJ01 = J01;
+    cscale(mJ01, T(-1));
+    c4<T> F = vvv(e1, J02, -k1, -(k0 + k2));
+    cadd(F, vvv(mJ01, e2, -(k0 + k1), -k2));
+    cscale(F, c3);
+    caxpy(F, cx<T>{c4g, T(0)}, vvvv_ordered(e1, e0, e2));
+    a[2] = a[4] = spdot(row_slash(ub, F), vb);  // 102, 201
+  }
+  // orderings grouped by the gluon next to the top: U(x), then U(x y) = U(x) e_y + ubar J(xy)
+  {  // x = 0: orderings 012 (a0), 021 (a1)
+    c4<T> U = row_prop(row_slash(ub, e0), kt + k0, mt);
+    cscale(U, -g * u0);
+    const cx<T> t = spdot(row_slash(U, J12), vb);
+    a[0] = a[0] + t;
+    a[1] = a[1] - t;
+    c4<T> r = row_slash(U, e1);
+    cadd(r, row_slash(ub, J01));
+    c4<T> W = row_prop(r, kt + k0 + k1, mt);
+    cscale(W, -g * u01);
+    a[0] = a[0] + spdot(row_slash(W, e2), vb);
+    r = row_slash(U, e2);
+    cadd(r, row_slash(ub, J02));
+    W = row_prop(r, kt + k0 + k2, mt);
+    cscale(W, -g * u02);
+    a[1] = a[1] + spdot(row_slash(W, e1), vb);
+  }
+  {  // x = 1: orderings 102 (a2), 120 (a3)
+    c4<T> U = row_prop(row_slash(ub, e1), kt + k1, mt);
+    cscale(U, -g * u1);
+    const cx<T> t = spdot(row_slash(U, J02), vb);
+    a[2] = a[2] + t;
+    a[3] = a[3] - t;
+    c4<T> r = row_slash(U, e0);
+    c4<T> b = row_slash(ub, J01);
+    cscale(b, T(-1));
+    cadd(r, b);
+    c4<T> W = row_prop(r, kt + k0 + k1, mt);
+    cscale(W, -g * u01);
+    a[2] = a[2] + spdot(row_slash(W, e2), vb);
+    r = row_slash(U, e2);
+    cadd(r, row_slash(ub, J12));
+    W = row_prop(r, kt + k1 + k2, mt);
+    cscale(W, -g * u12);
+    a[3] = a[3] + spdot(row_slash(W, e0), vb);
+  }
+  {  // x = 2: orderings 201 (a4), 210 (a5)
+    c4<T> U = row_prop(row_slash(ub, e2), kt + k2, mt);
+    cscale(U, -g * u2);
+    const cx<T> t = spdot(row_slash(U, J01), vb);
+    a[4] = a[4] + t;
+    a[5] = a[5] - t;
+    c4<T> r = row_slash(U, e0);
+    c4<T> b = row_slash(ub, J02);
+    cscale(b, T(-1));
+    cadd(r, b);
+    c4<T> W = row_prop(r, kt + k0 + k2, mt);
+    cscale(W, -g * u02);
+    a[4] = a[4] + spdot(row_slash(W, e1), vb);
+    r = row_slash(U, e1);
+    b = row_slash(ub, J12);
+    cscale(b, T(-1));
+    cadd(r, b);
+    W = row_prop(r, kt + k1 + k2, mt);
+    cscale(W, -g * u12);
+    a[5] = a[5] + spdot(row_slash(W, e0), vb);
+  }
+#pragma unroll
+  for (int f = 0; f < 6; ++f) A[f] = times_i(a[f]) * g;
+}
+
+// ----------------------------------------------------------------------------
 // e+(0) e-(1) -> u(2) ubar(3) [g(4)].  Photon exchange; charges Q_e = -1, Q_u = 2/3.
 template <typename T>
 ME_HD c4<T> lepton_current(const r4<double>* p, int hel, const Couplings& cp) {
@@ -280,8 +432,8 @@ ME_HD void amplitude(const r4<double>* p, int hel, const Couplings& cp, cx<T>* A
                                           const c4<T>* eps_override = nullptr, int ov_leg = -1) {
   if constexpr (PID == P_EE_UU) amp_ee_uu<T>(p, hel, cp, A);
   else if constexpr (PID == P_EE_UUG) amp_ee_uug<T>(p, hel, cp, A);
-  else if constexpr (PID == P_GG_TT) amp_ttng<T, 2>(p, hel, cp, eps_override, ov_leg, A);
-  else if constexpr (PID == P_GG_TTG) amp_ttng<T, 3>(p, hel, cp, eps_override, ov_leg, A);
+  else if constexpr (PID == P_GG_TT) amp_tt2_fast<T>(p, hel, cp, eps_override, ov_leg, A);
+  else if constexpr (PID == P_GG_TTG) amp_tt3_fast<T>(p, hel, cp, A);
   else if constexpr (PID == P_GG_TTGG) amp_ttng<T, 4>(p, hel, cp, eps_override, ov_leg, A);
   else if constexpr (PID == P_UU_TT) amp_uu_tt<T>(p, hel, cp, A);
   else if constexpr (PID == P_UU_TTG) amp_uu_ttg<T>(p, hel, cp, A);
