@@ -220,6 +220,35 @@ int me_poll(me_server* s, me_ticket t, me_result* out, int64_t timeout_us);
 /* Stop the scheduler, wait for in-flight work, free everything.  NULL is a no-op. */
 void me_server_destroy(me_server* s);
 
+/* ---------------------------------------------------------------- allocation-free variant
+ * The paper has no counterpart to this entry point.  It serves callers that cannot
+ * allocate GPU memory: code whose device memory belongs entirely to another allocator
+ * (for example a host application's caching pool), code that must not trigger the
+ * device-wide synchronisation that cudaMalloc and cudaFree imply, and code running
+ * where allocation is not permitted.
+ *
+ * Same weights as me_eval_real_subtracted ("ee_uug", "gg_ttg", "uu_ttg"), without a
+ * handle and without any allocation (no cudaMalloc, cudaFree or other allocating call).
+ * Its only scratch is a built-in device array -- the mixed-precision rescue list and
+ * its counter, (ME_NOALLOC_MAX_POINTS + 64) int32 = 4 MiB -- that every GPU loading the
+ * library holds until the process exits; the process tables live in a second built-in
+ * device object.
+ *  - momenta, ps_weights (optional) and out must be device memory of params->device;
+ *    n larger than ME_NOALLOC_MAX_POINTS is rejected with ME_ERR_ARG.
+ *  - the work is enqueued on `cuda_stream` (NULL: the legacy default stream) and the call
+ *    returns without waiting; results are ready when that stream reaches this point.
+ *  - the first call on a device sets the device up (looks up the built-in arrays'
+ *    device addresses and uploads the process tables, synchronously); make that first
+ *    call before any stream capture.
+ *  - all calls share the built-in scratch, which keeps the last call's contents; each
+ *    call clears the rescue counter on its stream before use.  Calls whose work overlaps
+ *    on the GPU (other streams, other threads) race on the scratch: serialise them.
+ *  - lanes_per_event 0 selects 4 (no autotuning); the accumulators are not touched.
+ */
+#define ME_NOALLOC_MAX_POINTS 1048576
+int me_eval_real_subtracted_noalloc(const char* process, const me_params* params, const double* momenta,
+                                    const double* ps_weights, int64_t n, double* out, void* cuda_stream);
+
 /* Message of the last failed call on this thread ("" if none).  Valid until the next
  * call on the same thread. */
 const char* me_last_error(void);

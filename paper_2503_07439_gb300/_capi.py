@@ -91,6 +91,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "me_submit": (ctypes.c_int, [vp, ctypes.POINTER(MERequest), ctypes.POINTER(ctypes.c_uint64)]),
         "me_poll": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.POINTER(MEResult), i64]),
         "me_server_destroy": (None, [vp]),
+        "me_eval_real_subtracted_noalloc": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(MEParams), vp, vp, i64,
+                                                           vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

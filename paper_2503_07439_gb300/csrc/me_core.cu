@@ -735,6 +735,40 @@ int me_internal_rescued_async(me_handle* h, int* dst) {
 
 int me_internal_fail(int code, const char* msg) { return fail(code, msg ? msg : ""); }
 
+int me_internal_build_tables(me::ColourTables* tab) {
+  if (!tab) return fail(ME_ERR_ARG, "NULL table");
+  return build_tables(*tab);
+}
+
+int me_internal_kparams(const char* process, const me_params* params, me::KParams* kp, int* pid) {
+  if (!process || !params || !kp || !pid) return fail(ME_ERR_ARG, "NULL argument");
+  if (params->version != ME_PARAMS_VERSION) return fail(ME_ERR_ARG, "params version mismatch");
+  if (params->precision != ME_PREC_FP64 && params->precision != ME_PREC_MIXED)
+    return fail(ME_ERR_ARG, "precision must be ME_PREC_FP64 or ME_PREC_MIXED");
+  if (!(params->xi_cut > 0 && params->xi_cut <= 1) || !(params->delta > 0 && params->delta <= 2) ||
+      !(params->alpha_s > 0) || !(params->alpha > 0) || !(params->mt > 0))
+    return fail(ME_ERR_ARG, "parameter out of range");
+  const ProcDesc* pd = nullptr;
+  for (const auto& d : kProcs)
+    if (std::strcmp(d.name, process) == 0) pd = &d;
+  if (!pd) return fail(ME_ERR_PROCESS, std::string("unknown process ") + process);
+  std::memset(kp, 0, sizeof(*kp));
+  kp->cp.gs = std::sqrt(4.0 * M_PI * params->alpha_s);
+  kp->cp.ee = std::sqrt(4.0 * M_PI * params->alpha);
+  kp->cp.mt = params->mt;
+  kp->avg_inv = 1.0 / pd->avg;
+  kp->born_avg_inv = pd->born_pid >= 0 ? 1.0 / kProcs[pd->born_pid].avg : 0.0;
+  kp->nlo_factor = 1.0;
+  kp->xi_cut = params->xi_cut;
+  kp->delta = params->delta;
+  kp->xi_thr = params->xi_thr;
+  kp->y_thr = params->y_thr;
+  kp->me_eps = params->me_eps;
+  kp->tol = params->tol;
+  *pid = pd->pid;
+  return ME_OK;
+}
+
 int me_internal_process_id(const char* name) {
   if (!name) return -1;
   for (const auto& d : kProcs)
