@@ -27,7 +27,7 @@ inline Flop& operator+=(Flop& a, Flop b) { ++g_ops; a.v += b.v; return a; }
 inline bool operator>(Flop a, Flop b) { return a.v > b.v; }
 inline bool operator>=(Flop a, Flop b) { return a.v >= b.v; }
 inline bool operator==(Flop a, Flop b) { return a.v == b.v; }
-inline Flop sqrt(Flop a) { ++g_ops; return Flop(std::sqrt(a.v)); }
+inline Flop msqrt(Flop a) { ++g_ops; return Flop(std::sqrt(a.v)); }  // found by argument lookup
 
 using namespace me;
 

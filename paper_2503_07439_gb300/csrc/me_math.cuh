@@ -21,6 +21,10 @@
 
 namespace me {
 
+// square root for every arithmetic type used by the amplitude code
+ME_HD float msqrt(float x) { return sqrtf(x); }
+ME_HD double msqrt(double x) { return ::sqrt(x); }
+
 template <typename T>
 struct cx {
   T re, im;
@@ -101,10 +105,10 @@ ME_HD c4<T> czero() {
 template <typename T>
 ME_HD void chi(const r4<T>& p, int lam, cx<T>& c0, cx<T>& c1) {
   T pt2 = p.x * p.x + p.y * p.y;
-  T pa = sqrt(pt2 + p.z * p.z);
+  T pa = msqrt(pt2 + p.z * p.z);
   T s = (p.z >= T(0)) ? pa + p.z : pt2 / (pa - p.z);
   if (s > T(0)) {
-    T rden = T(1) / sqrt(T(2) * pa * s);
+    T rden = T(1) / msqrt(T(2) * pa * s);
     if (lam > 0) {
       c0 = cx<T>{s * rden, T(0)};
       c1 = cx<T>{p.x * rden, p.y * rden};
@@ -125,8 +129,8 @@ ME_HD void chi(const r4<T>& p, int lam, cx<T>& c0, cx<T>& c1) {
 
 template <typename T>
 ME_HD void omegas(const r4<T>& p, T m, T& wp, T& wm) {
-  T pa = sqrt(p.x * p.x + p.y * p.y + p.z * p.z);
-  wp = sqrt(p.e + pa);
+  T pa = msqrt(p.x * p.x + p.y * p.y + p.z * p.z);
+  wp = msqrt(p.e + pa);
   wm = (m == T(0)) ? T(0) : m / wp;
 }
 
@@ -160,8 +164,8 @@ ME_HD c4<T> dbar(const c4<T>& s) {
 template <typename T>
 ME_HD c4<T> polvec(const r4<T>& k, int lam, bool outgoing) {
   T pt2 = k.x * k.x + k.y * k.y;
-  T pt = sqrt(pt2);
-  T ka = sqrt(pt2 + k.z * k.z);
+  T pt = msqrt(pt2);
+  T ka = msqrt(pt2 + k.z * k.z);
   T ct = k.z / ka, st = pt / ka;
   T cp = T(1), sp = T(0);
   if (pt > T(0)) {
