@@ -35,8 +35,19 @@ template <int PID>
 static double amp_ops(const r4<double>* p, const c4<Flop>* ov = nullptr, int ov_leg = -1, int hel = 5) {
   cx<Flop> J[24];
   const Couplings cp{1.2, 0.3, 173.0};
+  const Kin<PID, Flop> K = prepare<PID, Flop>(p, cp);
   g_ops = 0;
-  amplitude<PID, Flop>(p, hel, cp, J, ov, ov_leg);
+  amplitude<PID, Flop>(K, hel, cp, J, ov, ov_leg);
+  return (double)g_ops;
+}
+
+// per-event preparation (reciprocal denominators etc. in the amplitude's type)
+template <int PID>
+static double prep_ops(const r4<double>* p) {
+  const Couplings cp{1.2, 0.3, 173.0};
+  g_ops = 0;
+  const Kin<PID, Flop> K = prepare<PID, Flop>(p, cp);
+  (void)K;
   return (double)g_ops;
 }
 
@@ -58,9 +69,12 @@ int main() {
   const double h_uu = uu + csum_ops(2), h_uug = uug + csum_ops(4);
   // subtracted real: real helicities + Born tasks (soft with eikonal form, collinear, spin-correlated)
   const double quad2 = 10.0;
-  const double real_ee = 32 * h_eeg + 32 * h_ee;
-  const double real_gg = 32 * h_ggg + 16 * (h_gg + quad2) + 16 * h_gg + 16 * (gg_ov + csum_ops(2));
-  const double real_uu = 32 * h_uug + 16 * (h_uu + quad2) + 16 * h_uu;
+  const double pr_ee = prep_ops<P_EE_UU>(p), pr_eeg = prep_ops<P_EE_UUG>(p);
+  const double pr_gg = prep_ops<P_GG_TT>(p), pr_ggg = prep_ops<P_GG_TTG>(p);
+  const double pr_uu = prep_ops<P_UU_TT>(p), pr_uug = prep_ops<P_UU_TTG>(p);
+  const double real_ee = 32 * h_eeg + pr_eeg + 32 * h_ee + 2 * pr_ee;
+  const double real_gg = 32 * h_ggg + pr_ggg + 16 * (h_gg + quad2) + 16 * h_gg + 16 * (gg_ov + csum_ops(2)) + 3 * pr_gg;
+  const double real_uu = 32 * h_uug + pr_uug + 16 * (h_uu + quad2) + 16 * h_uu + 2 * pr_uu;
   std::printf(
       "{\"per_helicity\": {\"ee_uu\": %.0f, \"ee_uug\": %.0f, \"gg_tt\": %.0f, \"gg_ttg\": %.0f, "
       "\"gg_ttgg\": %.0f, \"uu_tt\": %.0f, \"uu_ttg\": %.0f},\n"
@@ -68,7 +82,8 @@ int main() {
       "\"gg_ttgg\": %.0f, \"uu_tt\": %.0f, \"uu_ttg\": %.0f},\n"
       " \"real_subtracted_per_event\": {\"ee_uug\": %.0f, \"gg_ttg\": %.0f, \"uu_ttg\": %.0f},\n"
       " \"colour_sum_per_event\": {\"gg_ttgg\": %.0f}}\n",
-      h_ee, h_eeg, h_gg, h_ggg, h_gggg, h_uu, h_uug, 16 * h_ee, 32 * h_eeg, 16 * h_gg, 32 * h_ggg, 64 * h_gggg,
-      16 * h_uu, 32 * h_uug, real_ee, real_gg, real_uu, 64 * csum_ops(24));
+      h_ee, h_eeg, h_gg, h_ggg, h_gggg, h_uu, h_uug, 16 * h_ee + pr_ee, 32 * h_eeg + pr_eeg, 16 * h_gg + pr_gg,
+      32 * h_ggg + pr_ggg, 64 * h_gggg + prep_ops<P_GG_TTGG>(p), 16 * h_uu + pr_uu, 32 * h_uug + pr_uug, real_ee,
+      real_gg, real_uu, 64 * csum_ops(24));
   return 0;
 }

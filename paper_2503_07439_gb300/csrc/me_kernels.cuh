@@ -8,6 +8,7 @@
 // masked afterwards (Sec. 4.3, Algorithm 2), so a warp never diverges on cuts.
 #pragma once
 #include "me_procs.cuh"
+#include "me_tc.cuh"
 
 // minimum resident 128-thread blocks per SM requested from the register allocator
 #ifndef ME_MINB
@@ -113,13 +114,47 @@ __global__ void __launch_bounds__(128, ME_MINB) k_tree(const double* __restrict_
   const long ev = idx ? (long)idx[gid] : gid;
   r4<double> k[NEXT];
   load_event<NEXT>(p, n, ev, k);
+  const Kin<PID, T> K = prepare<PID, T>(k, kp.cp);
   T acc = T(0);
   for (int h = lane; h < NHEL; h += LPE) {
     cx<T> J[NF];
-    amplitude<PID, T>(k, h, kp.cp, J);
+    amplitude<PID, T>(K, h, kp.cp, J);
     acc += colour_sum<PID, T>(kp.tab, J);
   }
   double tot = (double)group_sum<LPE>(acc, group_mask<LPE>());
+  if (lane == 0) {
+    const double w = wgt ? wgt[ev] : 1.0;
+    out[ev] = w * tot * kp.avg_inv * kp.nlo_factor;
+  }
+}
+
+// ---------------------------------------------------------------- tree |M|^2, colour sum on tensor cores
+// One warp per event, lanes <-> helicities (64 helicities in two passes of 32); the
+// 24-flow colour sum of each pass is one warp-wide bf16 tensor-core contraction
+// (me_tc.cuh).  float32 amplitudes; g g -> t tbar g g only.
+template <int PID>
+__global__ void __launch_bounds__(128, ME_MINB) k_tree_tc(const double* __restrict__ p, const double* __restrict__ wgt,
+                                                          long n, double* __restrict__ out, KParams kp,
+                                                          const int* __restrict__ idx, const int* __restrict__ count) {
+  static_assert(Proc<PID>::NFLOW == TC_NF && Proc<PID>::NHEL % 32 == 0, "tensor-core colour sum layout");
+  constexpr int NEXT = Proc<PID>::NEXT, NHEL = Proc<PID>::NHEL;
+  __shared__ __align__(16) unsigned char smem[4 * TC_SMEM_PER_WARP];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long gid = (long)blockIdx.x * (blockDim.x >> 5) + warp;
+  const long nev = idx ? (long)*count : n;
+  if (gid >= nev) return;  // uniform over the warp
+  const long ev = idx ? (long)idx[gid] : gid;
+  r4<double> k[NEXT];
+  load_event<NEXT>(p, n, ev, k);
+  const TcColourB cb = tc_load_colour(kp.tab->C[PID]);
+  const Kin<PID, float> K = prepare<PID, float>(k, kp.cp);
+  float acc = 0.0f;
+  for (int h = lane; h < NHEL; h += 32) {
+    cx<float> J[TC_NF];
+    amplitude<PID, float>(K, h, kp.cp, J);
+    acc += tc_colour_sum(J, cb, smem + warp * TC_SMEM_PER_WARP);
+  }
+  const double tot = (double)group_sum<32>(acc, 0xffffffffu);
   if (lane == 0) {
     const double w = wgt ? wgt[ev] : 1.0;
     out[ev] = w * tot * kp.avg_inv * kp.nlo_factor;
@@ -267,10 +302,13 @@ __global__ void __launch_bounds__(128, ME_MINB) k_real_sub(const double* __restr
 
   // real matrix element
   T accR = T(0);
-  for (int h = lane; h < NHEL; h += LPE) {
-    cx<T> J[NF];
-    amplitude<PID, T>(k, h, kp.cp, J);
-    accR += colour_sum<PID, T>(kp.tab, J);
+  {
+    const Kin<PID, T> K = prepare<PID, T>(k, kp.cp);
+    for (int h = lane; h < NHEL; h += LPE) {
+      cx<T> J[NF];
+      amplitude<PID, T>(K, h, kp.cp, J);
+      accR += colour_sum<PID, T>(kp.tab, J);
+    }
   }
   const double R = (double)group_sum<LPE>(accR, mask) * kp.avg_inv;
 
@@ -280,11 +318,14 @@ __global__ void __launch_bounds__(128, ME_MINB) k_real_sub(const double* __restr
     FsrKin f;
     fsr_map(k, f);
     T aB[2] = {T(0), T(0)};
-    for (int t = lane; t < 32; t += LPE) {
-      const int j = t >> 4, h = t & 15;
-      cx<T> J[BNF];
-      amplitude<BPID, T>(f.born[j], h, kp.cp, J);
-      aB[j] += colour_sum<BPID, T>(kp.tab, J);
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const Kin<BPID, T> KB = prepare<BPID, T>(f.born[j], kp.cp);
+      for (int h = lane; h < 16; h += LPE) {
+        cx<T> J[BNF];
+        amplitude<BPID, T>(KB, h, kp.cp, J);
+        aB[j] += colour_sum<BPID, T>(kp.tab, J);
+      }
     }
     double B[2];
     B[0] = (double)group_sum<LPE>(aB[0], mask) * kp.born_avg_inv;
@@ -327,25 +368,39 @@ __global__ void __launch_bounds__(128, ME_MINB) k_real_sub(const double* __restr
     eperp.v[1] = cx<T>{(T)f.cphi, T(0)};
     eperp.v[2] = cx<T>{(T)f.sphi, T(0)};
     eperp.v[3] = cx<T>{T(0), T(0)};
-    // Born tasks: [0,16) soft, [16,32) collinear, gg only: [32,40) perp leg 0, [40,48) perp leg 1
-    constexpr int NTASK = (BPID == P_GG_TT) ? 48 : 32;
+    // Born tasks: soft Born (eikonal-weighted correlators and plain), collinear Born,
+    // and for g g the spin-correlated Born of each beam (the polarised gluon's bit unused)
     T aE = T(0), aS = T(0), aC = T(0), aP[2] = {T(0), T(0)};
-    for (int t = lane; t < NTASK; t += LPE) {
-      cx<T> J[BNF];
-      if (t < 16) {
-        amplitude<BPID, T>(f.soft, t, kp.cp, J);
+    {
+      const Kin<BPID, T> KB = prepare<BPID, T>(f.soft, kp.cp);
+      for (int h = lane; h < 16; h += LPE) {
+        cx<T> J[BNF];
+        amplitude<BPID, T>(KB, h, kp.cp, J);
         aE += quad2(Et, J);
         aS += colour_sum<BPID, T>(kp.tab, J);
-      } else if (t < 32) {
-        amplitude<BPID, T>(f.coll[0], t - 16, kp.cp, J);
+      }
+    }
+    {
+      const Kin<BPID, T> KB = prepare<BPID, T>(f.coll[0], kp.cp);
+      for (int h = lane; h < 16; h += LPE) {
+        cx<T> J[BNF];
+        amplitude<BPID, T>(KB, h, kp.cp, J);
         aC += colour_sum<BPID, T>(kp.tab, J);
-      } else {
-        const int j = (t - 32) >> 3;
-        const int r = (t - 32) & 7;
-        // helicities of the three other legs; the polarised gluon's bit is ignored
-        const int h = j == 0 ? (r << 1) : ((r & 1) | ((r >> 1) << 2));
-        amplitude<BPID, T>(f.coll[j], h, kp.cp, J, &eperp, j);
-        aP[j] += colour_sum<BPID, T>(kp.tab, J);
+      }
+      if constexpr (BPID == P_GG_TT) {
+        for (int r = lane; r < 8; r += LPE) {
+          cx<T> J[BNF];
+          amplitude<BPID, T>(KB, r << 1, kp.cp, J, &eperp, 0);
+          aP[0] += colour_sum<BPID, T>(kp.tab, J);
+        }
+      }
+    }
+    if constexpr (BPID == P_GG_TT) {
+      const Kin<BPID, T> KB = prepare<BPID, T>(f.coll[1], kp.cp);
+      for (int r = lane; r < 8; r += LPE) {
+        cx<T> J[BNF];
+        amplitude<BPID, T>(KB, (r & 1) | ((r >> 1) << 2), kp.cp, J, &eperp, 1);
+        aP[1] += colour_sum<BPID, T>(kp.tab, J);
       }
     }
     const double bav = kp.born_avg_inv;
@@ -415,6 +470,14 @@ struct LaunchArgs {
 };
 enum KernelKind : int { K_TREE = 0, K_REAL = 1 };
 
+template <int PID>
+cudaError_t launch_tree_tc(const LaunchArgs& a, cudaStream_t st) {
+  const long blocks = (a.groups + 3) / 4;
+  if (blocks <= 0) return cudaSuccess;
+  k_tree_tc<PID><<<(unsigned)blocks, 128, 0, st>>>(a.p, a.wgt, a.n, a.out, a.kp, a.idx, a.count);
+  return cudaGetLastError();
+}
+
 template <int PID, typename T, int LPE>
 cudaError_t launch_one(int kind, const LaunchArgs& a, cudaStream_t st) {
   const int threads = 128;
@@ -433,7 +496,8 @@ cudaError_t launch_one(int kind, const LaunchArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// per-process launchers (one translation unit each); lpe in {1, 2, 4, 8, 16}
+// per-process launchers (one translation unit each); lpe in {1, 2, 4, 8, 16}; for
+// g g -> t tbar g g in float32, lpe 32 selects the tensor-core colour-sum kernel
 cudaError_t launch_ee(int pid, int kind, bool fp64, int lpe, const LaunchArgs& a, cudaStream_t st);
 cudaError_t launch_gg(int pid, int kind, bool fp64, int lpe, const LaunchArgs& a, cudaStream_t st);
 cudaError_t launch_ggg(int pid, int kind, bool fp64, int lpe, const LaunchArgs& a, cudaStream_t st);

@@ -14,8 +14,10 @@
 //      amplitude      A(s) = sum_j U(s_1..s_j) (i g Jslash(s_{j+1}..s_n)) v(tbar).
 //  * e+e- -> u ubar (g): photon current from the leptons inserted on the quark line.
 //  * u ubar -> t tbar (g): explicit diagrams, colour by Fierz onto a 2- (4-) element basis.
-// Momenta: all-outgoing (q = -p for incoming legs), kept in double for the
-// propagator denominators; spinors and currents are in T.
+// Momenta: all-outgoing (q = -p for incoming legs).  Everything that does not depend
+// on the helicities -- momenta in T and the reciprocal propagator denominators, whose
+// invariants are formed in float64 to avoid cancellation -- is prepared once per event
+// (prepare<PID,T>) and shared by all helicities; spinors and currents are in T.
 #pragma once
 #include "me_math.cuh"
 
@@ -66,89 +68,105 @@ ME_HD void nth_perm(int n, int idx, int* out) {
 ME_HD int hel_of(int hel, int leg) { return ((hel >> leg) & 1) ? 1 : -1; }
 
 // ----------------------------------------------------------------------------
-// t tbar + NG gluons.  Gluon legs: the two incoming legs 0,1 and outgoing legs 4,5..
-// Leg 2 = t (ubar), leg 3 = tbar (v).  `eps_override`: replace gluon leg `ov_leg`'s
-// polarisation by a given vector (spin-correlated Born), else nullptr.
+// Per-event kinematics of t tbar + NG gluons.  Gluon g (0..NG-1) is leg 0, 1, 4, 5.
+// ig[S] = 1/Q_S^2 for a gluon subset S (bit mask, |S| >= 2), iq[S] = 1/((p_t+Q_S)^2-m^2).
 template <typename T, int NG>
-ME_HD void amp_ttng(const r4<double>* p, int hel, const Couplings& cp, const c4<T>* eps_override,
-                         int ov_leg, cx<T>* A) {
+struct KinTT {
+  r4<T> pl[6];          // physical external momenta (wavefunctions)
+  r4<T> q[NG];          // outgoing gluon momenta
+  T ig[1 << NG];
+  T iq[1 << NG];
+};
+
+template <typename T, int NG>
+ME_HD KinTT<T, NG> prep_tt(const r4<double>* p, const Couplings& cp) {
+  KinTT<T, NG> K;
+  const int NEXT = NG + 2;
+  for (int l = 0; l < NEXT; ++l) K.pl[l] = cast4<T>(p[l]);
+  r4<double> q[NG];
+  for (int i = 0; i < NG; ++i) {
+    const int l = i < 2 ? i : i + 2;
+    q[i] = l < 2 ? -p[l] : p[l];
+    K.q[i] = cast4<T>(q[i]);
+  }
+  const double m2 = cp.mt * cp.mt;
+  for (int S = 1; S < (1 << NG); ++S) {
+    r4<double> Q{0.0, 0.0, 0.0, 0.0};
+    int cnt = 0;
+    for (int i = 0; i < NG; ++i)
+      if (S >> i & 1) {
+        Q = Q + q[i];
+        ++cnt;
+      }
+    K.ig[S] = cnt >= 2 ? T(1) / (T)mdot(Q, Q) : T(0);
+    const r4<double> P = p[2] + Q;
+    K.iq[S] = cnt <= NG - 1 ? T(1) / (T)(mdot(P, P) - m2) : T(0);
+  }
+  K.ig[0] = K.iq[0] = T(0);
+  return K;
+}
+
+// Generic colour-ordered recursion (used for 4 gluons): for every ordering, contiguous
+// gluon currents J[i][j] and the top line U[k]; denominators from the per-event table.
+template <typename T, int NG>
+ME_HD void amp_ttng(const KinTT<T, NG>& K, int hel, const Couplings& cp, cx<T>* A) {
   constexpr int NF = factorial(NG);
   const T g = (T)cp.gs;
   const T mt = (T)cp.mt;
-  int gleg[NG];
-  gleg[0] = 0;
-  gleg[1] = 1;
-#pragma unroll
-  for (int i = 2; i < NG; ++i) gleg[i] = 2 + i;
   c4<T> eps[NG];
-  r4<double> qg[NG];
 #pragma unroll
   for (int i = 0; i < NG; ++i) {
-    int l = gleg[i];
-    bool in = l < 2;
-    qg[i] = in ? -p[l] : p[l];
-    if (eps_override != nullptr && l == ov_leg)
-      eps[i] = *eps_override;
-    else
-      eps[i] = polvec(cast4<T>(p[l]), hel_of(hel, l), !in);
+    const int l = i < 2 ? i : i + 2;
+    eps[i] = polvec(K.pl[l], hel_of(hel, l), l >= 2);
   }
-  const c4<T> ub = dbar(spinor_u(cast4<T>(p[2]), mt, hel_of(hel, 2)));
-  const c4<T> vb = spinor_v(cast4<T>(p[3]), mt, hel_of(hel, 3));
-  const r4<double> qt = p[2];
-  const double mt2 = cp.mt * cp.mt;
-
+  const c4<T> ub = dbar(spinor_u(K.pl[2], mt, hel_of(hel, 2)));
+  const c4<T> vb = spinor_v(K.pl[3], mt, hel_of(hel, 3));
   for (int f = 0; f < NF; ++f) {
     int s[NG];
     nth_perm(NG, f, s);
-    // contiguous gluon currents J[i][j] of the ordering, momenta Q[i][j]
     c4<T> J[NG][NG];
-    r4<double> Q[NG][NG];
+    r4<T> Q[NG][NG];
+    int M[NG][NG];
 #pragma unroll
     for (int i = 0; i < NG; ++i) {
       J[i][i] = eps[s[i]];
-      Q[i][i] = qg[s[i]];
+      Q[i][i] = K.q[s[i]];
+      M[i][i] = 1 << s[i];
     }
 #pragma unroll
     for (int len = 2; len <= NG; ++len) {
 #pragma unroll
       for (int i = 0; i + len - 1 < NG; ++i) {
         const int j = i + len - 1;
-        Q[i][j] = Q[i][j - 1] + qg[s[j]];
-        const double q2 = mdot(Q[i][j], Q[i][j]);
-        const T c3 = (T)(-1.0 / q2) * g;
+        Q[i][j] = Q[i][j - 1] + K.q[s[j]];
+        M[i][j] = M[i][j - 1] | (1 << s[j]);
+        const T inv = K.ig[M[i][j]];
         c4<T> acc = czero<T>();
 #pragma unroll
-        for (int k = i; k < j; ++k) {
-          c4<T> w = vvv(J[i][k], J[k + 1][j], cast4<T>(-Q[i][k]), cast4<T>(-Q[k + 1][j]));
-          cadd(acc, w);
-        }
-        cscale(acc, c3);
+        for (int k = i; k < j; ++k) cadd(acc, vvv(J[i][k], J[k + 1][j], -Q[i][k], -Q[k + 1][j]));
+        cscale(acc, -g * inv);
         if (len >= 3) {
-          const T c4g = (T)(1.0 / q2) * g * g;
           c4<T> acc4 = czero<T>();
 #pragma unroll
           for (int k = i; k < j - 1; ++k)
 #pragma unroll
             for (int l = k + 1; l < j; ++l) cadd(acc4, vvvv_ordered(J[i][k], J[k + 1][l], J[l + 1][j]));
-          caxpy(acc, cx<T>{c4g, T(0)}, acc4);
+          caxpy(acc, cx<T>{g * g * inv, T(0)}, acc4);
         }
         J[i][j] = acc;
       }
     }
-    // quark line from the top side: U[k] = top with the first k gluons attached
     c4<T> U[NG];
     U[0] = ub;
-    r4<double> Qu = qt;
+    r4<T> Qu = K.pl[2];
 #pragma unroll
     for (int k = 1; k < NG; ++k) {
-      Qu = Qu + qg[s[k - 1]];
+      Qu = Qu + K.q[s[k - 1]];
       c4<T> acc = czero<T>();
 #pragma unroll
       for (int j = 0; j < k; ++j) cadd(acc, row_slash(U[j], J[j][k - 1]));
-      const double den = mdot(Qu, Qu) - mt2;
-      // (i g)(i)/den = -g/den
-      c4<T> pr = row_prop(acc, cast4<T>(Qu), mt);
-      cscale(pr, (T)(-1.0 / den) * g);
+      c4<T> pr = row_prop(acc, Qu, mt);
+      cscale(pr, -g * K.iq[M[0][k - 1]]);
       U[k] = pr;
     }
     cx<T> a = cx<T>{T(0), T(0)};
@@ -158,7 +176,6 @@ ME_HD void amp_ttng(const r4<double>* p, int hel, const Couplings& cp, const c4<
   }
 }
 
-// ----------------------------------------------------------------------------
 // t tbar + 2 or 3 gluons with every sub-current computed once per helicity.
 // Colour-ordered currents obey the reflection identity J(s reversed) = (-1)^(k+1) J(s)
 // for k gluons (V3 is antisymmetric in its two legs, the ordered V4 symmetric in its
@@ -166,62 +183,43 @@ ME_HD void amp_ttng(const r4<double>* p, int hel, const Couplings& cp, const c4<
 // and the amplitudes of all orderings then reuse them.  Orderings are numbered
 // lexicographically as in amp_ttng, so the colour basis is the same.
 template <typename T>
-ME_HD void amp_tt2_fast(const r4<double>* p, int hel, const Couplings& cp, const c4<T>* ov, int ov_leg, cx<T>* A) {
+ME_HD void amp_tt2_fast(const KinTT<T, 2>& K, int hel, const Couplings& cp, const c4<T>* ov, int ov_leg, cx<T>* A) {
   const T g = (T)cp.gs, mt = (T)cp.mt;
-  const double m2 = cp.mt * cp.mt;
-  const r4<double> Q0 = -p[0], Q1 = -p[1], Pt = p[2];
-  // inverse propagator denominators from float64 momentum sums
-  const T i01 = (T)(1.0 / mdot(Q0 + Q1, Q0 + Q1));
-  const T u0 = (T)(1.0 / (mdot(Pt + Q0, Pt + Q0) - m2));
-  const T u1 = (T)(1.0 / (mdot(Pt + Q1, Pt + Q1) - m2));
-  const r4<T> k0 = cast4<T>(Q0), k1 = cast4<T>(Q1), kt = cast4<T>(Pt);
-  const c4<T> e0 = (ov != nullptr && ov_leg == 0) ? *ov : polvec(cast4<T>(p[0]), hel_of(hel, 0), false);
-  const c4<T> e1 = (ov != nullptr && ov_leg == 1) ? *ov : polvec(cast4<T>(p[1]), hel_of(hel, 1), false);
+  const r4<T> k0 = K.q[0], k1 = K.q[1], kt = K.pl[2];
+  const c4<T> e0 = (ov != nullptr && ov_leg == 0) ? *ov : polvec(K.pl[0], hel_of(hel, 0), false);
+  const c4<T> e1 = (ov != nullptr && ov_leg == 1) ? *ov : polvec(K.pl[1], hel_of(hel, 1), false);
   const c4<T> ub = dbar(spinor_u(kt, mt, hel_of(hel, 2)));
-  const c4<T> vb = spinor_v(cast4<T>(p[3]), mt, hel_of(hel, 3));
+  const c4<T> vb = spinor_v(K.pl[3], mt, hel_of(hel, 3));
   c4<T> J01 = vvv(e0, e1, -k0, -k1);
-  cscale(J01, -g * i01);
+  cscale(J01, -g * K.ig[3]);
   const cx<T> s01 = spdot(row_slash(ub, J01), vb);
   c4<T> U0 = row_prop(row_slash(ub, e0), kt + k0, mt);
-  cscale(U0, -g * u0);
+  cscale(U0, -g * K.iq[1]);
   c4<T> U1 = row_prop(row_slash(ub, e1), kt + k1, mt);
-  cscale(U1, -g * u1);
+  cscale(U1, -g * K.iq[2]);
   // A(01) = ig[ub J01 v + U0 e1 v],  A(10) = ig[-ub J01 v + U1 e0 v]
   A[0] = times_i(s01 + spdot(row_slash(U0, e1), vb)) * g;
   A[1] = times_i(spdot(row_slash(U1, e0), vb) - s01) * g;
 }
 
 template <typename T>
-ME_HD void amp_tt3_fast(const r4<double>* p, int hel, const Couplings& cp, cx<T>* A) {
+ME_HD void amp_tt3_fast(const KinTT<T, 3>& K, int hel, const Couplings& cp, cx<T>* A) {
   const T g = (T)cp.gs, mt = (T)cp.mt;
-  const double m2 = cp.mt * cp.mt;
-  const r4<double> Q0 = -p[0], Q1 = -p[1], Q2 = p[4], Pt = p[2];
-  const T i01 = (T)(1.0 / mdot(Q0 + Q1, Q0 + Q1));
-  const T i02 = (T)(1.0 / mdot(Q0 + Q2, Q0 + Q2));
-  const T i12 = (T)(1.0 / mdot(Q1 + Q2, Q1 + Q2));
-  const r4<double> Qa = Q0 + Q1 + Q2;
-  const T i012 = (T)(1.0 / mdot(Qa, Qa));
-  const T u0 = (T)(1.0 / (mdot(Pt + Q0, Pt + Q0) - m2));
-  const T u1 = (T)(1.0 / (mdot(Pt + Q1, Pt + Q1) - m2));
-  const T u2 = (T)(1.0 / (mdot(Pt + Q2, Pt + Q2) - m2));
-  const T u01 = (T)(1.0 / (mdot(Pt + Q0 + Q1, Pt + Q0 + Q1) - m2));
-  const T u02 = (T)(1.0 / (mdot(Pt + Q0 + Q2, Pt + Q0 + Q2) - m2));
-  const T u12 = (T)(1.0 / (mdot(Pt + Q1 + Q2, Pt + Q1 + Q2) - m2));
-  const r4<T> k0 = cast4<T>(Q0), k1 = cast4<T>(Q1), k2 = cast4<T>(Q2), kt = cast4<T>(Pt);
-  const c4<T> e0 = polvec(cast4<T>(p[0]), hel_of(hel, 0), false);
-  const c4<T> e1 = polvec(cast4<T>(p[1]), hel_of(hel, 1), false);
-  const c4<T> e2 = polvec(k2, hel_of(hel, 4), true);
+  const r4<T> k0 = K.q[0], k1 = K.q[1], k2 = K.q[2], kt = K.pl[2];
+  const c4<T> e0 = polvec(K.pl[0], hel_of(hel, 0), false);
+  const c4<T> e1 = polvec(K.pl[1], hel_of(hel, 1), false);
+  const c4<T> e2 = polvec(K.pl[4], hel_of(hel, 4), true);
   const c4<T> ub = dbar(spinor_u(kt, mt, hel_of(hel, 2)));
-  const c4<T> vb = spinor_v(cast4<T>(p[3]), mt, hel_of(hel, 3));
+  const c4<T> vb = spinor_v(K.pl[3], mt, hel_of(hel, 3));
   // pair currents J(xy), x<y; J(yx) = -J(xy)
   c4<T> J01 = vvv(e0, e1, -k0, -k1);
-  cscale(J01, -g * i01);
+  cscale(J01, -g * K.ig[3]);
   c4<T> J02 = vvv(e0, e2, -k0, -k2);
-  cscale(J02, -g * i02);
+  cscale(J02, -g * K.ig[5]);
   c4<T> J12 = vvv(e1, e2, -k1, -k2);
-  cscale(J12, -g * i12);
+  cscale(J12, -g * K.ig[6]);
   // three-gluon currents F(abc) = F(cba): -(g/Q^2)[V3(a, bc) + V3(ab, c)] + (g^2/Q^2) V4(a,b,c)
-  const T c3 = -g * i012, c4g = g * g * i012;
+  const T c3 = -g * K.ig[7], c4g = g * g * K.ig[7];
   cx<T> a[6];
   {
     c4<T> F = vvv(e0, J12, -k0, -(k1 + k2));
@@ -251,24 +249,24 @@ ME_HD void amp_tt3_fast(const r4<double>* p, int hel, const Couplings& cp, cx<T>
   // orderings grouped by the gluon next to the top: U(x), then U(x y) = U(x) e_y + ubar J(xy)
   {  // x = 0: orderings 012 (a0), 021 (a1)
     c4<T> U = row_prop(row_slash(ub, e0), kt + k0, mt);
-    cscale(U, -g * u0);
+    cscale(U, -g * K.iq[1]);
     const cx<T> t = spdot(row_slash(U, J12), vb);
     a[0] = a[0] + t;
     a[1] = a[1] - t;
     c4<T> r = row_slash(U, e1);
     cadd(r, row_slash(ub, J01));
     c4<T> W = row_prop(r, kt + k0 + k1, mt);
-    cscale(W, -g * u01);
+    cscale(W, -g * K.iq[3]);
     a[0] = a[0] + spdot(row_slash(W, e2), vb);
     r = row_slash(U, e2);
     cadd(r, row_slash(ub, J02));
     W = row_prop(r, kt + k0 + k2, mt);
-    cscale(W, -g * u02);
+    cscale(W, -g * K.iq[5]);
     a[1] = a[1] + spdot(row_slash(W, e1), vb);
   }
   {  // x = 1: orderings 102 (a2), 120 (a3)
     c4<T> U = row_prop(row_slash(ub, e1), kt + k1, mt);
-    cscale(U, -g * u1);
+    cscale(U, -g * K.iq[2]);
     const cx<T> t = spdot(row_slash(U, J02), vb);
     a[2] = a[2] + t;
     a[3] = a[3] - t;
@@ -277,17 +275,17 @@ ME_HD void amp_tt3_fast(const r4<double>* p, int hel, const Couplings& cp, cx<T>
     cscale(b, T(-1));
     cadd(r, b);
     c4<T> W = row_prop(r, kt + k0 + k1, mt);
-    cscale(W, -g * u01);
+    cscale(W, -g * K.iq[3]);
     a[2] = a[2] + spdot(row_slash(W, e2), vb);
     r = row_slash(U, e2);
     cadd(r, row_slash(ub, J12));
     W = row_prop(r, kt + k1 + k2, mt);
-    cscale(W, -g * u12);
+    cscale(W, -g * K.iq[6]);
     a[3] = a[3] + spdot(row_slash(W, e0), vb);
   }
   {  // x = 2: orderings 201 (a4), 210 (a5)
     c4<T> U = row_prop(row_slash(ub, e2), kt + k2, mt);
-    cscale(U, -g * u2);
+    cscale(U, -g * K.iq[4]);
     const cx<T> t = spdot(row_slash(U, J01), vb);
     a[4] = a[4] + t;
     a[5] = a[5] - t;
@@ -296,14 +294,14 @@ ME_HD void amp_tt3_fast(const r4<double>* p, int hel, const Couplings& cp, cx<T>
     cscale(b, T(-1));
     cadd(r, b);
     c4<T> W = row_prop(r, kt + k0 + k2, mt);
-    cscale(W, -g * u02);
+    cscale(W, -g * K.iq[5]);
     a[4] = a[4] + spdot(row_slash(W, e1), vb);
     r = row_slash(U, e1);
     b = row_slash(ub, J12);
     cscale(b, T(-1));
     cadd(r, b);
     W = row_prop(r, kt + k1 + k2, mt);
-    cscale(W, -g * u12);
+    cscale(W, -g * K.iq[6]);
     a[5] = a[5] + spdot(row_slash(W, e0), vb);
   }
 #pragma unroll
@@ -313,41 +311,60 @@ ME_HD void amp_tt3_fast(const r4<double>* p, int hel, const Couplings& cp, cx<T>
 // ----------------------------------------------------------------------------
 // e+(0) e-(1) -> u(2) ubar(3) [g(4)].  Photon exchange; charges Q_e = -1, Q_u = 2/3.
 template <typename T>
-ME_HD c4<T> lepton_current(const r4<double>* p, int hel, const Couplings& cp) {
+struct KinEE {
+  r4<T> pl[5];
+  T is;      // 1/s of the photon
+  T i1, i2;  // 1/(p_u+k)^2, 1/(p_ubar+k)^2 (real emission)
+};
+
+template <typename T, int NEXT>
+ME_HD KinEE<T> prep_ee(const r4<double>* p) {
+  KinEE<T> K;
+  for (int l = 0; l < NEXT; ++l) K.pl[l] = cast4<T>(p[l]);
+  const r4<double> Q = p[0] + p[1];
+  K.is = T(1) / (T)mdot(Q, Q);
+  K.i1 = K.i2 = T(0);
+  if (NEXT == 5) {
+    const r4<double> Q1 = p[2] + p[4], Q2 = p[3] + p[4];
+    K.i1 = T(1) / (T)mdot(Q1, Q1);
+    K.i2 = T(1) / (T)mdot(Q2, Q2);
+  }
+  return K;
+}
+
+template <typename T>
+ME_HD c4<T> lepton_current(const KinEE<T>& K, int hel, const Couplings& cp) {
   // vbar(e+) gamma^mu u(e-) with the photon propagator: (e Q_e / s) vbar gamma u
-  c4<T> vb = dbar(spinor_v(cast4<T>(p[0]), T(0), hel_of(hel, 0)));
-  c4<T> u = spinor_u(cast4<T>(p[1]), T(0), hel_of(hel, 1));
-  r4<double> Q = p[0] + p[1];
+  c4<T> vb = dbar(spinor_v(K.pl[0], T(0), hel_of(hel, 0)));
+  c4<T> u = spinor_u(K.pl[1], T(0), hel_of(hel, 1));
   c4<T> L = vcurrent(vb, u);
-  cscale(L, (T)(-cp.ee / mdot(Q, Q)));
+  cscale(L, -(T)cp.ee * K.is);
   return L;
 }
 
 template <typename T>
-ME_HD void amp_ee_uu(const r4<double>* p, int hel, const Couplings& cp, cx<T>* A) {
-  c4<T> L = lepton_current<T>(p, hel, cp);
-  c4<T> ub = dbar(spinor_u(cast4<T>(p[2]), T(0), hel_of(hel, 2)));
-  c4<T> v = spinor_v(cast4<T>(p[3]), T(0), hel_of(hel, 3));
+ME_HD void amp_ee_uu(const KinEE<T>& K, int hel, const Couplings& cp, cx<T>* A) {
+  c4<T> L = lepton_current<T>(K, hel, cp);
+  c4<T> ub = dbar(spinor_u(K.pl[2], T(0), hel_of(hel, 2)));
+  c4<T> v = spinor_v(K.pl[3], T(0), hel_of(hel, 3));
   const T equ = (T)(cp.ee * (2.0 / 3.0));
   A[0] = times_i(spdot(row_slash(ub, L), v)) * equ;
 }
 
 template <typename T>
-ME_HD void amp_ee_uug(const r4<double>* p, int hel, const Couplings& cp, cx<T>* A) {
-  c4<T> L = lepton_current<T>(p, hel, cp);
-  c4<T> ub = dbar(spinor_u(cast4<T>(p[2]), T(0), hel_of(hel, 2)));
-  c4<T> v = spinor_v(cast4<T>(p[3]), T(0), hel_of(hel, 3));
-  c4<T> eps = polvec(cast4<T>(p[4]), hel_of(hel, 4), true);
+ME_HD void amp_ee_uug(const KinEE<T>& K, int hel, const Couplings& cp, cx<T>* A) {
+  c4<T> L = lepton_current<T>(K, hel, cp);
+  c4<T> ub = dbar(spinor_u(K.pl[2], T(0), hel_of(hel, 2)));
+  c4<T> v = spinor_v(K.pl[3], T(0), hel_of(hel, 3));
+  c4<T> eps = polvec(K.pl[4], hel_of(hel, 4), true);
   const T g = (T)cp.gs;
   const T equ = (T)(cp.ee * (2.0 / 3.0));
   // gluon on the quark side: ubar (i g eps) i(Q1slash)/Q1^2, Q1 = p_u + p_g
-  r4<double> Q1 = p[2] + p[4];
-  c4<T> u1 = row_prop(row_slash(ub, eps), cast4<T>(Q1), T(0));
-  cscale(u1, (T)(-1.0 / mdot(Q1, Q1)) * g);
+  c4<T> u1 = row_prop(row_slash(ub, eps), K.pl[2] + K.pl[4], T(0));
+  cscale(u1, -g * K.i1);
   // gluon on the antiquark side: i(-Q2slash)/Q2^2 (i g eps) v, Q2 = p_ubar + p_g
-  r4<double> Q2 = p[3] + p[4];
-  c4<T> v1 = col_prop(cast4<T>(Q2), T(0), slash_col(eps, v));
-  cscale(v1, (T)(-1.0 / mdot(Q2, Q2)) * g);
+  c4<T> v1 = col_prop(K.pl[3] + K.pl[4], T(0), slash_col(eps, v));
+  cscale(v1, -g * K.i2);
   cx<T> a = spdot(row_slash(u1, L), v) + spdot(row_slash(ub, L), v1);
   A[0] = times_i(a) * equ;
 }
@@ -357,66 +374,95 @@ ME_HD void amp_ee_uug(const r4<double>* p, int hel, const Couplings& cp, cx<T>* 
 //   Born: e1 = d_ik d_lj, e2 = d_ij d_lk;  (T^b)_ij (T^b)_lk = (e1 - e2/N)/2.
 //   Real: e1 = T^a_ik d_lj, e2 = d_ik T^a_lj, e3 = T^a_ij d_lk, e4 = d_ij T^a_lk.
 template <typename T>
-ME_HD c4<T> light_current(const c4<T>& vbar_ub, const c4<T>& u_u, const r4<double>& Q, T g) {
+struct KinUU {
+  r4<T> pl[5];
+  r4<T> q[5];  // outgoing momenta
+  T is;        // 1/(q0+q1)^2
+  T ia, ib;    // top / antitop propagators with the gluon
+  T ic, id;    // light-quark propagators with the gluon
+  T is3, it;   // 1/(q0+q1+q4)^2, 1/(q2+q3)^2
+};
+
+template <typename T, int NEXT>
+ME_HD KinUU<T> prep_uu(const r4<double>* p, const Couplings& cp) {
+  KinUU<T> K;
+  r4<double> q[5];
+  for (int l = 0; l < NEXT; ++l) {
+    K.pl[l] = cast4<T>(p[l]);
+    q[l] = l < 2 ? -p[l] : p[l];
+    K.q[l] = cast4<T>(q[l]);
+  }
+  const double m2 = cp.mt * cp.mt;
+  const r4<double> s01 = q[0] + q[1];
+  K.is = T(1) / (T)mdot(s01, s01);
+  K.ia = K.ib = K.ic = K.id = K.is3 = K.it = T(0);
+  if (NEXT == 5) {
+    const r4<double> a = q[2] + q[4], b = q[3] + q[4], c = q[1] + q[4], d = q[0] + q[4];
+    const r4<double> s3 = s01 + q[4], t = q[2] + q[3];
+    K.ia = T(1) / (T)(mdot(a, a) - m2);
+    K.ib = T(1) / (T)(mdot(b, b) - m2);
+    K.ic = T(1) / (T)mdot(c, c);
+    K.id = T(1) / (T)mdot(d, d);
+    K.is3 = T(1) / (T)mdot(s3, s3);
+    K.it = T(1) / (T)mdot(t, t);
+  }
+  return K;
+}
+
+template <typename T>
+ME_HD c4<T> light_current(const c4<T>& vbar_ub, const c4<T>& u_u, T inv, T g) {
   // (g/Q^2) vbar gamma u  (vertex i g gamma, propagator -i/Q^2)
   c4<T> J = vcurrent(vbar_ub, u_u);
-  cscale(J, (T)(1.0 / mdot(Q, Q)) * g);
+  cscale(J, g * inv);
   return J;
 }
 
 template <typename T>
-ME_HD void amp_uu_tt(const r4<double>* p, int hel, const Couplings& cp, cx<T>* A) {
+ME_HD void amp_uu_tt(const KinUU<T>& K, int hel, const Couplings& cp, cx<T>* A) {
   const T g = (T)cp.gs, mt = (T)cp.mt;
-  c4<T> uu = spinor_u(cast4<T>(p[0]), T(0), hel_of(hel, 0));
-  c4<T> vbu = dbar(spinor_v(cast4<T>(p[1]), T(0), hel_of(hel, 1)));
-  c4<T> ub = dbar(spinor_u(cast4<T>(p[2]), mt, hel_of(hel, 2)));
-  c4<T> vt = spinor_v(cast4<T>(p[3]), mt, hel_of(hel, 3));
-  c4<T> Ju = light_current(vbu, uu, p[0] + p[1], g);
+  c4<T> uu = spinor_u(K.pl[0], T(0), hel_of(hel, 0));
+  c4<T> vbu = dbar(spinor_v(K.pl[1], T(0), hel_of(hel, 1)));
+  c4<T> ub = dbar(spinor_u(K.pl[2], mt, hel_of(hel, 2)));
+  c4<T> vt = spinor_v(K.pl[3], mt, hel_of(hel, 3));
+  c4<T> Ju = light_current(vbu, uu, K.is, g);
   cx<T> d = times_i(spdot(row_slash(ub, Ju), vt)) * g;
   A[0] = d * T(0.5);
   A[1] = d * (T)(-1.0 / 6.0);
 }
 
 template <typename T>
-ME_HD void amp_uu_ttg(const r4<double>* p, int hel, const Couplings& cp, cx<T>* A) {
+ME_HD void amp_uu_ttg(const KinUU<T>& K, int hel, const Couplings& cp, cx<T>* A) {
   const T g = (T)cp.gs, mt = (T)cp.mt;
-  const double mt2 = cp.mt * cp.mt;
-  c4<T> uu = spinor_u(cast4<T>(p[0]), T(0), hel_of(hel, 0));
-  c4<T> vbu = dbar(spinor_v(cast4<T>(p[1]), T(0), hel_of(hel, 1)));
-  c4<T> ub = dbar(spinor_u(cast4<T>(p[2]), mt, hel_of(hel, 2)));
-  c4<T> vt = spinor_v(cast4<T>(p[3]), mt, hel_of(hel, 3));
-  c4<T> eps = polvec(cast4<T>(p[4]), hel_of(hel, 4), true);
-  // outgoing momenta
-  const r4<double> q0 = -p[0], q1 = -p[1], q2 = p[2], q3 = p[3], q4 = p[4];
-  // u-line current without emission: momentum q0+q1
-  c4<T> Ju = light_current(vbu, uu, q0 + q1, g);
+  c4<T> uu = spinor_u(K.pl[0], T(0), hel_of(hel, 0));
+  c4<T> vbu = dbar(spinor_v(K.pl[1], T(0), hel_of(hel, 1)));
+  c4<T> ub = dbar(spinor_u(K.pl[2], mt, hel_of(hel, 2)));
+  c4<T> vt = spinor_v(K.pl[3], mt, hel_of(hel, 3));
+  c4<T> eps = polvec(K.pl[4], hel_of(hel, 4), true);
+  const r4<T>* q = K.q;
+  // u-line current without emission
+  c4<T> Ju = light_current(vbu, uu, K.is, g);
   // D1: gluon off the top: ubar (ig eps) S_F(q2+q4) (ig Ju) v
-  r4<double> Qa = q2 + q4;
-  c4<T> r1 = row_prop(row_slash(ub, eps), cast4<T>(Qa), mt);
-  cscale(r1, (T)(-1.0 / (mdot(Qa, Qa) - mt2)) * g);
+  c4<T> r1 = row_prop(row_slash(ub, eps), q[2] + q[4], mt);
+  cscale(r1, -g * K.ia);
   cx<T> D1 = times_i(spdot(row_slash(r1, Ju), vt)) * g;
   // D2: gluon off the antitop: ubar (ig Ju) S_F(-(q3+q4)) (ig eps) v
-  r4<double> Qb = q3 + q4;
-  c4<T> c1 = col_prop(cast4<T>(Qb), mt, slash_col(eps, vt));
-  cscale(c1, (T)(-1.0 / (mdot(Qb, Qb) - mt2)) * g);
+  c4<T> c1 = col_prop(q[3] + q[4], mt, slash_col(eps, vt));
+  cscale(c1, -g * K.ib);
   cx<T> D2 = times_i(spdot(row_slash(ub, Ju), c1)) * g;
   // D3: gluon off the incoming antiquark (row side of the light line)
-  r4<double> Qc = q1 + q4;
-  c4<T> r3 = row_prop(row_slash(vbu, eps), cast4<T>(Qc), T(0));
-  cscale(r3, (T)(-1.0 / mdot(Qc, Qc)) * g);
-  c4<T> J3 = light_current(r3, uu, q0 + q1 + q4, g);
+  c4<T> r3 = row_prop(row_slash(vbu, eps), q[1] + q[4], T(0));
+  cscale(r3, -g * K.ic);
+  c4<T> J3 = light_current(r3, uu, K.is3, g);
   cx<T> D3 = times_i(spdot(row_slash(ub, J3), vt)) * g;
   // D4: gluon off the incoming quark (column side)
-  r4<double> Qd = q0 + q4;
-  c4<T> c4u = col_prop(cast4<T>(Qd), T(0), slash_col(eps, uu));
-  cscale(c4u, (T)(-1.0 / mdot(Qd, Qd)) * g);
-  c4<T> J4 = light_current(vbu, c4u, q0 + q1 + q4, g);
+  c4<T> c4u = col_prop(q[0] + q[4], T(0), slash_col(eps, uu));
+  cscale(c4u, -g * K.id);
+  c4<T> J4 = light_current(vbu, c4u, K.is3, g);
   cx<T> D4 = times_i(spdot(row_slash(ub, J4), vt)) * g;
   // D5: three-gluon vertex joining the light current, the heavy current and the gluon
   c4<T> Jt = vcurrent(ub, vt);
-  r4<double> Qt = q2 + q3;
-  cscale(Jt, (T)(1.0 / mdot(Qt, Qt)) * g);
-  c4<T> W = vvv(Ju, Jt, cast4<T>(-(q0 + q1)), cast4<T>(-Qt));
+  cscale(Jt, g * K.it);
+  c4<T> W = vvv(Ju, Jt, -(q[0] + q[1]), -(q[2] + q[3]));
   cx<T> D5 = cdot(W, eps) * g;
   const T h = T(0.5), hn = (T)(-1.0 / 6.0);
   cx<T> iD5 = times_i(D5);
@@ -427,16 +473,40 @@ ME_HD void amp_uu_ttg(const r4<double>* p, int hel, const Couplings& cp, cx<T>* 
 }
 
 // ----------------------------------------------------------------------------
+template <int PID, typename T> struct KinOf;
+template <typename T> struct KinOf<P_EE_UU, T> { using type = KinEE<T>; };
+template <typename T> struct KinOf<P_EE_UUG, T> { using type = KinEE<T>; };
+template <typename T> struct KinOf<P_GG_TT, T> { using type = KinTT<T, 2>; };
+template <typename T> struct KinOf<P_GG_TTG, T> { using type = KinTT<T, 3>; };
+template <typename T> struct KinOf<P_GG_TTGG, T> { using type = KinTT<T, 4>; };
+template <typename T> struct KinOf<P_UU_TT, T> { using type = KinUU<T>; };
+template <typename T> struct KinOf<P_UU_TTG, T> { using type = KinUU<T>; };
+template <int PID, typename T> using Kin = typename KinOf<PID, T>::type;
+
+// helicity-independent per-event kinematics
 template <int PID, typename T>
-ME_HD void amplitude(const r4<double>* p, int hel, const Couplings& cp, cx<T>* A,
-                                          const c4<T>* eps_override = nullptr, int ov_leg = -1) {
-  if constexpr (PID == P_EE_UU) amp_ee_uu<T>(p, hel, cp, A);
-  else if constexpr (PID == P_EE_UUG) amp_ee_uug<T>(p, hel, cp, A);
-  else if constexpr (PID == P_GG_TT) amp_tt2_fast<T>(p, hel, cp, eps_override, ov_leg, A);
-  else if constexpr (PID == P_GG_TTG) amp_tt3_fast<T>(p, hel, cp, A);
-  else if constexpr (PID == P_GG_TTGG) amp_ttng<T, 4>(p, hel, cp, eps_override, ov_leg, A);
-  else if constexpr (PID == P_UU_TT) amp_uu_tt<T>(p, hel, cp, A);
-  else if constexpr (PID == P_UU_TTG) amp_uu_ttg<T>(p, hel, cp, A);
+ME_HD Kin<PID, T> prepare(const r4<double>* p, const Couplings& cp) {
+  if constexpr (PID == P_EE_UU) return prep_ee<T, 4>(p);
+  else if constexpr (PID == P_EE_UUG) return prep_ee<T, 5>(p);
+  else if constexpr (PID == P_GG_TT) return prep_tt<T, 2>(p, cp);
+  else if constexpr (PID == P_GG_TTG) return prep_tt<T, 3>(p, cp);
+  else if constexpr (PID == P_GG_TTGG) return prep_tt<T, 4>(p, cp);
+  else if constexpr (PID == P_UU_TT) return prep_uu<T, 4>(p, cp);
+  else return prep_uu<T, 5>(p, cp);
+}
+
+// partial amplitudes of one helicity; `eps_override` replaces the polarisation of gluon
+// leg `ov_leg` (g g -> t tbar only: the spin-correlated Born)
+template <int PID, typename T>
+ME_HD void amplitude(const Kin<PID, T>& K, int hel, const Couplings& cp, cx<T>* A,
+                     const c4<T>* eps_override = nullptr, int ov_leg = -1) {
+  if constexpr (PID == P_EE_UU) amp_ee_uu<T>(K, hel, cp, A);
+  else if constexpr (PID == P_EE_UUG) amp_ee_uug<T>(K, hel, cp, A);
+  else if constexpr (PID == P_GG_TT) amp_tt2_fast<T>(K, hel, cp, eps_override, ov_leg, A);
+  else if constexpr (PID == P_GG_TTG) amp_tt3_fast<T>(K, hel, cp, A);
+  else if constexpr (PID == P_GG_TTGG) amp_ttng<T, 4>(K, hel, cp, A);
+  else if constexpr (PID == P_UU_TT) amp_uu_tt<T>(K, hel, cp, A);
+  else amp_uu_ttg<T>(K, hel, cp, A);
 }
 
 }  // namespace me
