@@ -126,6 +126,94 @@ def cpu_baseline(points_per_worker: int = 8192, max_workers: int = 8):
                       f"processes x {points_per_worker} points, FP64 numpy oracle, {wall:.1f} s wall"}
 
 
+def reduce_replicas(ms: float, events: float, dist=None, device: str = "cpu"):
+    """Replicas (one process per GPU, independent points): the job's time is the slowest
+    rank's, its work the sum over ranks.  No collective touches the data path."""
+    if dist is None:
+        return ms, events
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    e = torch.tensor([events], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(e, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(e.item())
+
+
+SERVE_KIND = {"ee_uu": "born", "ee_uug": "real_subtracted", "gg_tt": "born", "gg_ttg": "real_subtracted",
+              "gg_ttgg": "born", "uu_ttg": "real_subtracted"}
+
+
+def serving_metrics(me, n_requests: int = 200, load: float = 0.9, seed: int = 7, device: int = 0):
+    """Served mixed stream: Poisson arrivals (scaled to `load` x the measured capacity),
+    sizes log-uniform in [256, 65536], processes uniform; latency submit -> completion.
+    Compared with the plain FP64 path run one batch at a time on the same arrivals."""
+    import synth
+    reqs = synth.mixed_stream(n_requests, seed)
+    data = [synth.flat_points(r["process"], r["n"], r["seed"]) for r in reqs]
+    total = sum(r["n"] for r in reqs)
+    srv = me.Server(device=device, n_slots=4, precision=me.ME_PREC_MIXED)
+    for proc in SERVE_KIND:  # warm-up: handle creation and lane-layout tuning per slot
+        b = synth.flat_points(proc, 4096, 99)
+        ts = [srv.submit(proc, SERVE_KIND[proc], b.p) for _ in range(4)]
+        for t in ts:
+            srv.poll(t)
+    t0 = time.perf_counter()
+    ts = [srv.submit(r["process"], SERVE_KIND[r["process"]], d.p, d.wgt) for r, d in zip(reqs, data)]
+    for t in ts:
+        srv.poll(t)
+    capacity = total / (time.perf_counter() - t0)
+    rate = load * capacity / (total / n_requests)  # requests per second
+    arrivals = [r["arrival"] / rate for r in reqs]
+    lat = [0.0] * n_requests
+    tickets = [None] * n_requests
+    done = threading.Event()
+
+    def poller():
+        for i in range(n_requests):
+            while tickets[i] is None:
+                time.sleep(1e-4)
+            res = srv.poll(tickets[i])
+            lat[i] = res["t_total_us"] * 1e-3
+        done.set()
+
+    th = threading.Thread(target=poller)
+    th.start()
+    start = time.perf_counter()
+    for i, (r, d) in enumerate(zip(reqs, data)):
+        while time.perf_counter() - start < arrivals[i]:
+            time.sleep(5e-5)
+        tickets[i] = srv.submit(r["process"], SERVE_KIND[r["process"]], d.p, d.wgt)
+    done.wait()
+    th.join()
+    makespan = time.perf_counter() - start
+    srv.close()
+    # plain FP64 path, one batch at a time, same arrival times (queueing on the host clock)
+    hs = {p: me.Handle(p, precision=me.ME_PREC_FP64, device=device) for p in SERVE_KIND}
+    for p, h in hs.items():
+        (h.born if SERVE_KIND[p] == "born" else h.real_subtracted)(synth.flat_points(p, 1024, 98).p)
+    clock = 0.0
+    lat64 = []
+    busy = 0.0
+    for i, (r, d) in enumerate(zip(reqs, data)):
+        h = hs[r["process"]]
+        f = h.born if SERVE_KIND[r["process"]] == "born" else h.real_subtracted
+        t1 = time.perf_counter()
+        f(d.p, d.wgt)
+        svc = time.perf_counter() - t1
+        busy += svc
+        begin = max(clock, arrivals[i])
+        clock = begin + svc
+        lat64.append(1e3 * (clock - arrivals[i]))
+    for h in hs.values():
+        h.close()
+    return {"requests": n_requests, "points": total, "offered_load": load,
+            "capacity_events_per_s": capacity, "events_per_s": total / makespan,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "fp64_per_batch": {"events_per_s_busy": total / busy,
+                               "p50_ms": float(np.percentile(lat64, 50)),
+                               "p99_ms": float(np.percentile(lat64, 99))}}
+
+
 def run_reference(args):
     """The oracle as the reference arm: bounded samples of the workload on host cores."""
     rank = int(os.environ.get("RANK", "0"))
@@ -165,6 +253,7 @@ def main():
     ap.add_argument("--n", type=int, default=N_POINTS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-serving", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -224,11 +313,8 @@ def main():
     t_main, t_resc, t_red, calls = h.stage_times()
     h.enable_stage_timers(False)
     rescued = h.last_rescued()
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * n * args.steps / (ms * 1e-3)
+    ms, events = reduce_replicas(ms, float(n * args.steps), dist, device="cuda")
+    value = events / (ms * 1e-3)
 
     # plain float64 GPU path on the same batch
     h64 = me.Handle(PROCESS, precision=me.ME_PREC_FP64, device=local)
@@ -260,6 +346,9 @@ def main():
     h2d = n * 4 * 5 * 8 + n * 8
     d2h = n * 8
 
+    serve = None
+    if rank == 0 and not args.no_serving:
+        serve = serving_metrics(me, device=local)
     if rank != 0:
         return
     ops = mebuild.op_counts()
@@ -290,6 +379,7 @@ def main():
         "gpu_launches": 4 * args.steps,
         "clocks": clocks,
         "cpu_baseline": cpu,
+        "serving": serve,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:

@@ -62,8 +62,7 @@ extern "C" {
  *                    measured float32 error per unit of (|R S| + |CT|) (99.9th
  *                    percentile on flat points of the three real processes)
  *   device           CUDA device ordinal the handle runs on
- *   lanes_per_event  lanes sharing one point (1, 2, 4, 8 or 16; 0 = autotune); 32 is
- *                    the tensor-core colour-sum kernel of gg_ttgg in mixed precision
+ *   lanes_per_event  lanes sharing one point (1, 2, 4, 8 or 16; 0 = autotune)
  */
 typedef struct me_params {
   uint32_t version;

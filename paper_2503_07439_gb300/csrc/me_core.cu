@@ -430,10 +430,8 @@ static int choose_lpe(me_handle* h, int kind, bool fp64, const LaunchArgs& a) {
   int& slot = h->lpe[kind][fp64 ? 1 : 0];
   if (h->prm.lanes_per_event) return slot = h->prm.lanes_per_event;
   if (slot) return slot;
-  // g g -> t tbar g g in float32 also has the tensor-core colour-sum kernel (lpe 32)
-  const bool tc = h->proc->pid == P_GG_TTGG && kind == K_TREE && !fp64;
-  const int cands[6] = {1, 2, 4, 8, 16, 32};
-  const int ncand = tc ? 6 : 5;
+  const int cands[5] = {1, 2, 4, 8, 16};
+  const int ncand = 5;
   LaunchArgs t = a;
   t.groups = std::min<long>(a.groups, 1L << 15);
   t.kp.flag_unstable = 0;
@@ -494,8 +492,7 @@ int me_init(const char* process, const me_params* params, me_handle** out) {
       !(params->alpha_s > 0) || !(params->alpha > 0) || !(params->mt > 0))
     return fail(ME_ERR_ARG, "me_init: parameter out of range");
   const int l = params->lanes_per_event;
-  if (l != 0 && l != 1 && l != 2 && l != 4 && l != 8 && l != 16 && l != 32)
-    return fail(ME_ERR_ARG, "me_init: lanes_per_event");
+  if (l != 0 && l != 1 && l != 2 && l != 4 && l != 8 && l != 16) return fail(ME_ERR_ARG, "me_init: lanes_per_event");
   const ProcDesc* pd = nullptr;
   for (const auto& d : kProcs)
     if (std::strcmp(d.name, process) == 0) pd = &d;

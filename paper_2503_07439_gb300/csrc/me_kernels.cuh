@@ -100,64 +100,68 @@ __device__ __forceinline__ void load_event(const double* __restrict__ p, long n,
 }
 
 // ---------------------------------------------------------------- tree |M|^2
-// out[i] = wgt[i] * |M|^2(p_i) * nlo_factor.  `idx` (optional): event list to process
-// (the FP64 rescue of flagged points); `count` then holds its length on the device.
+// out[i] = wgt[i] * |M|^2(p_i) * nlo_factor.  `idx` (optional): event list to process;
+// `count` then holds its length on the device.
+// g g -> t tbar g g in float32 does its 24-flow colour sums on the tensor cores: each
+// lane holds one (event, helicity) row, the warp contracts its 32 rows with the colour
+// matrix in one bf16 mma sequence (me_tc.cuh).  All lanes then run the same number of
+// helicity iterations; lanes past the end of the batch contribute zero rows.
 template <int PID, typename T, int LPE>
-__global__ void __launch_bounds__(128, ME_MINB) k_tree(const double* __restrict__ p, const double* __restrict__ wgt, long n,
-                                              double* __restrict__ out, KParams kp, const int* __restrict__ idx,
-                                              const int* __restrict__ count) {
+__global__ void __launch_bounds__(128, ME_MINB) k_tree(const double* __restrict__ p, const double* __restrict__ wgt,
+                                                       long n, double* __restrict__ out, KParams kp,
+                                                       const int* __restrict__ idx, const int* __restrict__ count) {
   constexpr int NEXT = Proc<PID>::NEXT, NHEL = Proc<PID>::NHEL, NF = Proc<PID>::NFLOW;
+  constexpr bool TC = (PID == P_GG_TTGG) && std::is_same<T, float>::value;
   const long gid = ((long)blockIdx.x * blockDim.x + threadIdx.x) / LPE;
   const int lane = threadIdx.x % LPE;
   const long nev = idx ? (long)*count : n;
-  if (gid >= nev) return;
-  const long ev = idx ? (long)idx[gid] : gid;
-  r4<double> k[NEXT];
-  load_event<NEXT>(p, n, ev, k);
-  const Kin<PID, T> K = prepare<PID, T>(k, kp.cp);
-  T acc = T(0);
-  for (int h = lane; h < NHEL; h += LPE) {
-    cx<T> J[NF];
-    amplitude<PID, T>(K, h, kp.cp, J);
-    acc += colour_sum<PID, T>(kp.tab, J);
-  }
-  double tot = (double)group_sum<LPE>(acc, group_mask<LPE>());
-  if (lane == 0) {
-    const double w = wgt ? wgt[ev] : 1.0;
-    out[ev] = w * tot * kp.avg_inv * kp.nlo_factor;
-  }
-}
-
-// ---------------------------------------------------------------- tree |M|^2, colour sum on tensor cores
-// One warp per event, lanes <-> helicities (64 helicities in two passes of 32); the
-// 24-flow colour sum of each pass is one warp-wide bf16 tensor-core contraction
-// (me_tc.cuh).  float32 amplitudes; g g -> t tbar g g only.
-template <int PID>
-__global__ void __launch_bounds__(128, ME_MINB) k_tree_tc(const double* __restrict__ p, const double* __restrict__ wgt,
-                                                          long n, double* __restrict__ out, KParams kp,
-                                                          const int* __restrict__ idx, const int* __restrict__ count) {
-  static_assert(Proc<PID>::NFLOW == TC_NF && Proc<PID>::NHEL % 32 == 0, "tensor-core colour sum layout");
-  constexpr int NEXT = Proc<PID>::NEXT, NHEL = Proc<PID>::NHEL;
-  __shared__ __align__(16) unsigned char smem[4 * TC_SMEM_PER_WARP];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long gid = (long)blockIdx.x * (blockDim.x >> 5) + warp;
-  const long nev = idx ? (long)*count : n;
-  if (gid >= nev) return;  // uniform over the warp
-  const long ev = idx ? (long)idx[gid] : gid;
-  r4<double> k[NEXT];
-  load_event<NEXT>(p, n, ev, k);
-  const TcColourB cb = tc_load_colour(kp.tab->C[PID]);
-  const Kin<PID, float> K = prepare<PID, float>(k, kp.cp);
-  float acc = 0.0f;
-  for (int h = lane; h < NHEL; h += 32) {
-    cx<float> J[TC_NF];
-    amplitude<PID, float>(K, h, kp.cp, J);
-    acc += tc_colour_sum(J, cb, smem + warp * TC_SMEM_PER_WARP);
-  }
-  const double tot = (double)group_sum<32>(acc, 0xffffffffu);
-  if (lane == 0) {
-    const double w = wgt ? wgt[ev] : 1.0;
-    out[ev] = w * tot * kp.avg_inv * kp.nlo_factor;
+  if constexpr (!TC) {
+    if (gid >= nev) return;
+    const long ev = idx ? (long)idx[gid] : gid;
+    r4<double> k[NEXT];
+    load_event<NEXT>(p, n, ev, k);
+    const Kin<PID, T> K = prepare<PID, T>(k, kp.cp);
+    T acc = T(0);
+    for (int h = lane; h < NHEL; h += LPE) {
+      cx<T> J[NF];
+      amplitude<PID, T>(K, h, kp.cp, J);
+      acc += colour_sum<PID, T>(kp.tab, J);
+    }
+    const double tot = (double)group_sum<LPE>(acc, group_mask<LPE>());
+    if (lane == 0) {
+      const double w = wgt ? wgt[ev] : 1.0;
+      out[ev] = w * tot * kp.avg_inv * kp.nlo_factor;
+    }
+  } else {
+    __shared__ __align__(16) unsigned char smem[4 * TC_SMEM_PER_WARP];
+    unsigned char* wsm = smem + (threadIdx.x >> 5) * TC_SMEM_PER_WARP;
+    const bool active = gid < nev;
+    const long ev = active ? (idx ? (long)idx[gid] : gid) : 0;
+    r4<double> k[NEXT];
+    if (active) {
+      load_event<NEXT>(p, n, ev, k);
+    } else {
+#pragma unroll
+      for (int l = 0; l < NEXT; ++l) k[l] = r4<double>{1.0, 0.0, 0.0, 0.0};
+    }
+    const TcColourB cb = tc_load_colour(kp.tab->C[PID]);
+    const Kin<PID, float> K = prepare<PID, float>(k, kp.cp);
+    float acc = 0.0f;
+    for (int it = 0; it < NHEL / LPE; ++it) {
+      cx<float> J[NF];
+      if (active) {
+        amplitude<PID, float>(K, lane + it * LPE, kp.cp, J);
+      } else {
+#pragma unroll
+        for (int f = 0; f < NF; ++f) J[f] = cx<float>{0.0f, 0.0f};
+      }
+      acc += tc_colour_sum(J, cb, wsm);
+    }
+    const double tot = (double)group_sum<LPE>(acc, group_mask<LPE>());
+    if (active && lane == 0) {
+      const double w = wgt ? wgt[ev] : 1.0;
+      out[ev] = w * tot * kp.avg_inv * kp.nlo_factor;
+    }
   }
 }
 
@@ -470,14 +474,6 @@ struct LaunchArgs {
 };
 enum KernelKind : int { K_TREE = 0, K_REAL = 1 };
 
-template <int PID>
-cudaError_t launch_tree_tc(const LaunchArgs& a, cudaStream_t st) {
-  const long blocks = (a.groups + 3) / 4;
-  if (blocks <= 0) return cudaSuccess;
-  k_tree_tc<PID><<<(unsigned)blocks, 128, 0, st>>>(a.p, a.wgt, a.n, a.out, a.kp, a.idx, a.count);
-  return cudaGetLastError();
-}
-
 template <int PID, typename T, int LPE>
 cudaError_t launch_one(int kind, const LaunchArgs& a, cudaStream_t st) {
   const int threads = 128;
@@ -496,8 +492,7 @@ cudaError_t launch_one(int kind, const LaunchArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// per-process launchers (one translation unit each); lpe in {1, 2, 4, 8, 16}; for
-// g g -> t tbar g g in float32, lpe 32 selects the tensor-core colour-sum kernel
+// per-process launchers (one translation unit each); lpe in {1, 2, 4, 8, 16}
 cudaError_t launch_ee(int pid, int kind, bool fp64, int lpe, const LaunchArgs& a, cudaStream_t st);
 cudaError_t launch_gg(int pid, int kind, bool fp64, int lpe, const LaunchArgs& a, cudaStream_t st);
 cudaError_t launch_ggg(int pid, int kind, bool fp64, int lpe, const LaunchArgs& a, cudaStream_t st);
