@@ -40,6 +40,26 @@ UNIT = "events/s"
 WORKLOAD = ("gg->ttg real-emission minus FKS soft/collinear counterterms, sqrt(s)=1 TeV, m_t=173, "
             "2^20 flat massive-RAMBO points, mixed precision (fp32 amplitudes + fp64 rescue)")
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+# launches per step: main kernel (+ FP64 rescue for the subtracted real) + 2 reduction kernels
+WORKLOADS = {
+    "c2": {"calls": [("gg_ttg", "real_subtracted", SEED)], "n": N_POINTS, "metric": METRIC, "workload": WORKLOAD,
+           "kernel": "k_real_sub<gg_ttg, float>", "launches": 4, "l2": "inputs 168 MB per batch > 129 MB L2 (no flush)"},
+    "c0": {"calls": [("ee_uu", "nbody_nlo", 1), ("ee_uug", "real_subtracted", 2)], "n": 65536,
+           "metric": "e+e- -> u ubar NLO events/s (n-body + real-minus-counterterm, 1 GB300)",
+           "workload": "e+e- -> u ubar (g) at sqrt(s)=100 GeV: 65536 Born points (n-body NLO weight) + 65536 "
+                       "real points (FKS final-state sectors), mixed precision",
+           "kernel": "k_tree<ee_uu, float>", "launches": 7, "l2": "inputs 15 MB (< L2; compute-bound kernels)"},
+    "c1": {"calls": [("gg_tt", "born", 3)], "n": N_POINTS,
+           "metric": "gg -> t tbar LO events/s (1 GB300)",
+           "workload": "gg -> t tbar LO, sqrt(s_hat) ~ U[400,2000] GeV, 2^20 points, float32 amplitudes",
+           "kernel": "k_tree<gg_tt, float>", "launches": 3, "l2": "inputs 134 MB per batch > 129 MB L2 (no flush)"},
+    "c3": {"calls": [("gg_ttgg", "born", 6)], "n": 1 << 18,
+           "metric": "gg -> t tbar g g tree events/s (tensor-core colour sum, 1 GB300)",
+           "workload": "gg -> t tbar g g tree at sqrt(s)=2 TeV, 2^18 flat massive-RAMBO points, float32 "
+                       "amplitudes, 24-flow colour sum on tensor cores (bf16 x3 split, f32 accumulate)",
+           "kernel": "k_tree<gg_ttgg, float> (mma.sync bf16)", "launches": 3,
+           "l2": "inputs 50 MB (< L2; compute-bound kernel)"},
+}
 
 
 def _peaks():
@@ -254,6 +274,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--workload", default="c2", choices=["c0", "c1", "c2", "c3"],
+                    help="c2 (default): gg->ttg real-minus-CT; c0: e+e- NLO (n-body + real-minus-CT); "
+                         "c1: gg->tt LO; c3: gg->ttgg tree with the tensor-core colour sum")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -265,7 +288,7 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     # CPU baseline first (spawned pool, before any CUDA work in this process)
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "c2":
         cpu = cpu_baseline()
 
     import torch
@@ -280,24 +303,42 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    n = args.n
-    b = synth.flat_points(PROCESS, n, SEED, first_point=rank * n)
-    p_dev = torch.from_numpy(b.p).cuda()
-    w_dev = torch.from_numpy(b.wgt).cuda()
-    out_dev = torch.empty(n, dtype=torch.float64, device="cuda")
+    wl = WORKLOADS[args.workload]
+    n = args.n if args.workload == "c2" else wl["n"]
+    calls = []  # (process, entry point, batch)
+    for proc, entry, seed in wl["calls"]:
+        if proc == "gg_tt":
+            bb = synth.gg_tt_scan(n, seed, first_point=rank * n)
+        else:
+            bb = synth.flat_points(proc, n, seed, first_point=rank * n)
+        calls.append((proc, entry, bb))
     stream = torch.cuda.Stream()
-    h = me.Handle(PROCESS, precision=me.ME_PREC_MIXED, device=local)
-    h.set_stream(stream.cuda_stream)
+
+    def make(prec):
+        hs = []
+        for proc, entry, bb in calls:
+            hh = me.Handle(proc, precision=prec, device=local)
+            hh.set_stream(stream.cuda_stream)
+            hs.append((hh, getattr(hh, entry), torch.from_numpy(bb.p).cuda(), torch.from_numpy(bb.wgt).cuda(),
+                       torch.empty(n, dtype=torch.float64, device="cuda")))
+        return hs
+
+    handles = make(me.ME_PREC_MIXED)
+
+    def step(hs):
+        for hh, f, pd, wd, od in hs:
+            f(pd, wd, od)
 
     def barrier():
         if dist is not None:
             dist.barrier()
 
     for _ in range(warmup):
-        h.real_subtracted(p_dev, w_dev, out_dev)
+        step(handles)
     torch.cuda.synchronize()
-    h.stage_times()
-    h.enable_stage_timers(True)
+    for hh, *_ in handles:
+        hh.stage_times()
+        hh.enable_stage_timers(True)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     with Clocks(local) as clk:
@@ -305,78 +346,88 @@ def main():
         torch.cuda.synchronize()
         e0.record(stream)
         for _ in range(args.steps):
-            h.real_subtracted(p_dev, w_dev, out_dev)
+            step(handles)
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
     ms = e0.elapsed_time(e1)
-    t_main, t_resc, t_red, calls = h.stage_times()
-    h.enable_stage_timers(False)
-    rescued = h.last_rescued()
+    # the dominant kernel is the first call's main kernel
+    stages = [hh.stage_times() for hh, *_ in handles]
+    t_main, t_resc, t_red, ncalls = stages[0]
+    for hh, *_ in handles:
+        hh.enable_stage_timers(False)
+    rescued = sum(hh.last_rescued() for hh, *_ in handles)
     ms, events = reduce_replicas(ms, float(n * args.steps), dist, device="cuda")
     value = events / (ms * 1e-3)
 
-    # plain float64 GPU path on the same batch
-    h64 = me.Handle(PROCESS, precision=me.ME_PREC_FP64, device=local)
-    h64.set_stream(stream.cuda_stream)
-    h64.real_subtracted(p_dev, w_dev, out_dev)
+    # plain float64 GPU path on the same batches
+    h64 = make(me.ME_PREC_FP64)
+    step(h64)
     torch.cuda.synchronize()
     f0 = torch.cuda.Event(enable_timing=True)
     f1 = torch.cuda.Event(enable_timing=True)
     f0.record(stream)
     for _ in range(args.fp64_steps):
-        h64.real_subtracted(p_dev, w_dev, out_dev)
+        step(h64)
     f1.record(stream)
     torch.cuda.synchronize()
     fp64_ms = f0.elapsed_time(f1) / args.fp64_steps
     fp64_value = n / (fp64_ms * 1e-3)
 
     # end to end through the C ABI with pinned host buffers (copies inside the timed region)
-    p_host = torch.from_numpy(b.p).pin_memory()
-    w_host = torch.from_numpy(b.wgt).pin_memory()
-    out_host = torch.empty(n, dtype=torch.float64).pin_memory()
-    h.real_subtracted(p_host.numpy(), w_host.numpy(), out_host.numpy())
+    hosts = []
+    for (proc, entry, bb), (hh, f, *_rest) in zip(calls, handles):
+        hh.set_stream(None)
+        hosts.append((f, torch.from_numpy(bb.p).pin_memory(), torch.from_numpy(bb.wgt).pin_memory(),
+                      torch.empty(n, dtype=torch.float64).pin_memory()))
+
+    def host_step():
+        for f, ph, wh, oh in hosts:
+            f(ph.numpy(), wh.numpy(), oh.numpy())
+
+    host_step()
     barrier()
     t0 = time.perf_counter()
     e2e_steps = max(1, args.steps // 2)
     for _ in range(e2e_steps):
-        h.real_subtracted(p_host.numpy(), w_host.numpy(), out_host.numpy())
+        host_step()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     barrier()
-    h2d = n * 4 * 5 * 8 + n * 8
-    d2h = n * 8
+    h2d = sum(bb.p.nbytes + bb.wgt.nbytes for _, _, bb in calls)
+    d2h = len(calls) * n * 8
 
     serve = None
-    if rank == 0 and not args.no_serving:
+    if rank == 0 and not args.no_serving and args.workload == "c2":
         serve = serving_metrics(me, device=local)
     if rank != 0:
         return
     ops = mebuild.op_counts()
-    flops_event = ops["real_subtracted_per_event"][PROCESS]
-    main_ms = t_main / max(1, calls)
+    proc0, entry0, _ = calls[0]
+    flops_event = ops["real_subtracted_per_event" if entry0 == "real_subtracted" else "born_per_event"][proc0]
+    main_ms = t_main / max(1, ncalls)
     achieved = flops_event * n / (main_ms * 1e-3) / 1e12
     peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
     clocks = clk.summary()
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": wl["metric"], "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic (seeded Philox + RAMBO phase space)",
-        "config": {"workload": WORKLOAD, "process": PROCESS, "n_points": n, "sqrt_s": 1000.0, "seed": SEED,
-                   "precision": "mixed", "l2": "inputs 168 MB per batch > 129 MB L2 (no flush)",
+        "config": {"workload": wl["workload"], "processes": [c[0] for c in calls], "n_points": n,
+                   "precision": "mixed", "l2": wl["l2"],
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "fp64_path": {"value": fp64_value, "unit": UNIT, "ms_per_step": fp64_ms,
                       "mixed_over_fp64": value / world / fp64_value},
         "rescued_per_step": rescued,
-        "stage_ms_per_step": {"main_kernel": main_ms, "rescue_kernel": t_resc / max(1, calls),
-                              "reduction": t_red / max(1, calls)},
+        "stage_ms_per_step": {"main_kernel": main_ms, "rescue_kernel": t_resc / max(1, ncalls),
+                              "reduction": t_red / max(1, ncalls)},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
-                     "kernel": "k_real_sub<gg_ttg, float>",
+                     "kernel": wl["kernel"],
                      "peak_note": "fp32 FMA peak 152 SMs x 128 lanes x 2 flops x 2070 MHz (nominal units and "
                                   "max clock; no measured fp32 peak in MEASURED_PEAKS.json)",
                      "flops_per_event": flops_event},
         "e2e": {"value": n / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": 4 * args.steps,
+        "gpu_launches": wl["launches"] * args.steps,
         "clocks": clocks,
         "cpu_baseline": cpu,
         "serving": serve,

@@ -1,0 +1,123 @@
+"""Full-size workloads, in the launch configuration the benchmark uses: per-point accuracy
+of the mixed-precision path against the FP64 GPU path on every point, FP64 GPU against the
+oracle on sampled points, integrated results, and the e+e- K-factor on the GPU."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import fks
+from oracle import matrix_element as ome
+from oracle.matrix_element import to_points
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+REPORT = {}
+
+
+@pytest.fixture(scope="module")
+def me():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2503_07439_gb300 as m
+    yield m
+    path = os.environ.get("ME_ACCURACY_REPORT")
+    if path:
+        with open(path, "w") as f:
+            json.dump(REPORT, f, indent=1)
+
+
+def _stats(name, got, ref):
+    rel = np.abs(got - ref) / np.abs(ref)
+    st = {"n": int(got.size), "rel_median": float(np.median(rel)), "rel_q999": float(np.quantile(rel, 0.999)),
+          "rel_max": float(rel.max()), "integrated_rel": float(abs(got.sum() - ref.sum()) / abs(ref.sum()))}
+    REPORT[name] = st
+    return st
+
+
+def _dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def test_c0_kfactor_on_gpu(me):
+    """sigma_NLO / sigma_LO = 1 + alpha_s/pi from 65536 Born (n-body NLO weights) and 65536
+    real points (subtracted real), both paths."""
+    rs, alpha, alpha_s = 100.0, 1 / 132.507, 0.118
+    s = rs * rs
+    sig_lo = 4 * math.pi * alpha ** 2 * 3 * (4 / 9) / (3 * s)
+    born = synth.flat_points("ee_uu", 65536, 1)
+    real = synth.flat_points("ee_uug", 65536, 2)
+    for prec in (me.ME_PREC_FP64, me.ME_PREC_MIXED):
+        hb = me.Handle("ee_uu", precision=prec)
+        hr = me.Handle("ee_uug", precision=prec)
+        nb = hb.nbody_nlo(_dev(born.p), _dev(born.wgt)).cpu().numpy() / (2 * s)
+        lo = hb.born(_dev(born.p), _dev(born.wgt)).cpu().numpy() / (2 * s)
+        rw = hr.real_subtracted(_dev(real.p), _dev(real.wgt)).cpu().numpy() / (2 * s)
+        # correlated Born samples: the n-body factor is exact, only real - CT carries MC error
+        ratio = nb.mean() / lo.mean() + rw.mean() / sig_lo
+        err = rw.std() / math.sqrt(rw.size) / sig_lo
+        REPORT[f"c0_kfactor_{'fp64' if prec == me.ME_PREC_FP64 else 'mixed'}"] = {
+            "ratio": float(ratio), "mc_err": float(err), "target": 1 + alpha_s / math.pi}
+        assert abs(ratio - (1 + alpha_s / math.pi)) < 4e-3
+        assert abs(lo.mean() / sig_lo - 1) < 0.02
+
+
+def test_c1_gg_tt_full_batch(me):
+    b = synth.gg_tt_scan(1 << 20, 3)
+    p = _dev(b.p)
+    f64 = me.Handle("gg_tt", precision=me.ME_PREC_FP64).born(p).cpu().numpy()
+    f32 = me.Handle("gg_tt", precision=me.ME_PREC_MIXED).born(p).cpu().numpy()
+    st = _stats("c1_gg_tt_fp32_vs_fp64", f32, f64)
+    assert st["rel_q999"] <= 1e-5 and st["integrated_rel"] <= 1e-6
+    idx = np.random.default_rng(0).choice(b.n, 2000, replace=False)
+    ref = ome.me2("gg_tt", to_points(b.p[:, :, idx]))
+    assert np.max(np.abs(f64[idx] / ref - 1)) <= 1e-12
+
+
+def test_c2_gg_ttg_full_batch(me):
+    b = synth.flat_points("gg_ttg", 1 << 20, 4)
+    p, w = _dev(b.p), _dev(b.wgt)
+    f64 = me.Handle("gg_ttg", precision=me.ME_PREC_FP64).real_subtracted(p, w).cpu().numpy()
+    hm = me.Handle("gg_ttg", precision=me.ME_PREC_MIXED)
+    mix = hm.real_subtracted(p, w).cpu().numpy()
+    st = _stats("c2_gg_ttg_mixed_vs_fp64", mix, f64)
+    st["rescued"] = hm.last_rescued()
+    assert st["rel_q999"] <= 1e-5 and st["integrated_rel"] <= 1e-6
+    idx = np.random.default_rng(1).choice(b.n, 600, replace=False)
+    ref = fks.real_subtracted("gg_ttg", to_points(b.p[:, :, idx])) * b.wgt[idx]
+    _, parts = fks.real_subtracted("gg_ttg", to_points(b.p[:, :, idx]), detail=True)
+    mag = sum(np.abs(q["RS"]) + np.abs(q["RS"] - q["W"]) for q in parts) * b.wgt[idx]
+    assert np.all(np.abs(f64[idx] - ref) <= 1e-12 * mag)
+
+
+def test_c2_approach_points(me):
+    """2^16 points on soft/collinear approach sequences: mixed (with FP64 rescue) equals
+    FP64 to 1e-5 relative wherever FP64 resolves the point."""
+    b, lab = synth.approach_points("gg_ttg", 4096, 5)
+    p = _dev(b.p)
+    f64 = me.Handle("gg_ttg", precision=me.ME_PREC_FP64).real_subtracted(p).cpu().numpy()
+    hm = me.Handle("gg_ttg", precision=me.ME_PREC_MIXED)
+    mix = hm.real_subtracted(p).cpu().numpy()
+    ok = ~((lab["kind"] == 2) & (lab["value"] < 1e-6))  # soft-collinear 1e-8 x 1e-8: beyond FP64
+    st = _stats("c2_approach_mixed_vs_fp64", mix[ok], f64[ok])
+    st["rescued"] = hm.last_rescued()
+    assert st["rel_q999"] <= 1e-5
+    assert hm.last_rescued() >= int(0.9 * b.n)
+
+
+def test_c3_gg_ttgg_full_batch(me):
+    b = synth.flat_points("gg_ttgg", 1 << 18, 6)
+    p = _dev(b.p)
+    f64 = me.Handle("gg_ttgg", precision=me.ME_PREC_FP64).born(p).cpu().numpy()
+    tc = me.Handle("gg_ttgg", precision=me.ME_PREC_MIXED).born(p).cpu().numpy()
+    st = _stats("c3_gg_ttgg_tensorcore_vs_fp64", tc, f64)
+    assert st["rel_q999"] <= 1e-5 and st["integrated_rel"] <= 1e-6
+    idx = np.random.default_rng(2).choice(b.n, 24, replace=False)
+    ref = ome.me2("gg_ttgg", to_points(b.p[:, :, idx]))
+    rel = np.abs(f64[idx] / ref - 1)
+    assert np.mean(rel > 1e-12) <= 0.1 and rel.max() <= 1e-10
