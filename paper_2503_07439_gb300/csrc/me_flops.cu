@@ -5,7 +5,8 @@
 // arithmetic type counts as one operation (a fused multiply-add therefore counts two),
 // sign flips and comparisons count zero.  Momentum sums and propagator denominators,
 // which the kernels keep in float64, are not counted.  The colour sums are counted
-// from their loop structure.  Output: one JSON object with operations per helicity
+// from their loop structure.  Per event, one helicity of each flipped pair (h, -h) is
+// evaluated, as in the kernels.  Output: one JSON object with operations per helicity
 // and per event for every process and entry point.
 #include <cmath>
 #include <cstdio>
@@ -72,9 +73,10 @@ int main() {
   const double pr_ee = prep_ops<P_EE_UU>(p), pr_eeg = prep_ops<P_EE_UUG>(p);
   const double pr_gg = prep_ops<P_GG_TT>(p), pr_ggg = prep_ops<P_GG_TTG>(p);
   const double pr_uu = prep_ops<P_UU_TT>(p), pr_uug = prep_ops<P_UU_TTG>(p);
-  const double real_ee = 32 * h_eeg + pr_eeg + 32 * h_ee + 2 * pr_ee;
-  const double real_gg = 32 * h_ggg + pr_ggg + 16 * (h_gg + quad2) + 16 * h_gg + 16 * (gg_ov + csum_ops(2)) + 3 * pr_gg;
-  const double real_uu = 32 * h_uug + pr_uug + 16 * (h_uu + quad2) + 16 * h_uu + 2 * pr_uu;
+  // one helicity of each flipped pair is evaluated (the sums are doubled)
+  const double real_ee = 16 * h_eeg + pr_eeg + 16 * h_ee + 2 * pr_ee;
+  const double real_gg = 16 * h_ggg + pr_ggg + 8 * (h_gg + quad2) + 8 * h_gg + 8 * (gg_ov + csum_ops(2)) + 3 * pr_gg;
+  const double real_uu = 16 * h_uug + pr_uug + 8 * (h_uu + quad2) + 8 * h_uu + 2 * pr_uu;
   std::printf(
       "{\"per_helicity\": {\"ee_uu\": %.0f, \"ee_uug\": %.0f, \"gg_tt\": %.0f, \"gg_ttg\": %.0f, "
       "\"gg_ttgg\": %.0f, \"uu_tt\": %.0f, \"uu_ttg\": %.0f},\n"
@@ -82,8 +84,8 @@ int main() {
       "\"gg_ttgg\": %.0f, \"uu_tt\": %.0f, \"uu_ttg\": %.0f},\n"
       " \"real_subtracted_per_event\": {\"ee_uug\": %.0f, \"gg_ttg\": %.0f, \"uu_ttg\": %.0f},\n"
       " \"colour_sum_per_event\": {\"gg_ttgg\": %.0f}}\n",
-      h_ee, h_eeg, h_gg, h_ggg, h_gggg, h_uu, h_uug, 16 * h_ee + pr_ee, 32 * h_eeg + pr_eeg, 16 * h_gg + pr_gg,
-      32 * h_ggg + pr_ggg, 64 * h_gggg + prep_ops<P_GG_TTGG>(p), 16 * h_uu + pr_uu, 32 * h_uug + pr_uug, real_ee,
-      real_gg, real_uu, 64 * csum_ops(24));
+      h_ee, h_eeg, h_gg, h_ggg, h_gggg, h_uu, h_uug, 8 * h_ee + pr_ee, 16 * h_eeg + pr_eeg, 8 * h_gg + pr_gg,
+      16 * h_ggg + pr_ggg, 32 * h_gggg + prep_ops<P_GG_TTGG>(p), 8 * h_uu + pr_uu, 16 * h_uug + pr_uug, real_ee,
+      real_gg, real_uu, 32 * csum_ops(24));
   return 0;
 }

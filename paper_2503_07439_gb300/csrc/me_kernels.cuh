@@ -4,7 +4,10 @@
 // so that consecutive events are consecutive addresses; weights are float64 w[n].
 // A group of LPE consecutive lanes handles one event: the lanes split the helicity
 // sum (and, for the subtracted real, the Born-kinematics tasks) and reduce with warp
-// shuffles.  Born, real, soft and collinear terms are evaluated for every point and
+// shuffles.  Helicity sums run over one member of each pair (h, -h) -- the
+// configurations with leg 0 at + -- and are doubled: flipping every helicity leaves the
+// colour-summed squared amplitude (and every colour/spin-correlated one) unchanged for
+// these tree amplitudes with real couplings (pinned against the oracle).  Born, real, soft and collinear terms are evaluated for every point and
 // masked afterwards (Sec. 4.3, Algorithm 2), so a warp never diverges on cuts.
 #pragma once
 #include "me_procs.cuh"
@@ -122,12 +125,12 @@ __global__ void __launch_bounds__(128, ME_MINB) k_tree(const double* __restrict_
     load_event<NEXT>(p, n, ev, k);
     const Kin<PID, T> K = prepare<PID, T>(k, kp.cp);
     T acc = T(0);
-    for (int h = lane; h < NHEL; h += LPE) {
+    for (int t = lane; t < NHEL / 2; t += LPE) {
       cx<T> J[NF];
-      amplitude<PID, T>(K, h, kp.cp, J);
+      amplitude<PID, T>(K, 2 * t + 1, kp.cp, J);
       acc += colour_sum<PID, T>(kp.tab, J);
     }
-    const double tot = (double)group_sum<LPE>(acc, group_mask<LPE>());
+    const double tot = 2.0 * (double)group_sum<LPE>(acc, group_mask<LPE>());
     if (lane == 0) {
       const double w = wgt ? wgt[ev] : 1.0;
       out[ev] = w * tot * kp.avg_inv * kp.nlo_factor;
@@ -147,17 +150,17 @@ __global__ void __launch_bounds__(128, ME_MINB) k_tree(const double* __restrict_
     const TcColourB cb = tc_load_colour(kp.tab->C[PID]);
     const Kin<PID, float> K = prepare<PID, float>(k, kp.cp);
     float acc = 0.0f;
-    for (int it = 0; it < NHEL / LPE; ++it) {
+    for (int it = 0; it < NHEL / 2 / LPE; ++it) {
       cx<float> J[NF];
       if (active) {
-        amplitude<PID, float>(K, lane + it * LPE, kp.cp, J);
+        amplitude<PID, float>(K, 2 * (lane + it * LPE) + 1, kp.cp, J);
       } else {
 #pragma unroll
         for (int f = 0; f < NF; ++f) J[f] = cx<float>{0.0f, 0.0f};
       }
       acc += tc_colour_sum(J, cb, wsm);
     }
-    const double tot = (double)group_sum<LPE>(acc, group_mask<LPE>());
+    const double tot = 2.0 * (double)group_sum<LPE>(acc, group_mask<LPE>());
     if (active && lane == 0) {
       const double w = wgt ? wgt[ev] : 1.0;
       out[ev] = w * tot * kp.avg_inv * kp.nlo_factor;
@@ -308,13 +311,13 @@ __global__ void __launch_bounds__(128, ME_MINB) k_real_sub(const double* __restr
   T accR = T(0);
   {
     const Kin<PID, T> K = prepare<PID, T>(k, kp.cp);
-    for (int h = lane; h < NHEL; h += LPE) {
+    for (int t = lane; t < NHEL / 2; t += LPE) {
       cx<T> J[NF];
-      amplitude<PID, T>(K, h, kp.cp, J);
+      amplitude<PID, T>(K, 2 * t + 1, kp.cp, J);
       accR += colour_sum<PID, T>(kp.tab, J);
     }
   }
-  const double R = (double)group_sum<LPE>(accR, mask) * kp.avg_inv;
+  const double R = 2.0 * (double)group_sum<LPE>(accR, mask) * kp.avg_inv;
 
   double W = 0.0, mag = 0.0;
   bool near = false;
@@ -325,15 +328,15 @@ __global__ void __launch_bounds__(128, ME_MINB) k_real_sub(const double* __restr
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
       const Kin<BPID, T> KB = prepare<BPID, T>(f.born[j], kp.cp);
-      for (int h = lane; h < 16; h += LPE) {
+      for (int t = lane; t < 8; t += LPE) {
         cx<T> J[BNF];
-        amplitude<BPID, T>(KB, h, kp.cp, J);
+        amplitude<BPID, T>(KB, 2 * t + 1, kp.cp, J);
         aB[j] += colour_sum<BPID, T>(kp.tab, J);
       }
     }
     double B[2];
-    B[0] = (double)group_sum<LPE>(aB[0], mask) * kp.born_avg_inv;
-    B[1] = (double)group_sum<LPE>(aB[1], mask) * kp.born_avg_inv;
+    B[0] = 2.0 * (double)group_sum<LPE>(aB[0], mask) * kp.born_avg_inv;
+    B[1] = 2.0 * (double)group_sum<LPE>(aB[1], mask) * kp.born_avg_inv;
     const double th_s = f.xi < kp.xi_cut ? 1.0 : 0.0;
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
@@ -377,37 +380,39 @@ __global__ void __launch_bounds__(128, ME_MINB) k_real_sub(const double* __restr
     T aE = T(0), aS = T(0), aC = T(0), aP[2] = {T(0), T(0)};
     {
       const Kin<BPID, T> KB = prepare<BPID, T>(f.soft, kp.cp);
-      for (int h = lane; h < 16; h += LPE) {
+      for (int t = lane; t < 8; t += LPE) {
         cx<T> J[BNF];
-        amplitude<BPID, T>(KB, h, kp.cp, J);
+        amplitude<BPID, T>(KB, 2 * t + 1, kp.cp, J);
         aE += quad2(Et, J);
         aS += colour_sum<BPID, T>(kp.tab, J);
       }
     }
     {
       const Kin<BPID, T> KB = prepare<BPID, T>(f.coll[0], kp.cp);
-      for (int h = lane; h < 16; h += LPE) {
+      for (int t = lane; t < 8; t += LPE) {
         cx<T> J[BNF];
-        amplitude<BPID, T>(KB, h, kp.cp, J);
+        amplitude<BPID, T>(KB, 2 * t + 1, kp.cp, J);
         aC += colour_sum<BPID, T>(kp.tab, J);
       }
       if constexpr (BPID == P_GG_TT) {
-        for (int r = lane; r < 8; r += LPE) {
+        // polarised gluon 0; gluon 1 fixed to +, legs 2,3 free (the flip covers the rest)
+        for (int r = lane; r < 4; r += LPE) {
           cx<T> J[BNF];
-          amplitude<BPID, T>(KB, r << 1, kp.cp, J, &eperp, 0);
+          amplitude<BPID, T>(KB, 2 | (r << 2), kp.cp, J, &eperp, 0);
           aP[0] += colour_sum<BPID, T>(kp.tab, J);
         }
       }
     }
     if constexpr (BPID == P_GG_TT) {
       const Kin<BPID, T> KB = prepare<BPID, T>(f.coll[1], kp.cp);
-      for (int r = lane; r < 8; r += LPE) {
+      for (int r = lane; r < 4; r += LPE) {  // polarised gluon 1; gluon 0 fixed to +
         cx<T> J[BNF];
-        amplitude<BPID, T>(KB, (r & 1) | ((r >> 1) << 2), kp.cp, J, &eperp, 1);
+        amplitude<BPID, T>(KB, 1 | (r << 2), kp.cp, J, &eperp, 1);
         aP[1] += colour_sum<BPID, T>(kp.tab, J);
       }
     }
-    const double bav = kp.born_avg_inv;
+    // every sum ran over one helicity of each flipped pair (|M(h)|^2 = |M(-h)|^2)
+    const double bav = 2.0 * kp.born_avg_inv;
     const double x2R = -(4.0 * g2 / s) * (double)group_sum<LPE>(aE, mask) * bav;
     const double Bs = (double)group_sum<LPE>(aS, mask) * bav;
     const double Bc = (double)group_sum<LPE>(aC, mask) * bav;

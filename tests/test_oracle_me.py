@@ -195,3 +195,32 @@ def test_bose_symmetry():
         q = p.copy()
         q[:, [0, 1]] = q[:, [1, 0]]
         np.testing.assert_allclose(me.me2(name, q), me.me2(name, p), rtol=1e-12)
+
+
+@pytest.mark.parametrize("name", ["ee_uug", "gg_tt", "gg_ttg", "uu_ttg", "gg_ttgg"])
+def test_helicity_flip_symmetry(name):
+    """Flipping every helicity leaves the colour-summed |M|^2 unchanged (tree amplitudes,
+    real couplings); the same holds for colour correlators and for one gluon polarised
+    along a real transverse vector.  The CUDA path sums one member of each pair and doubles."""
+    d = me.diagrams(name)
+    k = to_points(synth.flat_points(name, 3, 12).p)
+    hel = helicities(d.n)
+    A = d.amplitudes(k, hel, CP.as_dict())
+    idx = {tuple(h): i for i, h in enumerate(hel)}
+    flip = np.array([idx[tuple(-h)] for h in hel])
+    per = np.einsum("nht,ts,nhs->nh", A.conj(), me.gram(name), A).real
+    np.testing.assert_allclose(per, per[:, flip], rtol=1e-11, atol=1e-14 * np.abs(per).max())
+    if name in ("gg_tt",):
+        for kk in range(4):
+            for ll in range(kk, 4):
+                pc = np.einsum("nht,ts,nhs->nh", A.conj(), me.gram(name, kk, ll), A).real
+                np.testing.assert_allclose(pc, pc[:, flip], atol=1e-12 * np.abs(pc).max())
+        ep = np.zeros((3, 4))
+        ep[:, 1], ep[:, 2] = 0.6, 0.8
+        for leg in (0, 1):
+            hl = helicities(4, {leg: 1})
+            Ap = d.amplitudes(k, hl, CP.as_dict(), override={leg: ep})
+            pp = np.einsum("nht,ts,nhs->nh", Ap.conj(), me.gram(name), Ap).real
+            ix = {tuple(np.delete(h, leg)): i for i, h in enumerate(hl)}
+            fl = np.array([ix[tuple(-np.delete(h, leg))] for h in hl])
+            np.testing.assert_allclose(pp, pp[:, fl], atol=1e-12 * np.abs(pp).max())
