@@ -6,8 +6,9 @@
 // sign flips and comparisons count zero.  Momentum sums and propagator denominators,
 // which the kernels keep in float64, are not counted.  The colour sums are counted
 // from their loop structure.  Per event, one helicity of each flipped pair (h, -h) is
-// evaluated, as in the kernels.  Output: one JSON object with operations per helicity
-// and per event for every process and entry point.
+// evaluated, as in the kernels, in helicity blocks.  Output: one JSON object with
+// operations per helicity (per-event Born count over the helicities evaluated) and per
+// event for every process and entry point.
 #include <cmath>
 #include <cstdio>
 
@@ -32,14 +33,15 @@ inline Flop msqrt(Flop a) { ++g_ops; return Flop(std::sqrt(a.v)); }  // found by
 
 using namespace me;
 
+// one helicity block (me_procs.cuh): amplitudes of four helicities plus their colour sums
 template <int PID>
-static double amp_ops(const r4<double>* p, const c4<Flop>* ov = nullptr, int ov_leg = -1, int hel = 5) {
-  cx<Flop> J[24];
+static double block_ops(const r4<double>* p, int hb = 1, const c4<Flop>* ov = nullptr, int ov_leg = -1) {
   const Couplings cp{1.2, 0.3, 173.0};
   const Kin<PID, Flop> K = prepare<PID, Flop>(p, cp);
   g_ops = 0;
-  amplitude<PID, Flop>(K, hel, cp, J, ov, ov_leg);
-  return (double)g_ops;
+  int calls = 0;
+  amplitude_block<PID, Flop>(K, hb, cp, [&](int, const cx<Flop>*) { ++calls; }, ov, ov_leg);
+  return (double)g_ops + calls * (4.0 * Proc<PID>::NFLOW * Proc<PID>::NFLOW + 4.0 * Proc<PID>::NFLOW);
 }
 
 // per-event preparation (reciprocal denominators etc. in the amplitude's type)
@@ -52,40 +54,39 @@ static double prep_ops(const r4<double>* p) {
   return (double)g_ops;
 }
 
-static double csum_ops(int nf) { return 4.0 * nf * nf + 4.0 * nf; }
+// Born |M|^2 of one event: every block of the half helicity set, plus the preparation
+template <int PID>
+static double born_ops(const r4<double>* p) {
+  double t = prep_ops<PID>(p);
+  for (int b = 0; b < n_live_blocks<PID>(); ++b) t += block_ops<PID>(p, live_block_hel<PID>(b));
+  return t;
+}
 
 int main() {
   // a generic massive 2 -> 4 configuration is enough: the count does not depend on values
   r4<double> p[6] = {{1000, 0, 0, 1000},     {1000, 0, 0, -1000}, {600, 100, 200, 300},
                      {700, -150, -100, 200}, {400, 30, -80, -300}, {300, 20, -20, -200}};
-  const double ee = amp_ops<P_EE_UU>(p), eeg = amp_ops<P_EE_UUG>(p);
-  const double gg = amp_ops<P_GG_TT>(p), ggg = amp_ops<P_GG_TTG>(p), gggg = amp_ops<P_GG_TTGG>(p);
-  const double uu = amp_ops<P_UU_TT>(p), uug = amp_ops<P_UU_TTG>(p);
   c4<Flop> e;
   for (int i = 0; i < 4; ++i) e.v[i] = cx<Flop>{Flop(0.5), Flop(0.0)};
-  const double gg_ov = amp_ops<P_GG_TT>(p, &e, 0);
-  // per-helicity cost = amplitude + colour sum
-  const double h_ee = ee + csum_ops(1), h_eeg = eeg + csum_ops(1);
-  const double h_gg = gg + csum_ops(2), h_ggg = ggg + csum_ops(6), h_gggg = gggg + csum_ops(24);
-  const double h_uu = uu + csum_ops(2), h_uug = uug + csum_ops(4);
-  // subtracted real: real helicities + Born tasks (soft with eikonal form, collinear, spin-correlated)
-  const double quad2 = 10.0;
-  const double pr_ee = prep_ops<P_EE_UU>(p), pr_eeg = prep_ops<P_EE_UUG>(p);
-  const double pr_gg = prep_ops<P_GG_TT>(p), pr_ggg = prep_ops<P_GG_TTG>(p);
-  const double pr_uu = prep_ops<P_UU_TT>(p), pr_uug = prep_ops<P_UU_TTG>(p);
-  // one helicity of each flipped pair is evaluated (the sums are doubled)
-  const double real_ee = 16 * h_eeg + pr_eeg + 16 * h_ee + 2 * pr_ee;
-  const double real_gg = 16 * h_ggg + pr_ggg + 8 * (h_gg + quad2) + 8 * h_gg + 8 * (gg_ov + csum_ops(2)) + 3 * pr_gg;
-  const double real_uu = 16 * h_uug + pr_uug + 8 * (h_uu + quad2) + 8 * h_uu + 2 * pr_uu;
-  std::printf(
-      "{\"per_helicity\": {\"ee_uu\": %.0f, \"ee_uug\": %.0f, \"gg_tt\": %.0f, \"gg_ttg\": %.0f, "
-      "\"gg_ttgg\": %.0f, \"uu_tt\": %.0f, \"uu_ttg\": %.0f},\n"
-      " \"born_per_event\": {\"ee_uu\": %.0f, \"ee_uug\": %.0f, \"gg_tt\": %.0f, \"gg_ttg\": %.0f, "
-      "\"gg_ttgg\": %.0f, \"uu_tt\": %.0f, \"uu_ttg\": %.0f},\n"
-      " \"real_subtracted_per_event\": {\"ee_uug\": %.0f, \"gg_ttg\": %.0f, \"uu_ttg\": %.0f},\n"
-      " \"colour_sum_per_event\": {\"gg_ttgg\": %.0f}}\n",
-      h_ee, h_eeg, h_gg, h_ggg, h_gggg, h_uu, h_uug, 8 * h_ee + pr_ee, 16 * h_eeg + pr_eeg, 8 * h_gg + pr_gg,
-      16 * h_ggg + pr_ggg, 32 * h_gggg + prep_ops<P_GG_TTGG>(p), 8 * h_uu + pr_uu, 16 * h_uug + pr_uug, real_ee,
-      real_gg, real_uu, 32 * csum_ops(24));
+  const double quad2 = 10.0;  // J^dagger E J for the 2x2 eikonal-weighted correlator matrix
+  // subtracted real: real blocks + Born tasks (soft with the eikonal form, collinear,
+  // spin-correlated for g g)
+  const double real_ee = born_ops<P_EE_UUG>(p) + 2 * born_ops<P_EE_UU>(p);
+  const double real_gg = born_ops<P_GG_TTG>(p) + born_ops<P_GG_TT>(p) + 8 * quad2 + born_ops<P_GG_TT>(p) +
+                         block_ops<P_GG_TT>(p, 2, &e, 0) + prep_ops<P_GG_TT>(p) + block_ops<P_GG_TT>(p, 1, &e, 1);
+  const double real_uu = born_ops<P_UU_TTG>(p) + born_ops<P_UU_TT>(p) + 8 * quad2 + born_ops<P_UU_TT>(p);
+  const double b[7] = {born_ops<P_EE_UU>(p),  born_ops<P_EE_UUG>(p), born_ops<P_GG_TT>(p), born_ops<P_GG_TTG>(p),
+                       born_ops<P_GG_TTGG>(p), born_ops<P_UU_TT>(p), born_ops<P_UU_TTG>(p)};
+  const int nh[7] = {16, 32, 16, 32, 64, 16, 32};
+  std::printf("{\"per_helicity\": {\"ee_uu\": %.0f, \"ee_uug\": %.0f, \"gg_tt\": %.0f, \"gg_ttg\": %.0f, "
+              "\"gg_ttgg\": %.0f, \"uu_tt\": %.0f, \"uu_ttg\": %.0f},\n",
+              2 * b[0] / nh[0], 2 * b[1] / nh[1], 2 * b[2] / nh[2], 2 * b[3] / nh[3], 2 * b[4] / nh[4],
+              2 * b[5] / nh[5], 2 * b[6] / nh[6]);
+  std::printf(" \"born_per_event\": {\"ee_uu\": %.0f, \"ee_uug\": %.0f, \"gg_tt\": %.0f, \"gg_ttg\": %.0f, "
+              "\"gg_ttgg\": %.0f, \"uu_tt\": %.0f, \"uu_ttg\": %.0f},\n",
+              b[0], b[1], b[2], b[3], b[4], b[5], b[6]);
+  std::printf(" \"real_subtracted_per_event\": {\"ee_uug\": %.0f, \"gg_ttg\": %.0f, \"uu_ttg\": %.0f},\n", real_ee,
+              real_gg, real_uu);
+  std::printf(" \"colour_sum_per_event\": {\"gg_ttgg\": %.0f}}\n", 32 * (4.0 * 24 * 24 + 4.0 * 24));
   return 0;
 }

@@ -3,11 +3,13 @@
 // Layout: momenta are structure-of-arrays float64 p[comp][leg][n] (comp = E,px,py,pz),
 // so that consecutive events are consecutive addresses; weights are float64 w[n].
 // A group of LPE consecutive lanes handles one event: the lanes split the helicity
-// sum (and, for the subtracted real, the Born-kinematics tasks) and reduce with warp
+// blocks (and, for the subtracted real, the Born-kinematics tasks) and reduce with warp
 // shuffles.  Helicity sums run over one member of each pair (h, -h) -- the
 // configurations with leg 0 at + -- and are doubled: flipping every helicity leaves the
 // colour-summed squared amplitude (and every colour/spin-correlated one) unchanged for
-// these tree amplitudes with real couplings (pinned against the oracle).  Born, real, soft and collinear terms are evaluated for every point and
+// these tree amplitudes with real couplings (pinned against the oracle).  A helicity
+// block (me_procs.cuh) is one configuration of the other legs with the four helicities
+// of the heavy pair, evaluated with shared gluon currents and quark-line rows.  Born, real, soft and collinear terms are evaluated for every point and
 // masked afterwards (Sec. 4.3, Algorithm 2), so a warp never diverges on cuts.
 #pragma once
 #include "me_procs.cuh"
@@ -108,12 +110,13 @@ __device__ __forceinline__ void load_event(const double* __restrict__ p, long n,
 // g g -> t tbar g g in float32 does its 24-flow colour sums on the tensor cores: each
 // lane holds one (event, helicity) row, the warp contracts its 32 rows with the colour
 // matrix in one bf16 mma sequence (me_tc.cuh).  All lanes then run the same number of
-// helicity iterations; lanes past the end of the batch contribute zero rows.
+// helicity blocks; lanes past the end of the batch compute a fixed finite configuration
+// whose sums are discarded.
 template <int PID, typename T, int LPE>
 __global__ void __launch_bounds__(128, ME_MINB) k_tree(const double* __restrict__ p, const double* __restrict__ wgt,
                                                        long n, double* __restrict__ out, KParams kp,
                                                        const int* __restrict__ idx, const int* __restrict__ count) {
-  constexpr int NEXT = Proc<PID>::NEXT, NHEL = Proc<PID>::NHEL, NF = Proc<PID>::NFLOW;
+  constexpr int NEXT = Proc<PID>::NEXT;
   constexpr bool TC = (PID == P_GG_TTGG) && std::is_same<T, float>::value;
   const long gid = ((long)blockIdx.x * blockDim.x + threadIdx.x) / LPE;
   const int lane = threadIdx.x % LPE;
@@ -125,11 +128,9 @@ __global__ void __launch_bounds__(128, ME_MINB) k_tree(const double* __restrict_
     load_event<NEXT>(p, n, ev, k);
     const Kin<PID, T> K = prepare<PID, T>(k, kp.cp);
     T acc = T(0);
-    for (int t = lane; t < NHEL / 2; t += LPE) {
-      cx<T> J[NF];
-      amplitude<PID, T>(K, 2 * t + 1, kp.cp, J);
-      acc += colour_sum<PID, T>(kp.tab, J);
-    }
+    for (int b = lane; b < n_live_blocks<PID>(); b += LPE)
+      amplitude_block<PID, T>(K, live_block_hel<PID>(b), kp.cp,
+                              [&](int, const cx<T>* J) { acc += colour_sum<PID, T>(kp.tab, J); });
     const double tot = 2.0 * (double)group_sum<LPE>(acc, group_mask<LPE>());
     if (lane == 0) {
       const double w = wgt ? wgt[ev] : 1.0;
@@ -143,22 +144,24 @@ __global__ void __launch_bounds__(128, ME_MINB) k_tree(const double* __restrict_
     r4<double> k[NEXT];
     if (active) {
       load_event<NEXT>(p, n, ev, k);
-    } else {
+    } else {  // a fixed finite configuration: the lane still joins every warp-wide colour sum
+      const double d[6][4] = {{1000, 0, 0, 1000},     {1000, 0, 0, -1000},     {600, 100, 200, 300},
+                              {700, -150, -100, 200}, {400, 30, -80, -300}, {300, 20, -20, -200}};
 #pragma unroll
-      for (int l = 0; l < NEXT; ++l) k[l] = r4<double>{1.0, 0.0, 0.0, 0.0};
+      for (int l = 0; l < NEXT; ++l) k[l] = r4<double>{d[l][0], d[l][1], d[l][2], d[l][3]};
     }
     const TcColourB cb = tc_load_colour(kp.tab->C[PID]);
     const Kin<PID, float> K = prepare<PID, float>(k, kp.cp);
+    constexpr int NB = n_live_blocks<PID>();
     float acc = 0.0f;
-    for (int it = 0; it < NHEL / 2 / LPE; ++it) {
-      cx<float> J[NF];
-      if (active) {
-        amplitude<PID, float>(K, 2 * (lane + it * LPE) + 1, kp.cp, J);
-      } else {
-#pragma unroll
-        for (int f = 0; f < NF; ++f) J[f] = cx<float>{0.0f, 0.0f};
-      }
-      acc += tc_colour_sum(J, cb, wsm);
+    // every lane runs the same number of blocks (a lane past the last block repeats one
+    // and discards it), so the warp-wide tensor-core calls stay converged
+    for (int it = 0; it < (NB + LPE - 1) / LPE; ++it) {
+      const int b = lane + it * LPE;
+      const float use = (active && b < NB) ? 1.0f : 0.0f;
+      amplitude_block<PID, float>(K, live_block_hel<PID>(b % NB), kp.cp, [&](int, const cx<float>* J) {
+        acc += use * tc_colour_sum(J, cb, wsm);
+      });
     }
     const double tot = 2.0 * (double)group_sum<LPE>(acc, group_mask<LPE>());
     if (active && lane == 0) {
@@ -293,7 +296,7 @@ __global__ void __launch_bounds__(128, ME_MINB) k_real_sub(const double* __restr
                                                   long n, double* __restrict__ out, KParams kp,
                                                   const int* __restrict__ idx, const int* __restrict__ count,
                                                   int* __restrict__ resc_list, int* __restrict__ resc_count) {
-  constexpr int NEXT = Proc<PID>::NEXT, NHEL = Proc<PID>::NHEL, NF = Proc<PID>::NFLOW;
+  constexpr int NEXT = Proc<PID>::NEXT;
   constexpr int BPID = (PID == P_EE_UUG) ? P_EE_UU : (PID == P_GG_TTG ? P_GG_TT : P_UU_TT);
   constexpr int BNF = Proc<BPID>::NFLOW;
   const long gid = ((long)blockIdx.x * blockDim.x + threadIdx.x) / LPE;
@@ -311,11 +314,9 @@ __global__ void __launch_bounds__(128, ME_MINB) k_real_sub(const double* __restr
   T accR = T(0);
   {
     const Kin<PID, T> K = prepare<PID, T>(k, kp.cp);
-    for (int t = lane; t < NHEL / 2; t += LPE) {
-      cx<T> J[NF];
-      amplitude<PID, T>(K, 2 * t + 1, kp.cp, J);
-      accR += colour_sum<PID, T>(kp.tab, J);
-    }
+    for (int b = lane; b < n_live_blocks<PID>(); b += LPE)
+      amplitude_block<PID, T>(K, live_block_hel<PID>(b), kp.cp,
+                              [&](int, const cx<T>* J) { accR += colour_sum<PID, T>(kp.tab, J); });
   }
   const double R = 2.0 * (double)group_sum<LPE>(accR, mask) * kp.avg_inv;
 
@@ -328,11 +329,9 @@ __global__ void __launch_bounds__(128, ME_MINB) k_real_sub(const double* __restr
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
       const Kin<BPID, T> KB = prepare<BPID, T>(f.born[j], kp.cp);
-      for (int t = lane; t < 8; t += LPE) {
-        cx<T> J[BNF];
-        amplitude<BPID, T>(KB, 2 * t + 1, kp.cp, J);
-        aB[j] += colour_sum<BPID, T>(kp.tab, J);
-      }
+      for (int b = lane; b < n_live_blocks<BPID>(); b += LPE)
+        amplitude_block<BPID, T>(KB, live_block_hel<BPID>(b), kp.cp,
+                                 [&](int, const cx<T>* J) { aB[j] += colour_sum<BPID, T>(kp.tab, J); });
     }
     double B[2];
     B[0] = 2.0 * (double)group_sum<LPE>(aB[0], mask) * kp.born_avg_inv;
@@ -380,35 +379,29 @@ __global__ void __launch_bounds__(128, ME_MINB) k_real_sub(const double* __restr
     T aE = T(0), aS = T(0), aC = T(0), aP[2] = {T(0), T(0)};
     {
       const Kin<BPID, T> KB = prepare<BPID, T>(f.soft, kp.cp);
-      for (int t = lane; t < 8; t += LPE) {
-        cx<T> J[BNF];
-        amplitude<BPID, T>(KB, 2 * t + 1, kp.cp, J);
-        aE += quad2(Et, J);
-        aS += colour_sum<BPID, T>(kp.tab, J);
-      }
+      for (int b = lane; b < n_live_blocks<BPID>(); b += LPE)
+        amplitude_block<BPID, T>(KB, live_block_hel<BPID>(b), kp.cp, [&](int, const cx<T>* J) {
+          aE += quad2(Et, J);
+          aS += colour_sum<BPID, T>(kp.tab, J);
+        });
     }
     {
       const Kin<BPID, T> KB = prepare<BPID, T>(f.coll[0], kp.cp);
-      for (int t = lane; t < 8; t += LPE) {
-        cx<T> J[BNF];
-        amplitude<BPID, T>(KB, 2 * t + 1, kp.cp, J);
-        aC += colour_sum<BPID, T>(kp.tab, J);
-      }
+      for (int b = lane; b < n_live_blocks<BPID>(); b += LPE)
+        amplitude_block<BPID, T>(KB, live_block_hel<BPID>(b), kp.cp,
+                                 [&](int, const cx<T>* J) { aC += colour_sum<BPID, T>(kp.tab, J); });
       if constexpr (BPID == P_GG_TT) {
-        // polarised gluon 0; gluon 1 fixed to +, legs 2,3 free (the flip covers the rest)
-        for (int r = lane; r < 4; r += LPE) {
-          cx<T> J[BNF];
-          amplitude<BPID, T>(KB, 2 | (r << 2), kp.cp, J, &eperp, 0);
-          aP[0] += colour_sum<BPID, T>(kp.tab, J);
-        }
+        // polarised gluon 0; gluon 1 fixed to +, the heavy pair free (the flip covers the rest)
+        if (lane == 0)
+          amplitude_block<BPID, T>(
+              KB, 2, kp.cp, [&](int, const cx<T>* J) { aP[0] += colour_sum<BPID, T>(kp.tab, J); }, &eperp, 0);
       }
     }
     if constexpr (BPID == P_GG_TT) {
-      const Kin<BPID, T> KB = prepare<BPID, T>(f.coll[1], kp.cp);
-      for (int r = lane; r < 4; r += LPE) {  // polarised gluon 1; gluon 0 fixed to +
-        cx<T> J[BNF];
-        amplitude<BPID, T>(KB, 1 | (r << 2), kp.cp, J, &eperp, 1);
-        aP[1] += colour_sum<BPID, T>(kp.tab, J);
+      if (lane == 1 % LPE) {  // polarised gluon 1; gluon 0 fixed to +
+        const Kin<BPID, T> KB = prepare<BPID, T>(f.coll[1], kp.cp);
+        amplitude_block<BPID, T>(
+            KB, 1, kp.cp, [&](int, const cx<T>* J) { aP[1] += colour_sum<BPID, T>(kp.tab, J); }, &eperp, 1);
       }
     }
     // every sum ran over one helicity of each flipped pair (|M(h)|^2 = |M(-h)|^2)
@@ -501,6 +494,7 @@ cudaError_t launch_one(int kind, const LaunchArgs& a, cudaStream_t st) {
 cudaError_t launch_ee(int pid, int kind, bool fp64, int lpe, const LaunchArgs& a, cudaStream_t st);
 cudaError_t launch_gg(int pid, int kind, bool fp64, int lpe, const LaunchArgs& a, cudaStream_t st);
 cudaError_t launch_ggg(int pid, int kind, bool fp64, int lpe, const LaunchArgs& a, cudaStream_t st);
+cudaError_t launch_ggg64(int kind, int lpe, const LaunchArgs& a, cudaStream_t st);
 cudaError_t launch_uu(int pid, int kind, bool fp64, int lpe, const LaunchArgs& a, cudaStream_t st);
 
 }  // namespace me
@@ -512,6 +506,15 @@ cudaError_t launch_uu(int pid, int kind, bool fp64, int lpe, const LaunchArgs& a
     case 4: return me::launch_one<PID, T, 4>(kind, a, st);               \
     case 8: return me::launch_one<PID, T, 8>(kind, a, st);               \
     case 16: return me::launch_one<PID, T, 16>(kind, a, st);             \
+    default: return cudaErrorInvalidValue;                               \
+  }
+// g g -> t tbar g g runs at most 8 lanes per event (it has 8 helicity blocks)
+#define ME_LPE_SWITCH8(PID, T)                                           \
+  switch (lpe) {                                                         \
+    case 1: return me::launch_one<PID, T, 1>(kind, a, st);               \
+    case 2: return me::launch_one<PID, T, 2>(kind, a, st);               \
+    case 4: return me::launch_one<PID, T, 4>(kind, a, st);               \
+    case 8: return me::launch_one<PID, T, 8>(kind, a, st);               \
     default: return cudaErrorInvalidValue;                               \
   }
 #define ME_PREC_SWITCH(PID)                      \

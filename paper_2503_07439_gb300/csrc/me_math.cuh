@@ -77,6 +77,11 @@ ME_HD void cadd(c4<T>& acc, const c4<T>& x) {
   for (int i = 0; i < 4; ++i) acc.v[i] = acc.v[i] + x.v[i];
 }
 template <typename T>
+ME_HD void csub(c4<T>& acc, const c4<T>& x) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) acc.v[i] = acc.v[i] - x.v[i];
+}
+template <typename T>
 ME_HD void caxpy(c4<T>& acc, cx<T> a, const c4<T>& x) {
 #pragma unroll
   for (int i = 0; i < 4; ++i) acc.v[i] = acc.v[i] + a * x.v[i];

@@ -309,6 +309,153 @@ ME_HD void amp_tt3_fast(const KinTT<T, 3>& K, int hel, const Couplings& cp, cx<T
 }
 
 // ----------------------------------------------------------------------------
+// Helicity blocks.  A block is one helicity configuration hb of every leg except the
+// heavy pair (legs 2 and 3; their bits in hb are zero) together with the four (t, tbar)
+// helicities hb | (r << 2), r = 0..3.  For t tbar + gluons the gluon currents depend on
+// the gluon helicities only and the quark-line rows ubar(t) ... on the top helicity
+// only, so a block builds the gluon currents once, the rows once per top helicity, and
+// closes each row with both antitop spinors: the partial amplitudes of the four
+// single-helicity evaluations, with the shared pieces computed once.
+// consume(r, A) receives the partial amplitudes of helicity hb | (r << 2).
+
+// g g -> t tbar.  A(01) = ig ubar [J01 + U0 e1] v,  A(10) = ig ubar [-J01 + U1 e0] v.
+template <typename T, class F>
+ME_HD void amp_tt2_block(const KinTT<T, 2>& K, int hb, const Couplings& cp, const c4<T>* ov, int ov_leg,
+                         F&& consume) {
+  const T g = (T)cp.gs, mt = (T)cp.mt;
+  const r4<T> k0 = K.q[0], k1 = K.q[1], kt = K.pl[2];
+  const c4<T> e0 = (ov != nullptr && ov_leg == 0) ? *ov : polvec(K.pl[0], hel_of(hb, 0), false);
+  const c4<T> e1 = (ov != nullptr && ov_leg == 1) ? *ov : polvec(K.pl[1], hel_of(hb, 1), false);
+  c4<T> J01 = vvv(e0, e1, -k0, -k1);
+  cscale(J01, -g * K.ig[3]);
+  const r4<T> Q0 = kt + k0, Q1 = kt + k1;
+  const c4<T> v[2] = {spinor_v(K.pl[3], mt, -1), spinor_v(K.pl[3], mt, 1)};
+#pragma unroll
+  for (int ht = 0; ht < 2; ++ht) {
+    const c4<T> ub = dbar(spinor_u(kt, mt, ht ? 1 : -1));
+    const c4<T> S = row_slash(ub, J01);
+    c4<T> U0 = row_prop(row_slash(ub, e0), Q0, mt);
+    cscale(U0, -g * K.iq[1]);
+    c4<T> U1 = row_prop(row_slash(ub, e1), Q1, mt);
+    cscale(U1, -g * K.iq[2]);
+    c4<T> R0 = row_slash(U0, e1);
+    cadd(R0, S);
+    c4<T> R1 = row_slash(U1, e0);
+    csub(R1, S);
+#pragma unroll
+    for (int hv = 0; hv < 2; ++hv) {
+      cx<T> A[2] = {times_i(spdot(R0, v[hv])) * g, times_i(spdot(R1, v[hv])) * g};
+      consume(ht | (hv << 1), A);
+    }
+  }
+}
+
+// g g -> t tbar g: the three-gluon currents F(012) = F(210), F(021) = F(120),
+// F(102) = F(201) and the pair currents J(xy) are built once per block; per top
+// helicity the row R_s of ordering s collects ubar F(s), U(x) J(yz) and W(xy) e_z.
+template <typename T, class F>
+ME_HD void amp_tt3_block(const KinTT<T, 3>& K, int hb, const Couplings& cp, F&& consume) {
+  const T g = (T)cp.gs, mt = (T)cp.mt;
+  const r4<T> k0 = K.q[0], k1 = K.q[1], k2 = K.q[2], kt = K.pl[2];
+  const c4<T> e0 = polvec(K.pl[0], hel_of(hb, 0), false);
+  const c4<T> e1 = polvec(K.pl[1], hel_of(hb, 1), false);
+  const c4<T> e2 = polvec(K.pl[4], hel_of(hb, 4), true);
+  c4<T> J01 = vvv(e0, e1, -k0, -k1);
+  cscale(J01, -g * K.ig[3]);
+  c4<T> J02 = vvv(e0, e2, -k0, -k2);
+  cscale(J02, -g * K.ig[5]);
+  c4<T> J12 = vvv(e1, e2, -k1, -k2);
+  cscale(J12, -g * K.ig[6]);
+  const T c3 = -g * K.ig[7], c4g = g * g * K.ig[7];
+  c4<T> F0 = vvv(e0, J12, -k0, -(k1 + k2));
+  cadd(F0, vvv(J01, e2, -(k0 + k1), -k2));
+  cscale(F0, c3);
+  caxpy(F0, cx<T>{c4g, T(0)}, vvvv_ordered(e0, e1, e2));
+  c4<T> F1 = vvv(J12, e0, -(k1 + k2), -k0);  // = vvv(e0, -J12, ...) by antisymmetry
+  cadd(F1, vvv(J02, e1, -(k0 + k2), -k1));
+  cscale(F1, c3);
+  caxpy(F1, cx<T>{c4g, T(0)}, vvvv_ordered(e0, e2, e1));
+  c4<T> F2 = vvv(e1, J02, -k1, -(k0 + k2));
+  cadd(F2, vvv(e2, J01, -k2, -(k0 + k1)));    // = vvv(-J01, e2, ...)
+  cscale(F2, c3);
+  caxpy(F2, cx<T>{c4g, T(0)}, vvvv_ordered(e1, e0, e2));
+  const c4<T> v[2] = {spinor_v(K.pl[3], mt, -1), spinor_v(K.pl[3], mt, 1)};
+  const r4<T> Q0 = kt + k0, Q1 = kt + k1, Q2 = kt + k2;
+  const r4<T> Q01 = Q0 + k1, Q02 = Q0 + k2, Q12 = Q1 + k2;
+  const T c01 = -g * K.iq[3], c02 = -g * K.iq[5], c12 = -g * K.iq[6];
+#pragma unroll
+  for (int ht = 0; ht < 2; ++ht) {
+    const c4<T> ub = dbar(spinor_u(kt, mt, ht ? 1 : -1));
+    c4<T> R[6];
+    R[0] = row_slash(ub, F0);  // orderings 012, 021, 102, 120, 201, 210
+    R[1] = row_slash(ub, F1);
+    R[2] = row_slash(ub, F2);
+    R[3] = R[1];
+    R[4] = R[2];
+    R[5] = R[0];
+    const c4<T> S01 = row_slash(ub, J01), S02 = row_slash(ub, J02), S12 = row_slash(ub, J12);
+    {  // first gluon 0: orderings 012, 021
+      c4<T> U = row_prop(row_slash(ub, e0), Q0, mt);
+      cscale(U, -g * K.iq[1]);
+      const c4<T> t = row_slash(U, J12);
+      cadd(R[0], t);
+      csub(R[1], t);
+      c4<T> r = row_slash(U, e1);
+      cadd(r, S01);
+      c4<T> W = row_prop(r, Q01, mt);
+      cscale(W, c01);
+      cadd(R[0], row_slash(W, e2));
+      r = row_slash(U, e2);
+      cadd(r, S02);
+      W = row_prop(r, Q02, mt);
+      cscale(W, c02);
+      cadd(R[1], row_slash(W, e1));
+    }
+    {  // first gluon 1: orderings 102, 120
+      c4<T> U = row_prop(row_slash(ub, e1), Q1, mt);
+      cscale(U, -g * K.iq[2]);
+      const c4<T> t = row_slash(U, J02);
+      cadd(R[2], t);
+      csub(R[3], t);
+      c4<T> r = row_slash(U, e0);
+      csub(r, S01);
+      c4<T> W = row_prop(r, Q01, mt);
+      cscale(W, c01);
+      cadd(R[2], row_slash(W, e2));
+      r = row_slash(U, e2);
+      cadd(r, S12);
+      W = row_prop(r, Q12, mt);
+      cscale(W, c12);
+      cadd(R[3], row_slash(W, e0));
+    }
+    {  // first gluon 2: orderings 201, 210
+      c4<T> U = row_prop(row_slash(ub, e2), Q2, mt);
+      cscale(U, -g * K.iq[4]);
+      const c4<T> t = row_slash(U, J01);
+      cadd(R[4], t);
+      csub(R[5], t);
+      c4<T> r = row_slash(U, e0);
+      csub(r, S02);
+      c4<T> W = row_prop(r, Q02, mt);
+      cscale(W, c02);
+      cadd(R[4], row_slash(W, e1));
+      r = row_slash(U, e1);
+      csub(r, S12);
+      W = row_prop(r, Q12, mt);
+      cscale(W, c12);
+      cadd(R[5], row_slash(W, e0));
+    }
+#pragma unroll
+    for (int hv = 0; hv < 2; ++hv) {
+      cx<T> A[6];
+#pragma unroll
+      for (int f = 0; f < 6; ++f) A[f] = times_i(spdot(R[f], v[hv])) * g;
+      consume(ht | (hv << 1), A);
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
 // e+(0) e-(1) -> u(2) ubar(3) [g(4)].  Photon exchange; charges Q_e = -1, Q_u = 2/3.
 template <typename T>
 struct KinEE {
@@ -507,6 +654,183 @@ ME_HD void amplitude(const Kin<PID, T>& K, int hel, const Couplings& cp, cx<T>* 
   else if constexpr (PID == P_GG_TTGG) amp_ttng<T, 4>(K, hel, cp, A);
   else if constexpr (PID == P_UU_TT) amp_uu_tt<T>(K, hel, cp, A);
   else amp_uu_ttg<T>(K, hel, cp, A);
+}
+
+// g g -> t tbar g g.  The ordered gluon currents are built once per block with the
+// reflection identities: 6 pairs J(xy), x < y; 12 triples J(xyz) (one of each
+// reversed pair); 12 quadruples J(wxyz) with w < z.  Per top helicity, the quark line
+// is extended ordering by ordering, U(w) -> U(wx) -> U(wxy), and the row of ordering
+// wxyz is ubar J(wxyz) + U(w) J(xyz) + U(wx) J(yz) + U(wxy) e_z.  Orderings are
+// numbered lexicographically, as in amp_ttng.
+template <typename T, class F>
+ME_HD void amp_tt4_block(const KinTT<T, 4>& K, int hb, const Couplings& cp, F&& consume) {
+  const T g = (T)cp.gs, mt = (T)cp.mt;
+  constexpr int LEG[4] = {0, 1, 4, 5};
+  c4<T> e[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) e[i] = polvec(K.pl[LEG[i]], hel_of(hb, LEG[i]), LEG[i] >= 2);
+  const r4<T>* q = K.q;
+  // pair currents, index pidx(x, y) for x < y
+  c4<T> J2[6];
+  auto pidx = [](int x, int y) { return x == 0 ? y - 1 : (x == 1 ? y + 1 : 5); };
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = x + 1; y < 4; ++y) {
+      c4<T> J = vvv(e[x], e[y], -q[x], -q[y]);
+      cscale(J, -g * K.ig[(1 << x) | (1 << y)]);
+      J2[pidx(x, y)] = J;
+    }
+  auto j2 = [&](int x, int y) {  // ordered pair current, J(yx) = -J(xy)
+    c4<T> J = J2[x < y ? pidx(x, y) : pidx(y, x)];
+    if (x > y) cscale(J, T(-1));
+    return J;
+  };
+  // triple currents J(xyz) for x < z (J(zyx) = J(xyz)); index tidx = 3 * (missing gluon) + (middle slot)
+  c4<T> J3[12];
+  auto tidx = [](int x, int y, int z) {
+    const int miss = 6 - x - y - z;
+    // the three gluons of the triple in increasing order a < b < c; middle y in {a, b, c}
+    const int a = miss == 0 ? 1 : 0;
+    const int c = miss == 3 ? 2 : 3;
+    return 3 * miss + (y == a ? 0 : (y == c ? 2 : 1));
+  };
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 4; ++y)
+#pragma unroll
+      for (int z = x + 1; z < 4; ++z) {
+        if (y == x || y == z) continue;
+        const int S = (1 << x) | (1 << y) | (1 << z);
+        c4<T> J = vvv(e[x], j2(y, z), -q[x], -(q[y] + q[z]));
+        cadd(J, vvv(j2(x, y), e[z], -(q[x] + q[y]), -q[z]));
+        cscale(J, -g * K.ig[S]);
+        caxpy(J, cx<T>{g * g * K.ig[S], T(0)}, vvvv_ordered(e[x], e[y], e[z]));
+        J3[tidx(x, y, z)] = J;
+      }
+  auto j3 = [&](int x, int y, int z) { return J3[tidx(x, y, z)]; };
+  // quadruple currents J(wxyz) for w < z (J(zyxw) = -J(wxyz)); index by ordering rank
+  c4<T> J4[12];
+  int n4 = 0;
+#pragma unroll
+  for (int w = 0; w < 4; ++w)
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) {
+        if (x == w || y == w || y == x) continue;
+        const int z = 6 - w - x - y;
+        if (z < w) continue;
+        const T c3 = -g * K.ig[15], c4g = g * g * K.ig[15];
+        c4<T> J = vvv(e[w], j3(x, y, z), -q[w], -(q[x] + q[y] + q[z]));
+        cadd(J, vvv(j2(w, x), j2(y, z), -(q[w] + q[x]), -(q[y] + q[z])));
+        cadd(J, vvv(j3(w, x, y), e[z], -(q[w] + q[x] + q[y]), -q[z]));
+        cscale(J, c3);
+        c4<T> V = vvvv_ordered(e[w], e[x], j2(y, z));
+        cadd(V, vvvv_ordered(e[w], j2(x, y), e[z]));
+        cadd(V, vvvv_ordered(j2(w, x), e[y], e[z]));
+        caxpy(J, cx<T>{c4g, T(0)}, V);
+        J4[n4++] = J;
+      }
+  // rank of the quadruple current of ordering wxyz among those with first < last
+  auto q4 = [](int w, int x, int y) {
+    // enumeration order above: w ascending, then x, then y, keeping z > w
+    int r = 0;
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b)
+        for (int c = 0; c < 4; ++c) {
+          if (b == a || c == a || c == b) continue;
+          const int d = 6 - a - b - c;
+          if (d < a) continue;
+          if (a == w && b == x && c == y) return r;
+          ++r;
+        }
+    return -1;
+  };
+  const c4<T> v[2] = {spinor_v(K.pl[3], mt, -1), spinor_v(K.pl[3], mt, 1)};
+  const r4<T> kt = K.pl[2];
+#pragma unroll 1
+  for (int ht = 0; ht < 2; ++ht) {
+    const c4<T> ub = dbar(spinor_u(kt, mt, ht ? 1 : -1));
+    cx<T> A[2][24];
+    int f = 0;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      c4<T> U1 = row_prop(row_slash(ub, e[w]), kt + q[w], mt);
+      cscale(U1, -g * K.iq[1 << w]);
+#pragma unroll
+      for (int x = 0; x < 4; ++x) {
+        if (x == w) continue;
+        c4<T> r2 = row_slash(ub, j2(w, x));
+        cadd(r2, row_slash(U1, e[x]));
+        c4<T> U2 = row_prop(r2, kt + q[w] + q[x], mt);
+        cscale(U2, -g * K.iq[(1 << w) | (1 << x)]);
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+          if (y == w || y == x) continue;
+          const int z = 6 - w - x - y;
+          c4<T> r3 = row_slash(ub, j3(w, x, y));
+          cadd(r3, row_slash(U1, j2(x, y)));
+          cadd(r3, row_slash(U2, e[y]));
+          c4<T> U3 = row_prop(r3, kt + q[w] + q[x] + q[y], mt);
+          cscale(U3, -g * K.iq[(1 << w) | (1 << x) | (1 << y)]);
+          c4<T> J = z > w ? J4[q4(w, x, y)] : J4[q4(z, y, x)];
+          if (z < w) cscale(J, T(-1));
+          c4<T> R = row_slash(ub, J);
+          cadd(R, row_slash(U1, j3(x, y, z)));
+          cadd(R, row_slash(U2, j2(y, z)));
+          cadd(R, row_slash(U3, e[z]));
+#pragma unroll
+          for (int hv = 0; hv < 2; ++hv) A[hv][f] = times_i(spdot(R, v[hv])) * g;
+          ++f;
+        }
+      }
+    }
+#pragma unroll
+    for (int hv = 0; hv < 2; ++hv) consume(ht | (hv << 1), A[hv]);
+  }
+}
+
+// Helicity blocks of one member of each flipped pair (leg 0 at +): NHEL / 8 blocks;
+// block b sets legs 1, 4, 5 from the bits of b.
+template <int PID> __host__ __device__ constexpr int n_blocks() { return Proc<PID>::NHEL / 8; }
+ME_HD int block_hel(int b) { return 1 | ((b & 1) << 1) | ((b >> 1) << 4); }
+
+// A massless fermion pair coupled through a vector current has opposite helicities
+// (chirality is conserved at the vertex; the wrong-chirality spinor components are
+// exactly zero): with legs 0, 1 such a pair (e+e-, u ubar), the blocks with leg 1 at +
+// vanish identically and are skipped, and for e+e- -> u ubar (g) the heavy-pair slots
+// (legs 2, 3 = u, ubar) with equal helicities vanish too.
+template <int PID> __host__ __device__ constexpr bool massless_initial_pair() {
+  return PID == P_EE_UU || PID == P_EE_UUG || PID == P_UU_TT || PID == P_UU_TTG;
+}
+template <int PID> __host__ __device__ constexpr int n_live_blocks() {
+  return massless_initial_pair<PID>() ? n_blocks<PID>() / 2 : n_blocks<PID>();
+}
+template <int PID> ME_HD int live_block_hel(int i) { return block_hel(massless_initial_pair<PID>() ? 2 * i : i); }
+
+// partial amplitudes of the four helicities hb | (r << 2) (see amp_tt2_block); processes
+// without a block routine evaluate them one at a time
+template <int PID, typename T, class F>
+ME_HD void amplitude_block(const Kin<PID, T>& K, int hb, const Couplings& cp, F&& consume,
+                           const c4<T>* eps_override = nullptr, int ov_leg = -1) {
+  if constexpr (PID == P_GG_TT) {
+    amp_tt2_block<T>(K, hb, cp, eps_override, ov_leg, consume);
+  } else if constexpr (PID == P_GG_TTG) {
+    amp_tt3_block<T>(K, hb, cp, consume);
+  } else if constexpr (PID == P_GG_TTGG) {
+    amp_tt4_block<T>(K, hb, cp, consume);
+  } else {
+    for (int r = 0; r < 4; ++r) {
+      if constexpr (PID == P_EE_UU || PID == P_EE_UUG) {
+        if (r == 0 || r == 3) continue;  // u, ubar with equal helicities: zero
+      }
+      cx<T> A[Proc<PID>::NFLOW];
+      amplitude<PID, T>(K, hb | (r << 2), cp, A, eps_override, ov_leg);
+      consume(r, A);
+    }
+  }
 }
 
 }  // namespace me
