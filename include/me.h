@@ -62,7 +62,9 @@ extern "C" {
  *                    measured float32 error per unit of (|R S| + |CT|) (99.9th
  *                    percentile on flat points of the three real processes)
  *   device           CUDA device ordinal the handle runs on
- *   lanes_per_event  lanes sharing one point (1, 2, 4, 8 or 16; 0 = autotune)
+ *   lanes_per_event  lanes sharing one point (1, 2, 4, 8 or 16; at most 8 for
+ *                    "gg_ttgg"; 0 = autotune: each candidate is timed on the
+ *                    handle's first call of each kind and precision)
  */
 typedef struct me_params {
   uint32_t version;
