@@ -40,6 +40,38 @@ UNIT = "events/s"
 WORKLOAD = ("gg->ttg real-emission minus FKS soft/collinear counterterms, sqrt(s)=1 TeV, m_t=173, "
             "2^20 flat massive-RAMBO points, mixed precision (fp32 amplitudes + fp64 rescue)")
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+FP64_PER_SM_CLK = 2  # DFMA thread-ops per SM per clock (ncu: ..._op_dfma_pred_on.avg.peak_sustained)
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu --set full
+# capture of each kernel (summaries in profiles/), with the hash of the kernel sources they
+# were taken on; reported only while the sources still hash the same.
+KERNEL_SOURCES_SHA = "59c593d510be4398"
+TRAFFIC = {
+    ("c2", "rescue"): {"bytes": 1.237547e9 + 4.801849e9, "points": 263843,
+                       "profile": "profiles/k_real_sub_gg_ttg_double_rescue.md"},
+    ("c2", "main"): {"bytes": 0.179097e9 + 0.252963e9, "points": 1 << 20,
+                     "profile": "profiles/k_real_sub_gg_ttg_float_2p20.md"},
+    ("c3", "main"): {"bytes": 20.039969e9 + 33.274347e9, "points": 1 << 18,
+                     "profile": "profiles/k_tree_gg_ttgg_float_tc_2p18.md"},
+}
+
+
+def kernel_sources_sha() -> str:
+    import glob
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_2503_07439_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(csrc, "*.cuh")) + glob.glob(os.path.join(csrc, "me_inst_*.cu"))):
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_launch(workload: str, stage: str, points: int):
+    t = TRAFFIC.get((workload, stage))
+    if t is None or kernel_sources_sha() != KERNEL_SOURCES_SHA:
+        return None
+    return t["bytes"] * points / t["points"]  # scales with the points of the launch
 # launches per step: main kernel (+ FP64 rescue for the subtracted real) + 2 reduction kernels
 WORKLOADS = {
     "c2": {"calls": [("gg_ttg", "real_subtracted", SEED)], "n": N_POINTS, "metric": METRIC, "workload": WORKLOAD,
@@ -163,18 +195,20 @@ SERVE_KIND = {"ee_uu": "born", "ee_uug": "real_subtracted", "gg_tt": "born", "gg
               "gg_ttgg": "born", "uu_ttg": "real_subtracted"}
 
 
-def serving_metrics(me, n_requests: int = 200, load: float = 0.9, seed: int = 7, device: int = 0):
-    """Served mixed stream: Poisson arrivals (scaled to `load` x the measured capacity),
-    sizes log-uniform in [256, 65536], processes uniform; latency submit -> completion.
-    Compared with the plain FP64 path run one batch at a time on the same arrivals."""
+def serving_metrics(me, n_requests: int = 400, loads=(0.5, 0.9, 1.2), seed: int = 7, device: int = 0,
+                    n_slots: int = 8):
+    """Served mixed stream: Poisson arrivals scaled to each offered load x the measured
+    capacity, sizes log-uniform in [256, 65536], processes uniform; latency submit ->
+    completion.  Compared with the plain FP64 path run one batch at a time on the same
+    arrivals (its service times are measured once, the queue is replayed per load)."""
     import synth
     reqs = synth.mixed_stream(n_requests, seed)
     data = [synth.flat_points(r["process"], r["n"], r["seed"]) for r in reqs]
     total = sum(r["n"] for r in reqs)
-    srv = me.Server(device=device, n_slots=4, precision=me.ME_PREC_MIXED)
-    for proc in SERVE_KIND:  # warm-up: handle creation and lane-layout tuning per slot
+    srv = me.Server(device=device, n_slots=n_slots, precision=me.ME_PREC_MIXED)
+    for proc in SERVE_KIND:  # warm-up: handles of every slot and lane-layout tuning
         b = synth.flat_points(proc, 4096, 99)
-        ts = [srv.submit(proc, SERVE_KIND[proc], b.p) for _ in range(4)]
+        ts = [srv.submit(proc, SERVE_KIND[proc], b.p) for _ in range(2 * n_slots)]
         for t in ts:
             srv.poll(t)
     t0 = time.perf_counter()
@@ -182,56 +216,60 @@ def serving_metrics(me, n_requests: int = 200, load: float = 0.9, seed: int = 7,
     for t in ts:
         srv.poll(t)
     capacity = total / (time.perf_counter() - t0)
-    rate = load * capacity / (total / n_requests)  # requests per second
-    arrivals = [r["arrival"] / rate for r in reqs]
-    lat = [0.0] * n_requests
-    tickets = [None] * n_requests
-    done = threading.Event()
 
-    def poller():
-        for i in range(n_requests):
-            while tickets[i] is None:
-                time.sleep(1e-4)
-            res = srv.poll(tickets[i])
-            lat[i] = res["t_total_us"] * 1e-3
-        done.set()
+    def run_load(load):
+        rate = load * capacity / (total / n_requests)  # requests per second
+        arrivals = [r["arrival"] / rate for r in reqs]
+        lat = [0.0] * n_requests
+        tickets = [None] * n_requests
+        done = threading.Event()
 
-    th = threading.Thread(target=poller)
-    th.start()
-    start = time.perf_counter()
-    for i, (r, d) in enumerate(zip(reqs, data)):
-        while time.perf_counter() - start < arrivals[i]:
-            time.sleep(5e-5)
-        tickets[i] = srv.submit(r["process"], SERVE_KIND[r["process"]], d.p, d.wgt)
-    done.wait()
-    th.join()
-    makespan = time.perf_counter() - start
+        def poller():
+            for i in range(n_requests):
+                while tickets[i] is None:
+                    time.sleep(1e-4)
+                lat[i] = srv.poll(tickets[i])["t_total_us"] * 1e-3
+            done.set()
+
+        th = threading.Thread(target=poller)
+        th.start()
+        start = time.perf_counter()
+        for i, (r, d) in enumerate(zip(reqs, data)):
+            while time.perf_counter() - start < arrivals[i]:
+                time.sleep(5e-5)
+            tickets[i] = srv.submit(r["process"], SERVE_KIND[r["process"]], d.p, d.wgt)
+        done.wait()
+        th.join()
+        return arrivals, {"offered_load": load, "events_per_s": total / (time.perf_counter() - start),
+                          "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))}
+
+    runs = [run_load(x) for x in loads]
     srv.close()
-    # plain FP64 path, one batch at a time, same arrival times (queueing on the host clock)
+    # plain FP64 path, one batch at a time: service time of every request, then the
+    # same arrival times replayed through a single-server queue per load
     hs = {p: me.Handle(p, precision=me.ME_PREC_FP64, device=device) for p in SERVE_KIND}
     for p, h in hs.items():
         (h.born if SERVE_KIND[p] == "born" else h.real_subtracted)(synth.flat_points(p, 1024, 98).p)
-    clock = 0.0
-    lat64 = []
-    busy = 0.0
-    for i, (r, d) in enumerate(zip(reqs, data)):
+    svc = []
+    for r, d in zip(reqs, data):
         h = hs[r["process"]]
         f = h.born if SERVE_KIND[r["process"]] == "born" else h.real_subtracted
         t1 = time.perf_counter()
         f(d.p, d.wgt)
-        svc = time.perf_counter() - t1
-        busy += svc
-        begin = max(clock, arrivals[i])
-        clock = begin + svc
-        lat64.append(1e3 * (clock - arrivals[i]))
+        svc.append(time.perf_counter() - t1)
     for h in hs.values():
         h.close()
-    return {"requests": n_requests, "points": total, "offered_load": load,
-            "capacity_events_per_s": capacity, "events_per_s": total / makespan,
-            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "fp64_per_batch": {"events_per_s_busy": total / busy,
-                               "p50_ms": float(np.percentile(lat64, 50)),
-                               "p99_ms": float(np.percentile(lat64, 99))}}
+    out = []
+    for arrivals, m in runs:
+        clock, lat64 = 0.0, []
+        for a, t in zip(arrivals, svc):
+            clock = max(clock, a) + t
+            lat64.append(1e3 * (clock - a))
+        m["fp64_per_batch"] = {"events_per_s": total / clock, "p50_ms": float(np.percentile(lat64, 50)),
+                               "p99_ms": float(np.percentile(lat64, 99))}
+        out.append(m)
+    return {"requests": n_requests, "points": total, "slots": n_slots, "capacity_events_per_s": capacity,
+            "fp64_per_batch_events_per_s_busy": total / sum(svc), "loads": out}
 
 
 def run_reference(args):
@@ -405,8 +443,27 @@ def main():
     proc0, entry0, _ = calls[0]
     flops_event = ops["real_subtracted_per_event" if entry0 == "real_subtracted" else "born_per_event"][proc0]
     main_ms = t_main / max(1, ncalls)
-    achieved = flops_event * n / (main_ms * 1e-3) / 1e12
-    peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    resc_ms = t_resc / max(1, ncalls)
+    resc_pts = handles[0][0].last_rescued()
+    peak32 = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    peak64 = SM_COUNT * FP64_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    # roofline of the dominant kernel of the step (by its CUDA-event time)
+    rl_main = {"bound": "alu", "achieved": flops_event * n / (main_ms * 1e-3) / 1e12, "peak": peak32,
+               "unit": "TFLOP/s", "traffic": traffic_per_launch(args.workload, "main", n), "kernel": wl["kernel"],
+               "peak_note": "fp32 FMA peak 152 SMs x 128 lanes x 2 flops x 2070 MHz (nominal units at max clock; "
+                            "MEASURED_PEAKS.json has no fp32 figure)",
+               "flops_per_event": flops_event, "ms_per_launch": main_ms}
+    rl_main["frac"] = rl_main["achieved"] / peak32
+    roofline, other = rl_main, None
+    if resc_pts > 0 and resc_ms > main_ms:
+        rl_resc = {"bound": "alu", "achieved": flops_event * resc_pts / (resc_ms * 1e-3) / 1e12, "peak": peak64,
+                   "unit": "TFLOP/s", "traffic": traffic_per_launch(args.workload, "rescue", resc_pts),
+                   "kernel": wl["kernel"].replace("float", "double") + " (float64 rescue of the flagged points)",
+                   "peak_note": "fp64 peak 152 SMs x 2 DFMA/clk x 2 flops x 2070 MHz (nominal units at max clock; "
+                                "MEASURED_PEAKS.json has no fp64 figure)",
+                   "flops_per_event": flops_event, "points_per_launch": resc_pts, "ms_per_launch": resc_ms}
+        rl_resc["frac"] = rl_resc["achieved"] / peak64
+        roofline, other = rl_resc, rl_main
     clocks = clk.summary()
     line = {
         "metric": wl["metric"], "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -420,12 +477,8 @@ def main():
         "rescued_per_step": rescued,
         "stage_ms_per_step": {"main_kernel": main_ms, "rescue_kernel": t_resc / max(1, ncalls),
                               "reduction": t_red / max(1, ncalls)},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "kernel": wl["kernel"],
-                     "peak_note": "fp32 FMA peak 152 SMs x 128 lanes x 2 flops x 2070 MHz (nominal units and "
-                                  "max clock; no measured fp32 peak in MEASURED_PEAKS.json)",
-                     "flops_per_event": flops_event},
+        "roofline": roofline,
+        "roofline_other_kernel": other,
         "e2e": {"value": n / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": wl["launches"] * args.steps,
         "clocks": clocks,

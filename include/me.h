@@ -165,12 +165,12 @@ void me_destroy(me_handle* h);
 /* ---------------------------------------------------------------- request loop
  * Continuous batching of phase-space batches from many integration channels
  * (the multi-event interface of Sec. 4.4; points stay on the device for the whole
- * evaluation, Sec. 4.3).  A server owns `n_slots` CUDA streams on one device; a
- * scheduler thread admits queued requests, oldest first, whenever a slot is free
- * and the sum of the in-flight requests' buffers (n * (4 n_ext + 2) * 8 bytes) stays
- * within `mem_budget_bytes`, so requests that arrive while others run are admitted
- * as slots and memory free up and their work overlaps on the GPU.  A request's
- * result does not depend on what else is in flight.
+ * evaluation, Sec. 4.3).  A server owns `n_slots` slots on one device, each a host
+ * thread with its own CUDA stream; a free slot admits the oldest queued request
+ * whenever the sum of the in-flight requests' buffers (n * (4 n_ext + 2) * 8 bytes)
+ * stays within `mem_budget_bytes`, so requests that arrive while others run are
+ * admitted as slots and memory free up, and their staging and kernels overlap.  A
+ * request's result does not depend on what else is in flight.
  */
 #define ME_KIND_BORN 0             /* me_eval_born */
 #define ME_KIND_REAL_SUBTRACTED 1  /* me_eval_real_subtracted */
@@ -205,12 +205,12 @@ typedef struct me_result {
   double sum_w, sum_w2;      /* of out[] */
   double t_queue_us;         /* submit -> admission */
   double t_device_us;        /* copies + kernels on the slot's stream (CUDA events) */
-  double t_total_us;         /* submit -> completion seen by the scheduler */
+  double t_total_us;         /* submit -> completion seen by the slot thread */
 } me_result;
 
 /* Defaults: device 0, 4 slots, queue 4096, 8 GiB budget, mixed precision. */
 void me_default_server_params(me_server_params* p);
-/* Start a server and its scheduler thread.  ME_ERR_ARG for bad parameters. */
+/* Start a server and its slot threads.  ME_ERR_ARG for bad parameters. */
 int me_server_create(const me_server_params* params, me_server** out);
 /* Queue a request; returns a ticket.  ME_ERR_BUSY when the queue is full or the
  * request alone exceeds the memory budget; ME_ERR_PROCESS for an unknown process. */
@@ -219,7 +219,7 @@ int me_submit(me_server* s, const me_request* req, me_ticket* out);
  * the ticket retired; ME_ERR_TIMEOUT: not finished yet (poll again); ME_ERR_ARG:
  * unknown or already retired ticket.  The wait is on the host only. */
 int me_poll(me_server* s, me_ticket t, me_result* out, int64_t timeout_us);
-/* Stop the scheduler, wait for in-flight work, free everything.  NULL is a no-op. */
+/* Stop the slot threads, wait for in-flight work, free everything.  NULL is a no-op. */
 void me_server_destroy(me_server* s);
 
 /* ---------------------------------------------------------------- allocation-free variant

@@ -9,7 +9,9 @@
 #include <complex>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -426,10 +428,22 @@ static cudaError_t dispatch(int pid, int kind, bool fp64, int lpe, const LaunchA
 }
 
 // pick lanes-per-event by timing each candidate once on the caller's batch (first use)
+// Lane layouts chosen by timing, shared by every handle of the process (key: device,
+// process, kind, precision), so that later handles -- e.g. the slots of a server --
+// reuse the first handle's choice instead of tuning again.
+static std::mutex g_lpe_mu;
+static std::map<std::tuple<int, int, int, int>, int> g_lpe_cache;
+
 static int choose_lpe(me_handle* h, int kind, bool fp64, const LaunchArgs& a) {
   int& slot = h->lpe[kind][fp64 ? 1 : 0];
   if (h->prm.lanes_per_event) return slot = h->prm.lanes_per_event;
   if (slot) return slot;
+  const auto key = std::make_tuple(h->prm.device, h->proc->pid, kind, fp64 ? 1 : 0);
+  {
+    std::lock_guard<std::mutex> lk(g_lpe_mu);
+    auto it = g_lpe_cache.find(key);
+    if (it != g_lpe_cache.end()) return slot = it->second;
+  }
   const int cands[5] = {1, 2, 4, 8, 16};
   const int ncand = 5;
   LaunchArgs t = a;
@@ -457,6 +471,10 @@ static int choose_lpe(me_handle* h, int kind, bool fp64, const LaunchArgs& a) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaGetLastError();
+  {
+    std::lock_guard<std::mutex> lk(g_lpe_mu);
+    g_lpe_cache.emplace(key, pick);
+  }
   return slot = pick;
 }
 

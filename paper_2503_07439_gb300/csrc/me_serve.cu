@@ -1,11 +1,15 @@
 // Request loop: continuous batching of phase-space batches from many integration
 // channels (multi-event interface of Sec. 4.4, kept on the device between requests as
-// argued in Sec. 4.3).  A scheduler thread admits queued requests into free slots
-// while the device-memory budget allows; each slot owns a CUDA stream, pinned staging
-// buffers and one handle per process, so admitted requests of any process overlap on
-// the GPU.  Completion is detected by polling CUDA events (never a device-side wait).
+// argued in Sec. 4.3).  Each of the n_slots slots owns a host thread, a CUDA stream,
+// pinned staging buffers and one handle per process.  A slot thread takes the oldest
+// queued request whenever the device-memory budget allows, stages it (host copy into
+// pinned memory, then asynchronous copies), launches it on its stream and waits for it
+// on the host, so staging, launches and completions of different requests proceed in
+// parallel and their kernels overlap on the GPU.  Completion is detected by polling a
+// CUDA event (never a device-side wait).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -60,7 +64,7 @@ struct me_server {
   std::deque<Req*> pending;
   std::unordered_map<uint64_t, Req*> reqs;
   std::vector<Slot> slots;
-  std::thread worker;
+  std::vector<std::thread> workers;  // one per slot
   bool stop = false;
   int64_t mem_in_use = 0;
   uint64_t next_ticket = 1;
@@ -88,7 +92,7 @@ static int slot_reserve(Slot& s, int64_t n, int n_ext) {
   return ME_OK;
 }
 
-// launch one admitted request on its slot (called by the worker without the lock)
+// stage and launch one admitted request on its slot (slot thread, without the lock)
 static int start(me_server* sv, Slot& s, Req* r) {
   cudaSetDevice(sv->prm.device);
   int rc = slot_reserve(s, r->n, r->n_ext);
@@ -140,57 +144,56 @@ static void finish(Req* r, Slot& s, int status) {
   r->res.t_total_us = std::chrono::duration<double, std::micro>(now - r->t_submit).count();
 }
 
-static void worker_loop(me_server* sv) {
+// Host-side wait for a slot's completion event: a short spin for small requests, then
+// sleeps growing to 200 us.  Every kernel of the path runs to completion on its own
+// (no device-side waits), so the event always completes or reports an error.
+static cudaError_t wait_event(cudaEvent_t e) {
+  const auto t0 = clk::now();
+  int sleep_us = 0;
+  for (;;) {
+    const cudaError_t q = cudaEventQuery(e);
+    if (q != cudaErrorNotReady) return q;
+    if (std::chrono::duration<double, std::micro>(clk::now() - t0).count() < 100.0) {
+      std::this_thread::yield();
+      continue;
+    }
+    sleep_us = std::min(200, std::max(10, 2 * sleep_us));
+    std::this_thread::sleep_for(std::chrono::microseconds(sleep_us));
+  }
+}
+
+// One slot: admit the oldest request when the memory budget allows (first in, first
+// out: a request that does not fit blocks the ones behind it), run it, retire it.
+static void slot_loop(me_server* sv, int si) {
+  Slot& s = sv->slots[si];
   cudaSetDevice(sv->prm.device);
   std::unique_lock<std::mutex> lk(sv->mu);
   while (!sv->stop) {
-    bool progress = false;
-    // completions
-    for (auto& s : sv->slots) {
-      if (!s.cur) continue;
-      cudaError_t q = cudaEventQuery(s.e1);
-      if (q == cudaErrorNotReady) continue;
-      Req* r = s.cur;
-      s.cur = nullptr;
-      finish(r, s, q == cudaSuccess ? ME_OK : ME_ERR_CUDA);
-      sv->mem_in_use -= (int64_t)r->bytes;
-      r->done = true;
-      progress = true;
-    }
-    if (progress) sv->cv_done.notify_all();
-    // admissions: FIFO while a slot and memory are free
-    while (!sv->pending.empty()) {
-      Req* r = sv->pending.front();
-      Slot* free_slot = nullptr;
-      for (auto& s : sv->slots)
-        if (!s.cur) {
-          free_slot = &s;
-          break;
-        }
-      if (!free_slot) break;
-      if (sv->mem_in_use + (int64_t)r->bytes > sv->prm.mem_budget_bytes && sv->mem_in_use > 0) break;
-      sv->pending.pop_front();
-      r->t_admit = clk::now();
-      sv->mem_in_use += (int64_t)r->bytes;
-      free_slot->cur = r;
-      lk.unlock();
-      int rc = start(sv, *free_slot, r);
-      lk.lock();
-      if (rc != ME_OK) {
-        free_slot->cur = nullptr;
-        finish(r, *free_slot, rc);
-        sv->mem_in_use -= (int64_t)r->bytes;
-        r->done = true;
-        sv->cv_done.notify_all();
+    Req* r = nullptr;
+    if (!sv->pending.empty()) {
+      Req* head = sv->pending.front();
+      if (sv->mem_in_use + (int64_t)head->bytes <= sv->prm.mem_budget_bytes || sv->mem_in_use == 0) {
+        r = head;
+        sv->pending.pop_front();
+        sv->mem_in_use += (int64_t)r->bytes;
+        r->t_admit = clk::now();
       }
-      progress = true;
     }
-    if (!progress) {
-      bool busy = false;
-      for (auto& s : sv->slots) busy |= s.cur != nullptr;
-      // bounded host-side wait: short when work is in flight, longer when idle
-      sv->cv_work.wait_for(lk, busy ? std::chrono::microseconds(20) : std::chrono::milliseconds(5));
+    if (!r) {
+      sv->cv_work.wait_for(lk, std::chrono::milliseconds(5));
+      continue;
     }
+    lk.unlock();
+    s.cur = r;
+    int rc = start(sv, s, r);
+    if (rc == ME_OK && wait_event(s.e1) != cudaSuccess) rc = ME_ERR_CUDA;
+    finish(r, s, rc);
+    s.cur = nullptr;
+    lk.lock();
+    sv->mem_in_use -= (int64_t)r->bytes;
+    r->done = true;
+    sv->cv_done.notify_all();
+    sv->cv_work.notify_all();  // memory was released: the head may fit now
   }
 }
 
@@ -227,7 +230,7 @@ int me_server_create(const me_server_params* prm, me_server** out) {
     }
     *s.h_resc = 0;
   }
-  sv->worker = std::thread(worker_loop, sv);
+  for (int i = 0; i < prm->n_slots; ++i) sv->workers.emplace_back(slot_loop, sv, i);
   *out = sv;
   return ME_OK;
 }
@@ -264,7 +267,7 @@ int me_submit(me_server* sv, const me_request* rq, me_ticket* out) {
   sv->reqs[r->ticket] = r;
   sv->pending.push_back(r);
   *out = r->ticket;
-  sv->cv_work.notify_one();
+  sv->cv_work.notify_all();
   return ME_OK;
 }
 
@@ -291,7 +294,8 @@ void me_server_destroy(me_server* sv) {
     sv->stop = true;
   }
   sv->cv_work.notify_all();
-  if (sv->worker.joinable()) sv->worker.join();
+  for (auto& t : sv->workers)
+    if (t.joinable()) t.join();
   cudaSetDevice(sv->prm.device);
   for (auto& s : sv->slots) {
     if (s.st) cudaStreamSynchronize(s.st);
