@@ -44,13 +44,13 @@ FP64_PER_SM_CLK = 2  # DFMA thread-ops per SM per clock (ncu: ..._op_dfma_pred_o
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu --set full
 # capture of each kernel (summaries in profiles/), with the hash of the kernel sources they
 # were taken on; reported only while the sources still hash the same.
-KERNEL_SOURCES_SHA = "59c593d510be4398"
+KERNEL_SOURCES_SHA = "c790d9d398d62b73"
 TRAFFIC = {
-    ("c2", "rescue"): {"bytes": 1.237547e9 + 4.801849e9, "points": 263843,
+    ("c2", "rescue"): {"bytes": 0.698594e9 + 3.733798e9, "points": 188216,
                        "profile": "profiles/k_real_sub_gg_ttg_double_rescue.md"},
-    ("c2", "main"): {"bytes": 0.179097e9 + 0.252963e9, "points": 1 << 20,
+    ("c2", "main"): {"bytes": 0.177508e9 + 0.286597e9, "points": 1 << 20,
                      "profile": "profiles/k_real_sub_gg_ttg_float_2p20.md"},
-    ("c3", "main"): {"bytes": 20.039969e9 + 33.274347e9, "points": 1 << 18,
+    ("c3", "main"): {"bytes": 0.052774e9 + 0.022590e9, "points": 1 << 18,
                      "profile": "profiles/k_tree_gg_ttgg_float_tc_2p18.md"},
 }
 
@@ -89,7 +89,7 @@ WORKLOADS = {
            "metric": "gg -> t tbar g g tree events/s (tensor-core colour sum, 1 GB300)",
            "workload": "gg -> t tbar g g tree at sqrt(s)=2 TeV, 2^18 flat massive-RAMBO points, float32 "
                        "amplitudes, 24-flow colour sum on tensor cores (bf16 x3 split, f32 accumulate)",
-           "kernel": "k_tree<gg_ttgg, float> (mma.sync bf16)", "launches": 3,
+           "kernel": "k_tree_tc4 (gg_ttgg, float; four lanes per event, mma.sync bf16 colour sum)", "launches": 3,
            "l2": "inputs 50 MB (< L2; compute-bound kernel)"},
 }
 
@@ -244,6 +244,7 @@ def serving_metrics(me, n_requests: int = 400, loads=(0.5, 0.9, 1.2), seed: int 
                           "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))}
 
     runs = [run_load(x) for x in loads]
+    gstats = srv.stats()
     srv.close()
     # plain FP64 path, one batch at a time: service time of every request, then the
     # same arrival times replayed through a single-server queue per load
@@ -269,35 +270,63 @@ def serving_metrics(me, n_requests: int = 400, loads=(0.5, 0.9, 1.2), seed: int 
                                "p99_ms": float(np.percentile(lat64, 99))}
         out.append(m)
     return {"requests": n_requests, "points": total, "slots": n_slots, "capacity_events_per_s": capacity,
-            "fp64_per_batch_events_per_s_busy": total / sum(svc), "loads": out}
+            "fp64_per_batch_events_per_s_busy": total / sum(svc), "loads": out,
+            "graph_replays": gstats["graph_runs"], "ordinary_runs": gstats["plain_runs"]}
+
+
+def _reference_chunk(args):
+    """Reference-arm worker: the FP64 oracle on one block of points of one call (spawned)."""
+    proc, entry, seed, first, n = args
+    sys.path.insert(0, ROOT)
+    import synth
+    from oracle import fks
+    from oracle import matrix_element as ome
+    from oracle import nlo_ee
+    if proc == "gg_tt":
+        b = synth.gg_tt_scan(n, seed, first_point=first)
+    else:
+        b = synth.flat_points(proc, n, seed, first_point=first)
+    k = ome.to_points(b.p)
+    t0 = time.perf_counter()
+    if entry == "real_subtracted":
+        fks.real_subtracted(proc, k)
+    elif entry == "nbody_nlo":
+        nlo_ee.nbody_nlo(k)
+    else:
+        ome.me2(proc, k)
+    return n, time.perf_counter() - t0
 
 
 def run_reference(args):
-    """The oracle as the reference arm: bounded samples of the workload on host cores."""
+    """The oracle as the reference arm: bounded samples of the selected workload, spread
+    over the host cores (spawned processes), one sample per step."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    per_step = 512
-    t_total = 0.0
-    import synth
-    from oracle import fks
-    from oracle.matrix_element import to_points
-    for s in range(args.warmup + args.steps):
-        b = synth.flat_points(PROCESS, per_step, SEED, first_point=s * per_step)
-        k = to_points(b.p)
-        t0 = time.perf_counter()
-        fks.real_subtracted(PROCESS, k)
-        dt = time.perf_counter() - t0
-        if s >= args.warmup:
-            t_total += dt
-    value = args.steps * per_step / t_total
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+    wl = WORKLOADS[args.workload]
+    workers = max(1, min(8, os.cpu_count() or 1))
+    per_worker = {"c2": 1024, "c0": 4096, "c1": 4096, "c3": 4}[args.workload]
+    ctx = mp.get_context("spawn")
+    t_total, points = 0.0, 0
+    with ctx.Pool(workers) as pool:
+        for s in range(args.warmup + args.steps):
+            jobs = [(proc, entry, seed, (s * workers + i) * per_worker, per_worker)
+                    for proc, entry, seed in wl["calls"] for i in range(workers)]
+            t0 = time.perf_counter()
+            pool.map(_reference_chunk, jobs)
+            dt = time.perf_counter() - t0
+            if s >= args.warmup:
+                t_total += dt
+                points += workers * per_worker  # events per step (one per call, as in the GPU arm)
+    value = points / t_total
+    sample = (f"{workers} spawned processes x {per_worker} points per call per step of the same workload "
+              f"({len(wl['calls'])} call(s)), FP64 numpy oracle, wall clock")
+    line = {"impl": "reference", "metric": wl["metric"], "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded Philox + RAMBO)",
-            "config": {"workload": WORKLOAD, "points_per_step": per_step},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{per_step} points per step of the same workload, single process"},
+            "config": {"workload": wl["workload"], "points_per_step": workers * per_worker},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -312,6 +341,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--lanes-per-event", type=int, default=0,
+                    help="pin the lane layout of every handle (0: autotune; profiling runs pin it, "
+                         "since launch timing under a profiler misleads the tuner)")
     ap.add_argument("--workload", default="c2", choices=["c0", "c1", "c2", "c3"],
                     help="c2 (default): gg->ttg real-minus-CT; c0: e+e- NLO (n-body + real-minus-CT); "
                          "c1: gg->tt LO; c3: gg->ttgg tree with the tensor-core colour sum")
@@ -355,7 +387,7 @@ def main():
     def make(prec):
         hs = []
         for proc, entry, bb in calls:
-            hh = me.Handle(proc, precision=prec, device=local)
+            hh = me.Handle(proc, precision=prec, device=local, lanes_per_event=args.lanes_per_event)
             hh.set_stream(stream.cuda_stream)
             hs.append((hh, getattr(hh, entry), torch.from_numpy(bb.p).cuda(), torch.from_numpy(bb.wgt).cuda(),
                        torch.empty(n, dtype=torch.float64, device="cuda")))

@@ -58,9 +58,14 @@ extern "C" {
  *   xi_thr, y_thr    mixed mode: points with xi < xi_thr or 1-y < y_thr in an active
  *                    counterterm region are re-evaluated in float64
  *   tol, me_eps      mixed mode: a point is re-evaluated in float64 when
- *                    (|R S| + |CT|) * me_eps > tol * |R S - CT|; me_eps is the
- *                    measured float32 error per unit of (|R S| + |CT|) (99.9th
- *                    percentile on flat points of the three real processes)
+ *                    E (1 + sqrt(0.01 / rho)) me_eps > tol |W|, W = R S - CT summed
+ *                    over sectors, E = sum over sectors of |R S| + |CT_coll| +
+ *                    |CT_soft - CT_softcoll| (the soft pair shares its Born values, so
+ *                    their errors cancel), rho = min over sectors of 1 - y (float32
+ *                    amplitude errors grow towards the collinear limit); me_eps is
+ *                    calibrated so that, with the flagged points re-evaluated, 99.9 %
+ *                    of flat points of each real process stay within 0.7 tol (a 30 %
+ *                    margin) and points on soft/collinear approach sequences within tol
  *   device           CUDA device ordinal the handle runs on
  *   lanes_per_event  lanes sharing one point (1, 2, 4, 8 or 16; at most 8 for
  *                    "gg_ttgg"; 0 = autotune: each candidate is timed on the
@@ -85,7 +90,7 @@ typedef struct me_params {
 typedef struct me_handle me_handle;
 
 /* Fill `p` with the defaults: FP64, alpha = 1/132.507, alpha_s = 0.118, mt = 173,
- * xi_cut = 0.5, delta = 1, xi_thr = 1e-3, y_thr = 1e-3, tol = 1e-5, me_eps = 8e-7,
+ * xi_cut = 0.5, delta = 1, xi_thr = 1e-3, y_thr = 1e-3, tol = 1e-5, me_eps = 4e-7,
  * device 0, lanes_per_event 0.  Never fails. */
 void me_default_params(me_params* p);
 
@@ -186,6 +191,7 @@ typedef struct me_server_params {
   int32_t max_queue;         /* pending requests beyond which me_submit returns ME_ERR_BUSY */
   int64_t mem_budget_bytes;  /* admission budget for in-flight request buffers */
   me_params params;          /* physics and precision, shared by all requests */
+  int32_t use_graphs;        /* 1: replay each (process, kind) launch sequence from a captured CUDA graph */
 } me_server_params;
 
 /* One batch: host buffers owned by the caller, kept alive until me_poll returns it. */
@@ -208,7 +214,7 @@ typedef struct me_result {
   double t_total_us;         /* submit -> completion seen by the slot thread */
 } me_result;
 
-/* Defaults: device 0, 4 slots, queue 4096, 8 GiB budget, mixed precision. */
+/* Defaults: device 0, 4 slots, queue 4096, 8 GiB budget, mixed precision, graphs on. */
 void me_default_server_params(me_server_params* p);
 /* Start a server and its slot threads.  ME_ERR_ARG for bad parameters. */
 int me_server_create(const me_server_params* params, me_server** out);
@@ -219,6 +225,9 @@ int me_submit(me_server* s, const me_request* req, me_ticket* out);
  * the ticket retired; ME_ERR_TIMEOUT: not finished yet (poll again); ME_ERR_ARG:
  * unknown or already retired ticket.  The wait is on the host only. */
 int me_poll(me_server* s, me_ticket t, me_result* out, int64_t timeout_us);
+/* Requests run so far by replaying a captured CUDA graph (every request of a
+ * (process, kind, weights) key after the first on a slot) and by ordinary launches. */
+int me_server_stats(me_server* s, int64_t* graph_runs, int64_t* plain_runs);
 /* Stop the slot threads, wait for in-flight work, free everything.  NULL is a no-op. */
 void me_server_destroy(me_server* s);
 

@@ -43,7 +43,8 @@ class MEParams(ctypes.Structure):
 
 class MEServerParams(ctypes.Structure):
     _fields_ = [("version", ctypes.c_uint32), ("device", ctypes.c_int32), ("n_slots", ctypes.c_int32),
-                ("max_queue", ctypes.c_int32), ("mem_budget_bytes", ctypes.c_int64), ("params", MEParams)]
+                ("max_queue", ctypes.c_int32), ("mem_budget_bytes", ctypes.c_int64), ("params", MEParams),
+                ("use_graphs", ctypes.c_int32)]
 
 
 class MERequest(ctypes.Structure):
@@ -91,6 +92,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "me_submit": (ctypes.c_int, [vp, ctypes.POINTER(MERequest), ctypes.POINTER(ctypes.c_uint64)]),
         "me_poll": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.POINTER(MEResult), i64]),
         "me_server_destroy": (None, [vp]),
+        "me_server_stats": (ctypes.c_int, [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
         "me_eval_real_subtracted_noalloc": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(MEParams), vp, vp, i64,
                                                            vp, vp]),
     }
@@ -237,13 +239,14 @@ class Server:
     """Request loop (me_server_create / me_submit / me_poll / me_server_destroy)."""
 
     def __init__(self, device: int = 0, n_slots: int = 4, max_queue: int = 4096, mem_budget_bytes: int = 0,
-                 precision: int = ME_PREC_MIXED, **params):
+                 precision: int = ME_PREC_MIXED, use_graphs: bool = True, **params):
         self.lib = library()
         sp = MEServerParams()
         self.lib.me_default_server_params(ctypes.byref(sp))
         sp.device = device
         sp.n_slots = n_slots
         sp.max_queue = max_queue
+        sp.use_graphs = 1 if use_graphs else 0
         if mem_budget_bytes:
             sp.mem_budget_bytes = mem_budget_bytes
         sp.params = default_params(precision=precision, device=device, **params)
@@ -274,6 +277,12 @@ class Server:
         return {"status": r.status, "n": r.n, "n_rescued": r.n_rescued, "sum_w": r.sum_w, "sum_w2": r.sum_w2,
                 "t_queue_us": r.t_queue_us, "t_device_us": r.t_device_us, "t_total_us": r.t_total_us,
                 "out": ko}
+
+    def stats(self) -> dict:
+        """Requests run by replaying a captured CUDA graph and by ordinary launches."""
+        g, p = ctypes.c_int64(), ctypes.c_int64()
+        _check(self.lib.me_server_stats(self.s, ctypes.byref(g), ctypes.byref(p)))
+        return {"graph_runs": g.value, "plain_runs": p.value}
 
     def close(self):
         if getattr(self, "s", None):

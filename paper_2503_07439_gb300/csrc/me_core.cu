@@ -34,9 +34,10 @@ static int fail(int code, const std::string& msg) {
   } while (0)
 
 // ---------------------------------------------------------------- reductions
-__global__ void k_partials(const double* __restrict__ w, long n, double* __restrict__ part) {
+__global__ void k_partials(const double* __restrict__ w, long n, double* __restrict__ part, const int* __restrict__ cnt) {
   __shared__ double s1[256], s2[256];
   double a = 0.0, b = 0.0;
+  if (cnt) n = *cnt;
   for (long i = (long)blockIdx.x * 256 + threadIdx.x; i < n; i += (long)gridDim.x * 256) {
     const double x = w[i];
     a += x;
@@ -58,8 +59,10 @@ __global__ void k_partials(const double* __restrict__ w, long n, double* __restr
   }
 }
 
-__global__ void k_finish(const double* __restrict__ part, int nblk, double* __restrict__ acc, long n) {
+__global__ void k_finish(const double* __restrict__ part, int nblk, double* __restrict__ acc, long n,
+                         const int* __restrict__ cnt) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
+    if (cnt) n = *cnt;
     double a = 0.0, b = 0.0;
     for (int i = 0; i < nblk; ++i) {
       a += part[2 * i];
@@ -332,7 +335,13 @@ static int device_setup(int dev, ColourTables** d_tab) {
   if (!g_dev[dev].ready) {
     ME_CUDA(cudaSetDevice(dev));
     ME_CUDA(cudaMalloc(&g_dev[dev].d_tab, sizeof(ColourTables)));
-    ME_CUDA(cudaMemcpy(g_dev[dev].d_tab, g_host_tab, sizeof(ColourTables), cudaMemcpyHostToDevice));
+    cudaStream_t st;  // a private stream: no legacy-stream synchronisation
+    ME_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    const cudaError_t e1 = cudaMemcpyAsync(g_dev[dev].d_tab, g_host_tab, sizeof(ColourTables), cudaMemcpyHostToDevice, st);
+    const cudaError_t e2 = cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+    ME_CUDA(e1);
+    ME_CUDA(e2);
     g_dev[dev].ready = true;
   }
   *d_tab = g_dev[dev].d_tab;
@@ -493,7 +502,7 @@ void me_default_params(me_params* p) {
   p->xi_thr = 1e-3;
   p->y_thr = 1e-3;
   p->tol = 1e-5;
-  p->me_eps = 8e-7;
+  p->me_eps = 4e-7;
   p->device = 0;
   p->lanes_per_event = 0;
 }
@@ -532,8 +541,6 @@ int me_init(const char* process, const me_params* params, me_handle** out) {
     me_destroy(h);
     return fail(ME_ERR_OOM, "me_init: allocation failed");
   }
-  cudaMemset(h->d_acc, 0, 3 * sizeof(double));
-  cudaMemset(h->d_nresc, 0, sizeof(int));
   KParams& kp = h->kp;
   std::memset(&kp, 0, sizeof(kp));
   kp.cp.gs = std::sqrt(4.0 * M_PI * params->alpha_s);
@@ -549,7 +556,11 @@ int me_init(const char* process, const me_params* params, me_handle** out) {
   kp.me_eps = params->me_eps;
   kp.tol = params->tol;
   kp.tab = d_tab;
-  if (cudaDeviceSynchronize() != cudaSuccess) {
+  // stream-ordered on the handle's own stream: no device-wide synchronisation, so a
+  // handle can be created while other threads capture CUDA graphs
+  if (cudaMemsetAsync(h->d_acc, 0, 3 * sizeof(double), h->own_stream) != cudaSuccess ||
+      cudaMemsetAsync(h->d_nresc, 0, sizeof(int), h->own_stream) != cudaSuccess ||
+      cudaStreamSynchronize(h->own_stream) != cudaSuccess) {
     me_destroy(h);
     return fail(ME_ERR_CUDA, "me_init: device error");
   }
@@ -630,8 +641,8 @@ static int run(me_handle* h, int kind, double nlo_factor, const double* momenta,
     ME_CUDA(dispatch(h->proc->pid, kind, true, lpe64, r, h->stream));
   }
   if (timed) ME_CUDA(cudaEventRecord(ev[2], h->stream));
-  k_partials<<<RED_BLOCKS, 256, 0, h->stream>>>(O, n, h->d_part);
-  k_finish<<<1, 32, 0, h->stream>>>(h->d_part, RED_BLOCKS, h->d_acc, n);
+  k_partials<<<RED_BLOCKS, 256, 0, h->stream>>>(O, n, h->d_part, nullptr);
+  k_finish<<<1, 32, 0, h->stream>>>(h->d_part, RED_BLOCKS, h->d_acc, n, nullptr);
   ME_CUDA(cudaGetLastError());
   if (timed) ME_CUDA(cudaEventRecord(ev[3], h->stream));
   if (!dout) ME_CUDA(cudaMemcpyAsync(out, O, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -643,12 +654,17 @@ int me_eval_born(me_handle* h, const double* momenta, const double* ps_weights, 
   return run(h, K_TREE, 1.0, momenta, ps_weights, n, out);
 }
 
+// n-body NLO factor of e+e- -> u ubar: 1 + a_s [5 - 2 pi^2/3 - (3 + 4 ln xi_c) ln(delta/2)]
+static double nbody_factor(const me_handle* h) {
+  const double a_s = h->prm.alpha_s * (4.0 / 3.0) / (2.0 * M_PI);
+  const double c = 5.0 - 2.0 * M_PI * M_PI / 3.0 - (3.0 + 4.0 * std::log(h->prm.xi_cut)) * std::log(0.5 * h->prm.delta);
+  return 1.0 + a_s * c;
+}
+
 int me_eval_nbody_nlo(me_handle* h, const double* momenta, const double* ps_weights, int64_t n, double* out) {
   if (!h) return fail(ME_ERR_ARG, "NULL handle");
   if (h->proc->pid != P_EE_UU) return fail(ME_ERR_PROCESS, "me_eval_nbody_nlo: only defined for ee_uu");
-  const double a_s = h->prm.alpha_s * (4.0 / 3.0) / (2.0 * M_PI);
-  const double c = 5.0 - 2.0 * M_PI * M_PI / 3.0 - (3.0 + 4.0 * std::log(h->prm.xi_cut)) * std::log(0.5 * h->prm.delta);
-  return run(h, K_TREE, 1.0 + a_s * c, momenta, ps_weights, n, out);
+  return run(h, K_TREE, nbody_factor(h), momenta, ps_weights, n, out);
 }
 
 int me_eval_real_subtracted(me_handle* h, const double* momenta, const double* ps_weights, int64_t n, double* out) {
@@ -742,6 +758,70 @@ void me_destroy(me_handle* h) {
 }
 
 }  // extern "C"
+
+// kernel kind and Born factor of an ME_KIND_* request
+static int kind_of(const me_handle* h, int me_kind, double* nlo) {
+  *nlo = 1.0;
+  if (me_kind == ME_KIND_REAL_SUBTRACTED) {
+    if (h->proc->born_pid < 0) return -1;
+    return K_REAL;
+  }
+  if (me_kind == ME_KIND_NBODY_NLO) {
+    if (h->proc->pid != P_EE_UU) return -1;
+    *nlo = nbody_factor(h);
+  }
+  return K_TREE;
+}
+
+int me_internal_prepare_counted(me_handle* h, int me_kind, int64_t cap) {
+  double nlo;
+  const int kind = kind_of(h, me_kind, &nlo);
+  if (kind < 0) return fail(ME_ERR_PROCESS, "counted launch: kind not defined for the process");
+  const bool mixed = h->prm.precision == ME_PREC_MIXED;
+  if (!h->lpe[kind][mixed ? 0 : 1] || (kind == K_REAL && mixed && !h->lpe[kind][1]))
+    return fail(ME_ERR_ARG, "counted launch: run one ordinary call of this kind first");
+  ME_CUDA(cudaSetDevice(h->device));
+  return ensure_capacity(h, (size_t)cap);
+}
+
+int me_internal_launch_counted(me_handle* h, int me_kind, const double* d_p, const double* d_w, int64_t cap,
+                               const int* d_n, double* d_out) {
+  double nlo;
+  const int kind = kind_of(h, me_kind, &nlo);
+  const bool mixed = h->prm.precision == ME_PREC_MIXED;
+  if (kind < 0 || cap <= 0 || (size_t)cap > h->cap || !d_p || !d_n || !d_out)
+    return fail(ME_ERR_ARG, "counted launch: bad arguments or handle not prepared");
+  const int lpe = h->lpe[kind][mixed ? 0 : 1], lpe64 = h->lpe[kind][1];
+  LaunchArgs a{};
+  a.p = d_p;
+  a.wgt = d_w;
+  a.n = cap;
+  a.out = d_out;
+  a.kp = h->kp;
+  a.kp.nlo_factor = nlo;
+  a.count = d_n;
+  a.groups = cap;
+  a.resc_list = h->d_resc;
+  a.resc_count = h->d_nresc;
+  h->last_kind = K_TREE;
+  if (kind == K_REAL && mixed) {
+    a.kp.flag_unstable = 1;
+    ME_CUDA(cudaMemsetAsync(h->d_nresc, 0, sizeof(int), h->stream));
+    h->last_kind = K_REAL;
+  }
+  ME_CUDA(dispatch(h->proc->pid, kind, !mixed, lpe, a, h->stream));
+  if (kind == K_REAL && mixed) {
+    LaunchArgs r = a;
+    r.kp.flag_unstable = 0;
+    r.idx = h->d_resc;
+    r.count = h->d_nresc;
+    ME_CUDA(dispatch(h->proc->pid, kind, true, lpe64, r, h->stream));
+  }
+  k_partials<<<RED_BLOCKS, 256, 0, h->stream>>>(d_out, cap, h->d_part, d_n);
+  k_finish<<<1, 32, 0, h->stream>>>(h->d_part, RED_BLOCKS, h->d_acc, cap, d_n);
+  ME_CUDA(cudaGetLastError());
+  return ME_OK;
+}
 
 int me_internal_rescued_async(me_handle* h, int* dst) {
   if (!h || !dst) return fail(ME_ERR_ARG, "NULL argument");

@@ -7,6 +7,15 @@
 // Enqueue, on the handle's stream, a copy of the last call's rescue count to `dst`
 // (host-pinned); returns ME_OK or an error code.
 int me_internal_rescued_async(me_handle* h, int* dst);
+// Launches of one batch whose size is read on the device (*d_n <= cap; momenta with
+// stride cap, weights optional): the main kernel, the float64 rescue of the flagged
+// points (mixed precision, subtracted real) and the reduction, on the handle's stream.
+// Allocates nothing and never synchronises, so the sequence can be captured in a CUDA
+// graph and replayed for any batch size up to cap.  me_internal_prepare_counted (outside
+// any capture, after one ordinary call of the kind) sizes the handle's scratch for cap.
+int me_internal_prepare_counted(me_handle* h, int me_kind, int64_t cap);
+int me_internal_launch_counted(me_handle* h, int me_kind, const double* d_p, const double* d_w, int64_t cap,
+                               const int* d_n, double* d_out);
 // Process id (index into the library's process table) of a name, or -1.
 int me_internal_process_id(const char* name);
 // Record the thread-local message returned by me_last_error(); returns `code`.

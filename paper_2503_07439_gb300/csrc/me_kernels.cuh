@@ -105,8 +105,9 @@ __device__ __forceinline__ void load_event(const double* __restrict__ p, long n,
 }
 
 // ---------------------------------------------------------------- tree |M|^2
-// out[i] = wgt[i] * |M|^2(p_i) * nlo_factor.  `idx` (optional): event list to process;
-// `count` then holds its length on the device.
+// out[i] = wgt[i] * |M|^2(p_i) * nlo_factor.  `count` (optional): the number of events,
+// read on the device; `idx` (optional): the list of events to process (its length in
+// `count`).  Momenta have stride n either way.
 // g g -> t tbar g g in float32 does its 24-flow colour sums on the tensor cores: each
 // lane holds one (event, helicity) row, the warp contracts its 32 rows with the colour
 // matrix in one bf16 mma sequence (me_tc.cuh).  All lanes then run the same number of
@@ -120,7 +121,7 @@ __global__ void __launch_bounds__(128, ME_MINB) k_tree(const double* __restrict_
   constexpr bool TC = (PID == P_GG_TTGG) && std::is_same<T, float>::value;
   const long gid = ((long)blockIdx.x * blockDim.x + threadIdx.x) / LPE;
   const int lane = threadIdx.x % LPE;
-  const long nev = idx ? (long)*count : n;
+  const long nev = count ? (long)*count : n;
   if constexpr (!TC) {
     if (gid >= nev) return;
     const long ev = idx ? (long)idx[gid] : gid;
@@ -171,18 +172,216 @@ __global__ void __launch_bounds__(128, ME_MINB) k_tree(const double* __restrict_
   }
 }
 
+// ---------------------------------------------------------------- g g -> t tbar g g, float32, tensor cores
+// Four lanes share one event and one helicity block at a time (me_procs.cuh: the gluon
+// helicities fixed, the four (t, tbar) helicities open):
+//  1. the 34 gluon four-vectors of the block -- polarisations e[4], ordered currents
+//     J(xy) (6, x < y), J(xyz) (12, one of each reversed pair), J(wxyz) (12, w < z) --
+//     are built cooperatively (a quarter each) into the event's shared-memory area;
+//  2. lane w extends the quark line for the six orderings that start with gluon w,
+//     U(w) -> U(wx) -> U(wxy), for both top helicities, and writes the partial
+//     amplitudes of both antitop helicities into shared-memory rows;
+//  3. one warp-wide tensor-core colour sum (me_tc.cuh) takes the warp's 32 rows
+//     (8 events x 4 heavy-pair helicities): lane 4e + h receives helicity h of event e.
+// Everything a lane needs stays on chip, so the 5e5 flops of an event run from registers
+// and shared memory.  In a warp that holds the end of the batch, events past it compute
+// a fixed finite configuration and are discarded, so every warp-wide step stays
+// converged; warps entirely past the end return at once.
+constexpr int TC4_EV_FLOATS = 276;  // 34 four-vectors x 8 floats, padded so 8 events hit distinct banks
+constexpr int TC4_ROW = 25;         // floats per amplitude row (24 flows, padded)
+constexpr int TC4_WARP_FLOATS = 8 * TC4_EV_FLOATS + 2 * 32 * TC4_ROW;
+constexpr int TC4_SMEM_PER_WARP = TC4_WARP_FLOATS * 4 + TC_SMEM_PER_WARP;
+constexpr int TC4_THREADS = 128;
+constexpr int TC4_SMEM = (TC4_THREADS / 32) * TC4_SMEM_PER_WARP;
+
+// J(xyz) representatives, slot t = 3 * (missing gluon) + (position of the middle gluon
+// among the three in increasing order); packed x | y << 4 | z << 8, x < z
+__constant__ short kJ3Rep[12] = {0x312, 0x321, 0x231, 0x302, 0x320, 0x230,
+                                 0x301, 0x310, 0x130, 0x201, 0x210, 0x120};
+// J(wxyz) representatives (w < z), enumerated by w, then x, then y: packed w | x<<4 | y<<8 | z<<12
+__constant__ short kJ4Rep[12] = {0x3210, 0x2310, 0x3120, 0x1320, 0x2130, 0x1230,
+                                 0x3201, 0x2301, 0x3021, 0x2031, 0x3102, 0x3012};
+// ordering f (lexicographic) -> +-(1 + representative of J(wxyz)); minus: reversed, J = -J(rep)
+__constant__ signed char kJ4OfOrdering[24] = {1,  2,  3,   4,  5,  6,  7,   8,  9,  -6, 10, -4,
+                                              11, -10, 12, -5, -8, -2, -12, -9, -11, -3, -7, -1};
+
+__device__ __forceinline__ void st_c4(float* b, int slot, const c4<float>& v) {
+  float4* p = reinterpret_cast<float4*>(b + 8 * slot);
+  p[0] = make_float4(v.v[0].re, v.v[0].im, v.v[1].re, v.v[1].im);
+  p[1] = make_float4(v.v[2].re, v.v[2].im, v.v[3].re, v.v[3].im);
+}
+__device__ __forceinline__ c4<float> ld_c4(const float* b, int slot) {
+  const float4* p = reinterpret_cast<const float4*>(b + 8 * slot);
+  const float4 a = p[0], c = p[1];
+  return c4<float>{{{a.x, a.y}, {a.z, a.w}, {c.x, c.y}, {c.z, c.w}}};
+}
+__device__ __forceinline__ int pair_slot(int x, int y) {  // x < y
+  return 4 + (x == 0 ? y - 1 : (x == 1 ? y + 1 : 5));
+}
+__device__ __forceinline__ c4<float> ld_j2(const float* b, int x, int y) {
+  c4<float> J = ld_c4(b, pair_slot(x < y ? x : y, x < y ? y : x));
+  if (x > y) cscale(J, -1.0f);
+  return J;
+}
+__device__ __forceinline__ int triple_slot(int x, int y, int z) {  // any order: J(zyx) = J(xyz)
+  const int miss = 6 - x - y - z;
+  const int a = miss == 0 ? 1 : 0, c = miss == 3 ? 2 : 3;
+  return 10 + 3 * miss + (y == a ? 0 : (y == c ? 2 : 1));
+}
+
+template <int LPE>
+__global__ void __launch_bounds__(TC4_THREADS, 2) k_tree_tc4(const double* __restrict__ p, const double* __restrict__ wgt,
+                                                             long n, double* __restrict__ out, KParams kp,
+                                                             const int* __restrict__ idx, const int* __restrict__ count) {
+  static_assert(LPE == 4, "four lanes per event");
+  constexpr int PID = P_GG_TTGG;
+  extern __shared__ __align__(16) float tc4_smem[];
+  const int warp = threadIdx.x >> 5, wl = threadIdx.x & 31;
+  float* wsm = tc4_smem + warp * (TC4_SMEM_PER_WARP / 4);
+  float* cur = wsm + (wl >> 2) * TC4_EV_FLOATS;         // this event's four-vectors
+  float* are = wsm + 8 * TC4_EV_FLOATS;                 // amplitude rows, real parts [32][TC4_ROW]
+  float* aim = are + 32 * TC4_ROW;                      // imaginary parts
+  unsigned char* stage = reinterpret_cast<unsigned char*>(wsm + TC4_WARP_FLOATS);
+  const long gid = ((long)blockIdx.x * blockDim.x + threadIdx.x) / 4;
+  const int lane = threadIdx.x & 3;
+  const long nev = count ? (long)*count : n;
+  // a warp whose eight events all lie past the batch leaves together (every
+  // synchronisation below is warp-wide), so a grid sized for a capacity costs little
+  if (((long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u)) / 4 >= nev) return;
+  const bool active = gid < nev;
+  const long ev = active ? (idx ? (long)idx[gid] : gid) : 0;
+  r4<double> k[6];
+  if (active) {
+    load_event<6>(p, n, ev, k);
+  } else {
+    const double d[6][4] = {{1000, 0, 0, 1000},     {1000, 0, 0, -1000},     {600, 100, 200, 300},
+                            {700, -150, -100, 200}, {400, 30, -80, -300}, {300, 20, -20, -200}};
+#pragma unroll
+    for (int l = 0; l < 6; ++l) k[l] = r4<double>{d[l][0], d[l][1], d[l][2], d[l][3]};
+  }
+  const TcColourB cb = tc_load_colour(kp.tab->C[PID]);
+  const Kin<PID, float> K = prepare<PID, float>(k, kp.cp);
+  const float g = (float)kp.cp.gs, mt = (float)kp.cp.mt;
+  const r4<float>* q = K.q;
+  const r4<float> kt = K.pl[2];
+  const c4<float> v[2] = {spinor_v_of(K.wtb, -1), spinor_v_of(K.wtb, 1)};
+  constexpr int LEG[4] = {0, 1, 4, 5};
+  float acc = 0.0f;
+  for (int b = 0; b < n_live_blocks<PID>(); ++b) {
+    const int hb = live_block_hel<PID>(b);
+    // 1. polarisation of gluon `lane`
+    st_c4(cur, lane, polvec_of(K.wg[lane], hel_of(hb, LEG[lane]), LEG[lane] >= 2));
+    __syncwarp();
+    // 2. pair currents: slots 4 + lane and 8 + lane (< 10)
+    for (int pp = lane; pp < 6; pp += 4) {
+      const int x = pp < 3 ? 0 : (pp < 5 ? 1 : 2);
+      const int y = pp < 3 ? pp + 1 : (pp < 5 ? pp - 1 : 3);
+      c4<float> J = vvv(ld_c4(cur, x), ld_c4(cur, y), -q[x], -q[y]);
+      cscale(J, -g * K.ig[(1 << x) | (1 << y)]);
+      st_c4(cur, 4 + pp, J);
+    }
+    __syncwarp();
+    // 3. triple currents
+    for (int t = lane; t < 12; t += 4) {
+      const int r = kJ3Rep[t], x = r & 15, y = (r >> 4) & 15, z = r >> 8;
+      const int S = (1 << x) | (1 << y) | (1 << z);
+      const c4<float> ex = ld_c4(cur, x), ey = ld_c4(cur, y), ez = ld_c4(cur, z);
+      c4<float> J = vvv(ex, ld_j2(cur, y, z), -q[x], -(q[y] + q[z]));
+      cadd(J, vvv(ld_j2(cur, x, y), ez, -(q[x] + q[y]), -q[z]));
+      cscale(J, -g * K.ig[S]);
+      caxpy(J, cx<float>{g * g * K.ig[S], 0.0f}, vvvv_ordered(ex, ey, ez));
+      st_c4(cur, 10 + t, J);
+    }
+    __syncwarp();
+    // 4. quadruple currents
+    for (int t = lane; t < 12; t += 4) {
+      const int r = kJ4Rep[t], w = r & 15, x = (r >> 4) & 15, y = (r >> 8) & 15, z = r >> 12;
+      const c4<float> ew = ld_c4(cur, w), ez = ld_c4(cur, z);
+      const c4<float> jwx = ld_j2(cur, w, x), jxy = ld_j2(cur, x, y), jyz = ld_j2(cur, y, z);
+      c4<float> J = vvv(ew, ld_c4(cur, triple_slot(x, y, z)), -q[w], -(q[x] + q[y] + q[z]));
+      cadd(J, vvv(jwx, jyz, -(q[w] + q[x]), -(q[y] + q[z])));
+      cadd(J, vvv(ld_c4(cur, triple_slot(w, x, y)), ez, -(q[w] + q[x] + q[y]), -q[z]));
+      cscale(J, -g * K.ig[15]);
+      c4<float> V = vvvv_ordered(ew, ld_c4(cur, x), jyz);
+      cadd(V, vvvv_ordered(ew, jxy, ez));
+      cadd(V, vvvv_ordered(jwx, ld_c4(cur, y), ez));
+      caxpy(J, cx<float>{g * g * K.ig[15], 0.0f}, V);
+      st_c4(cur, 22 + t, J);
+    }
+    __syncwarp();
+    // 5. quark line for the orderings starting with gluon w = lane
+    const int w = lane;
+    for (int ht = 0; ht < 2; ++ht) {
+      const c4<float> ub = dbar(spinor_u_of(K.wt, ht ? 1 : -1));
+      const int row0 = (wl & ~3) + 2 * ht;  // rows of (this event, ht, hv = 0 / 1)
+      c4<float> U1 = row_prop(row_slash(ub, ld_c4(cur, w)), kt + q[w], mt);
+      cscale(U1, -g * K.iq[1 << w]);
+      int f = 6 * w;
+      for (int x = 0; x < 4; ++x) {
+        if (x == w) continue;
+        c4<float> r2 = row_slash(ub, ld_j2(cur, w, x));
+        cadd(r2, row_slash(U1, ld_c4(cur, x)));
+        c4<float> U2 = row_prop(r2, kt + q[w] + q[x], mt);
+        cscale(U2, -g * K.iq[(1 << w) | (1 << x)]);
+        for (int y = 0; y < 4; ++y) {
+          if (y == w || y == x) continue;
+          const int z = 6 - w - x - y;
+          c4<float> r3 = row_slash(ub, ld_c4(cur, triple_slot(w, x, y)));
+          cadd(r3, row_slash(U1, ld_j2(cur, x, y)));
+          cadd(r3, row_slash(U2, ld_c4(cur, y)));
+          c4<float> U3 = row_prop(r3, kt + q[w] + q[x] + q[y], mt);
+          cscale(U3, -g * K.iq[(1 << w) | (1 << x) | (1 << y)]);
+          const int s4 = kJ4OfOrdering[f];
+          c4<float> R = row_slash(ub, ld_c4(cur, 22 + (s4 > 0 ? s4 : -s4) - 1));
+          if (s4 < 0) cscale(R, -1.0f);
+          cadd(R, row_slash(U1, ld_c4(cur, triple_slot(x, y, z))));
+          cadd(R, row_slash(U2, ld_j2(cur, y, z)));
+          cadd(R, row_slash(U3, ld_c4(cur, z)));
+#pragma unroll
+          for (int hv = 0; hv < 2; ++hv) {
+            const cx<float> a = times_i(spdot(R, v[hv])) * g;
+            are[(row0 + hv) * TC4_ROW + f] = a.re;
+            aim[(row0 + hv) * TC4_ROW + f] = a.im;
+          }
+          ++f;
+        }
+      }
+    }
+    __syncwarp();
+    // 6. colour sum of row wl (this event, heavy-pair helicity lane) on the tensor cores
+    cx<float> J[TC_NF];
+#pragma unroll
+    for (int fl = 0; fl < TC_NF; ++fl) J[fl] = cx<float>{are[wl * TC4_ROW + fl], aim[wl * TC4_ROW + fl]};
+    const float sres = tc_colour_sum(J, cb, stage);
+    if (active) acc += sres;
+    __syncwarp();
+  }
+  const double tot = 2.0 * (double)group_sum<4>(acc, group_mask<4>());
+  if (active && lane == 0) {
+    const double w8 = wgt ? wgt[ev] : 1.0;
+    out[ev] = w8 * tot * kp.avg_inv * kp.nlo_factor;
+  }
+}
+
 // ---------------------------------------------------------------- FKS kinematics (double)
-__device__ __forceinline__ r4<double> boost(const r4<double>& p, double bx, double by, double bz) {
-  const double b2 = bx * bx + by * by + bz * bz;
-  const double g = 1.0 / sqrt(1.0 - b2);
-  const double bp = bx * p.x + by * p.y + bz * p.z;
-  const double g2 = b2 > 0.0 ? (g - 1.0) / b2 : 0.0;
-  const double c = g2 * bp + g * p.e;
-  return r4<double>{g * (p.e + bp), p.x + c * bx, p.y + c * by, p.z + c * bz};
+// Float64 throughout (the maps fix the counter-event kinematics that the subtraction
+// compares with the real).  GB300 issues float64 at 1/64 of the float32 rate, and a
+// float64 division or square root costs ~10 pipe instructions, so the maps use reciprocal
+// square roots and shared reciprocals, and boost with the system momentum and mass.
+
+// p (given in the rest frame of a system with momentum Q, mass M) in the frame where the
+// system has momentum Q:  E' = (E Q0 + Q.p)/M,  p' = p + Q (E' + E)/(Q0 + M).
+// sgn = -1 boosts the other way (from the frame of Q into its rest frame).
+__device__ __forceinline__ r4<double> boost_by(const r4<double>& p, const r4<double>& Q, double inv_m, double m,
+                                               double sgn) {
+  const double qp = Q.x * p.x + Q.y * p.y + Q.z * p.z;
+  const double e = (p.e * Q.e + sgn * qp) * inv_m;
+  const double c = sgn * (e + p.e) / (Q.e + m);
+  return r4<double>{e, p.x + c * Q.x, p.y + c * Q.y, p.z + c * Q.z};
 }
 
 __device__ __forceinline__ void unit3(const r4<double>& p, double& x, double& y, double& z) {
-  const double a = 1.0 / sqrt(p.x * p.x + p.y * p.y + p.z * p.z);
+  const double a = rsqrt(p.x * p.x + p.y * p.y + p.z * p.z);
   x = p.x * a;
   y = p.y * a;
   z = p.z * a;
@@ -202,7 +401,7 @@ struct IsrKin {
 };
 
 __device__ __forceinline__ void isr_map(const r4<double>* k, double mass, IsrKin& o) {
-  const double rs = k[0].e + k[1].e, s = rs * rs;
+  const double rs = k[0].e + k[1].e, s = rs * rs, is = 1.0 / s;
   o.xi = 2.0 * k[4].e / rs;
   unit3(k[4], o.qdir[0], o.qdir[1], o.qdir[2]);
   double b0[3], b1[3];
@@ -211,25 +410,29 @@ __device__ __forceinline__ void isr_map(const r4<double>* k, double mass, IsrKin
   o.y[0] = o.qdir[0] * b0[0] + o.qdir[1] * b0[1] + o.qdir[2] * b0[2];
   o.y[1] = o.qdir[0] * b1[0] + o.qdir[1] * b1[1] + o.qdir[2] * b1[2];
   const double d0 = 1.0 - o.y[0], d1 = 1.0 - o.y[1];
-  o.S[0] = d1 / (d0 + d1);
-  o.S[1] = d0 / (d0 + d1);
-  const double pt = sqrt(o.qdir[0] * o.qdir[0] + o.qdir[1] * o.qdir[1]);
-  o.cphi = pt > 0.0 ? o.qdir[0] / pt : 1.0;
-  o.sphi = pt > 0.0 ? o.qdir[1] / pt : 0.0;
+  const double idd = 1.0 / (d0 + d1);
+  o.S[0] = d1 * idd;
+  o.S[1] = d0 * idd;
+  const double pt2 = o.qdir[0] * o.qdir[0] + o.qdir[1] * o.qdir[1];
+  const double ipt = pt2 > 0.0 ? rsqrt(pt2) : 0.0;
+  o.cphi = pt2 > 0.0 ? o.qdir[0] * ipt : 1.0;
+  o.sphi = pt2 > 0.0 ? o.qdir[1] * ipt : 0.0;
   // heavy-pair rest-frame direction of the quark
   const r4<double> Q = k[0] + k[1] - k[4];
-  const r4<double> ks = boost(k[2], -Q.x / Q.e, -Q.y / Q.e, -Q.z / Q.e);
+  const double Q2 = mdot(Q, Q), iMQ = rsqrt(Q2);
+  const r4<double> ks = boost_by(k[2], Q, iMQ, Q2 * iMQ, -1.0);
   double n[3];
   unit3(ks, n[0], n[1], n[2]);
-  const double beta = sqrt(1.0 - 4.0 * mass * mass / s);
+  const double m4 = 4.0 * mass * mass;
+  const double beta = sqrt(1.0 - m4 * is);
   o.soft[0] = k[0];
   o.soft[1] = k[1];
   const double e = 0.5 * rs, pa = 0.5 * rs * beta;
   o.soft[2] = r4<double>{e, pa * n[0], pa * n[1], pa * n[2]};
   o.soft[3] = r4<double>{e, -pa * n[0], -pa * n[1], -pa * n[2]};
   const double z = 1.0 - o.xi;
-  const double M = sqrt(s * z);
-  const double bQ = sqrt(fmax(0.0, 1.0 - 4.0 * mass * mass / (s * z)));
+  const double sz = s * z, iM = rsqrt(sz), M = sz * iM;
+  const double bQ = sqrt(fmax(0.0, 1.0 - m4 * is / z));
   const double eQ = 0.5 * M, pQ = 0.5 * M * bQ;
   const r4<double> tr{eQ, pQ * n[0], pQ * n[1], pQ * n[2]};
   const r4<double> tbr{eQ, -pQ * n[0], -pQ * n[1], -pQ * n[2]};
@@ -238,12 +441,13 @@ __device__ __forceinline__ void isr_map(const r4<double>* k, double mass, IsrKin
     o.coll[j][0] = j == 0 ? scale(z, k[0]) : k[0];
     o.coll[j][1] = j == 1 ? scale(z, k[1]) : k[1];
     const r4<double> Qc = o.coll[j][0] + o.coll[j][1];
-    const double bx = Qc.x / Qc.e, by = Qc.y / Qc.e, bz = Qc.z / Qc.e;
-    o.coll[j][2] = boost(tr, bx, by, bz);
-    o.coll[j][3] = boost(tbr, bx, by, bz);
+    const double Mc2 = mdot(Qc, Qc), iMc = rsqrt(Mc2);
+    o.coll[j][2] = boost_by(tr, Qc, iMc, Mc2 * iMc, 1.0);
+    o.coll[j][3] = boost_by(tbr, Qc, iMc, Mc2 * iMc, 1.0);
   }
-  o.K = s * bQ / (64.0 * PI * PI * PI * beta);
-  o.K0 = s / (64.0 * PI * PI * PI);
+  constexpr double i64pi3 = 1.0 / (64.0 * PI * PI * PI);
+  o.K = s * bQ * i64pi3 / beta;
+  o.K0 = s * i64pi3;
 }
 
 // Final-state FKS sectors (i = gluon leg 4, j = leg 2 or 3) of massless 2 -> 3.
@@ -301,7 +505,7 @@ __global__ void __launch_bounds__(128, ME_MINB) k_real_sub(const double* __restr
   constexpr int BNF = Proc<BPID>::NFLOW;
   const long gid = ((long)blockIdx.x * blockDim.x + threadIdx.x) / LPE;
   const int lane = threadIdx.x % LPE;
-  const long nev = idx ? (long)*count : n;
+  const long nev = count ? (long)*count : n;
   if (gid >= nev) return;
   const long ev = idx ? (long)idx[gid] : gid;
   const unsigned mask = group_mask<LPE>();
@@ -321,10 +525,13 @@ __global__ void __launch_bounds__(128, ME_MINB) k_real_sub(const double* __restr
   const double R = 2.0 * (double)group_sum<LPE>(accR, mask) * kp.avg_inv;
 
   double W = 0.0, mag = 0.0;
+  double ysec[2] = {-1.0, -1.0};  // y_j of both sectors (collinear resolution of the flag)
   bool near = false;
   if constexpr (PID == P_EE_UUG) {
     FsrKin f;
     fsr_map(k, f);
+    ysec[0] = f.y[0];
+    ysec[1] = f.y[1];
     T aB[2] = {T(0), T(0)};
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
@@ -345,25 +552,34 @@ __global__ void __launch_bounds__(128, ME_MINB) k_real_sub(const double* __restr
       const double Gc = f.K1 * (2.0 / (s * (1.0 - f.xi))) * 2.0 * g2 * CF_ * (1.0 + (1.0 - f.xi) * (1.0 - f.xi)) * B[j];
       const double Gsc = f.K0 * (2.0 / s) * 2.0 * g2 * 2.0 * CF_ * B[j];
       const double th_c = f.y[j] > 1.0 - kp.delta ? 1.0 : 0.0;
-      const double ct = (th_s * Gs + th_c * Gc - th_s * th_c * Gsc) / (f.xi * f.xi * (1.0 - f.y[j]) * f.K[j]);
+      const double iden = 1.0 / (f.xi * f.xi * (1.0 - f.y[j]) * f.K[j]);
+      const double ct = (th_s * Gs + th_c * Gc - th_s * th_c * Gsc) * iden;
       const double rsj = R * f.S[j];
       W += rsj - ct;
-      mag += fabs(rsj) + fabs(ct);
+      // error scale: the real, the collinear term, and the soft pair (whose Borns are shared)
+      mag += fabs(rsj) + fabs(th_c * Gc * iden) + fabs(th_s * (Gs - th_c * Gsc) * iden);
       near |= (th_s > 0.0 && f.xi < kp.xi_thr) || (th_c > 0.0 && 1.0 - f.y[j] < kp.y_thr);
     }
   } else {
     IsrKin f;
     isr_map(k, kp.cp.mt, f);
+    ysec[0] = f.y[0];
+    ysec[1] = f.y[1];
     // eikonal-weighted colour-correlation matrix E = sum_{k,l} w_kl C^{kl} (2x2)
     const int ci = (BPID == P_GG_TT) ? 0 : 1;
     double E[4] = {0.0, 0.0, 0.0, 0.0};
     {
+      // w_ab = (p_a.p_b) / ((p_a.q)(p_b.q)), q = (1, gluon direction): four reciprocals
+      const r4<double> qq{1.0, f.qdir[0], f.qdir[1], f.qdir[2]};
+      double iaq[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) iaq[a] = 1.0 / mdot(f.soft[a], qq);
       int pr = 0;
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = a; b < 4; ++b, ++pr) {
-          const double w = eik(f.soft[a], f.soft[b], f.qdir) * (a == b ? 1.0 : 2.0);
+          const double w = mdot(f.soft[a], f.soft[b]) * iaq[a] * iaq[b] * (a == b ? 1.0 : 2.0);
 #pragma unroll
           for (int q = 0; q < 4; ++q) E[q] += w * kp.tab->Ccorr[ci][pr][q];
         }
@@ -414,26 +630,31 @@ __global__ void __launch_bounds__(128, ME_MINB) k_real_sub(const double* __restr
       Bp[0] = (double)group_sum<LPE>(aP[0], mask) * bav;
       Bp[1] = (double)group_sum<LPE>(aP[1], mask) * bav;
     }
-    const double xi = f.xi, z = 1.0 - xi;
+    const double xi = f.xi, z = 1.0 - xi, iz = 1.0 / z, is2 = 2.0 / s;
     const double th_s = xi < kp.xi_cut ? 1.0 : 0.0;
+    // 1 / (xi^2 (1 - y_j) K) of both sectors from one reciprocal
+    const double den0 = xi * xi * (1.0 - f.y[0]) * f.K, den1 = xi * xi * (1.0 - f.y[1]) * f.K;
+    const double rden = 1.0 / (den0 * den1);
+    const double iden[2] = {den1 * rden, den0 * rden};
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
       const double Gs = (1.0 - f.y[j]) * f.S[j] * f.K0 * x2R;
       double xiP, xiP0;
       if constexpr (BPID == P_GG_TT) {
-        xiP = 2.0 * CA_ * ((z + xi * xi * z) * Bc + 2.0 * (xi * xi / z) * Bp[j]);
+        xiP = 2.0 * CA_ * ((z + xi * xi * z) * Bc + 2.0 * (xi * xi * iz) * Bp[j]);
         xiP0 = 2.0 * CA_ * Bs;
       } else {
         xiP = CF_ * (1.0 + z * z) * Bc;
         xiP0 = 2.0 * CF_ * Bs;
       }
-      const double Gc = f.K * (2.0 / s) * (1.0 / z) * 2.0 * g2 * xiP;
-      const double Gsc = f.K0 * (2.0 / s) * 2.0 * g2 * xiP0;
+      const double Gc = f.K * is2 * iz * 2.0 * g2 * xiP;
+      const double Gsc = f.K0 * is2 * 2.0 * g2 * xiP0;
       const double th_c = f.y[j] > 1.0 - kp.delta ? 1.0 : 0.0;
-      const double ct = (th_s * Gs + th_c * Gc - th_s * th_c * Gsc) / (xi * xi * (1.0 - f.y[j]) * f.K);
+      const double ct = (th_s * Gs + th_c * Gc - th_s * th_c * Gsc) * iden[j];
       const double rsj = R * f.S[j];
       W += rsj - ct;
-      mag += fabs(rsj) + fabs(ct);
+      // error scale: the real, the collinear term, and the soft pair (whose Borns are shared)
+      mag += fabs(rsj) + fabs(th_c * Gc * iden[j]) + fabs(th_s * (Gs - th_c * Gsc) * iden[j]);
       near |= (th_s > 0.0 && xi < kp.xi_thr) || (th_c > 0.0 && 1.0 - f.y[j] < kp.y_thr);
     }
   }
@@ -441,8 +662,12 @@ __global__ void __launch_bounds__(128, ME_MINB) k_real_sub(const double* __restr
     const double w = wgt ? wgt[ev] : 1.0;
     out[ev] = w * W;
     if (kp.flag_unstable) {
-      // cancellation test: the bulk-precision error of W is ~ me_eps (|R S| + |CT|)
-      const bool unstable = near || !(mag * kp.me_eps <= kp.tol * fabs(W));
+      // cancellation test: the bulk-precision error of W is ~ me_eps x (error scale); the
+      // float32 amplitude error per unit scale grows towards the collinear limit, as
+      // 1 + sqrt(rho_0 / rho) with rho = min_j (1 - y_j), rho_0 = 0.01
+      const float rho = fmaxf((float)fmin(1.0 - ysec[0], 1.0 - ysec[1]), 1e-30f);
+      const double grow = 1.0 + (double)sqrtf(0.01f / rho);
+      const bool unstable = near || !(mag * grow * kp.me_eps <= kp.tol * fabs(W));
       if (unstable) {
         const int slot = atomicAdd(resc_count, 1);
         resc_list[slot] = (int)ev;
@@ -454,8 +679,10 @@ __global__ void __launch_bounds__(128, ME_MINB) k_real_sub(const double* __restr
 // ---------------------------------------------------------------- weight accumulation
 // Deterministic two-pass reduction: per-block partial (sum w, sum w^2) in a fixed tree
 // order, then one block adds the partials in block order.  No floating atomics.
-__global__ void k_partials(const double* __restrict__ w, long n, double* __restrict__ part);
-__global__ void k_finish(const double* __restrict__ part, int nblk, double* __restrict__ acc, long n);
+// `cnt` (optional, device): the number of points, read on the device (at most n).
+__global__ void k_partials(const double* __restrict__ w, long n, double* __restrict__ part, const int* __restrict__ cnt);
+__global__ void k_finish(const double* __restrict__ part, int nblk, double* __restrict__ acc, long n,
+                         const int* __restrict__ cnt);
 
 // ---------------------------------------------------------------- launch registry
 struct LaunchArgs {
@@ -465,7 +692,7 @@ struct LaunchArgs {
   double* out;
   KParams kp;
   const int* idx;    // optional event list (rescue), length *count on the device
-  const int* count;
+  const int* count;  // optional number of events, read on the device (events 0..*count-1 without idx)
   int* resc_list;    // real kernel in bulk precision: unstable points are appended here
   int* resc_count;
   long groups;       // number of event groups to launch (n, or the list capacity)
@@ -474,12 +701,29 @@ enum KernelKind : int { K_TREE = 0, K_REAL = 1 };
 
 template <int PID, typename T, int LPE>
 cudaError_t launch_one(int kind, const LaunchArgs& a, cudaStream_t st) {
+  (void)cudaGetLastError();  // the launch status below must not report an earlier call's error
   const int threads = 128;
   const long total = a.groups * LPE;
   const long blocks = (total + threads - 1) / threads;
   if (blocks <= 0) return cudaSuccess;
   if (kind == K_TREE) {
-    k_tree<PID, T, LPE><<<(unsigned)blocks, threads, 0, st>>>(a.p, a.wgt, a.n, a.out, a.kp, a.idx, a.count);
+    if constexpr (PID == P_GG_TTGG && std::is_same<T, float>::value) {
+      if constexpr (LPE != 4) {
+        return cudaErrorInvalidValue;
+      } else {
+        static bool attr_set[64] = {};
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (dev < 64 && !attr_set[dev]) {
+          cudaFuncSetAttribute(k_tree_tc4<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC4_SMEM);
+          attr_set[dev] = true;
+        }
+        const long tb = (total + TC4_THREADS - 1) / TC4_THREADS;
+        k_tree_tc4<4><<<(unsigned)tb, TC4_THREADS, TC4_SMEM, st>>>(a.p, a.wgt, a.n, a.out, a.kp, a.idx, a.count);
+      }
+    } else {
+      k_tree<PID, T, LPE><<<(unsigned)blocks, threads, 0, st>>>(a.p, a.wgt, a.n, a.out, a.kp, a.idx, a.count);
+    }
   } else {
     if constexpr (PID == P_EE_UUG || PID == P_GG_TTG || PID == P_UU_TTG)
       k_real_sub<PID, T, LPE><<<(unsigned)blocks, threads, 0, st>>>(a.p, a.wgt, a.n, a.out, a.kp, a.idx, a.count,

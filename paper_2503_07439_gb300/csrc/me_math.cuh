@@ -192,6 +192,91 @@ ME_HD c4<T> polvec(const r4<T>& k, int lam, bool outgoing) {
   return e;
 }
 
+// Helicity-independent ingredients of the wavefunctions, computed once per event and
+// shared by all helicities (the same operations, in the same order, as the routines above).
+// Fermion: omega_+, omega_- and the two-spinor chi_+ = (a, bx + i by), chi_- = (-bx + i by, a).
+template <typename T>
+struct wf_f {
+  T wp, wm, a, bx, by;
+};
+template <typename T>
+ME_HD wf_f<T> wf_fermion(const r4<T>& p, T m) {
+  wf_f<T> w;
+  omegas(p, m, w.wp, w.wm);
+  T pt2 = p.x * p.x + p.y * p.y;
+  T pa = msqrt(pt2 + p.z * p.z);
+  T s = (p.z >= T(0)) ? pa + p.z : pt2 / (pa - p.z);
+  if (s > T(0)) {
+    T rden = T(1) / msqrt(T(2) * pa * s);
+    w.a = s * rden;
+    w.bx = p.x * rden;
+    w.by = p.y * rden;
+  } else {  // exactly along -z
+    w.a = T(0);
+    w.bx = T(1);
+    w.by = T(0);
+  }
+  return w;
+}
+template <typename T>
+ME_HD void chi_of(const wf_f<T>& w, int lam, cx<T>& c0, cx<T>& c1) {
+  if (lam > 0) {
+    c0 = cx<T>{w.a, T(0)};
+    c1 = cx<T>{w.bx, w.by};
+  } else {
+    c0 = cx<T>{-w.bx, w.by};
+    c1 = cx<T>{w.a, T(0)};
+  }
+}
+template <typename T>
+ME_HD c4<T> spinor_u_of(const wf_f<T>& w, int lam) {
+  cx<T> a, b;
+  chi_of(w, lam, a, b);
+  T top = lam > 0 ? w.wm : w.wp, bot = lam > 0 ? w.wp : w.wm;
+  return c4<T>{{top * a, top * b, bot * a, bot * b}};
+}
+template <typename T>
+ME_HD c4<T> spinor_v_of(const wf_f<T>& w, int lam) {
+  cx<T> a, b;
+  chi_of(w, -lam, a, b);
+  T top = lam > 0 ? -w.wp : w.wm;
+  T bot = lam > 0 ? w.wm : -w.wp;
+  return c4<T>{{top * a, top * b, bot * a, bot * b}};
+}
+// Vector: (ct cp, ct sp, st, sp, cp) / sqrt(2) of the momentum direction.
+template <typename T>
+struct wf_v {
+  T ccp, csp, st, sp, cp;
+};
+template <typename T>
+ME_HD wf_v<T> wf_vector(const r4<T>& k) {
+  T pt2 = k.x * k.x + k.y * k.y;
+  T pt = msqrt(pt2);
+  T ka = msqrt(pt2 + k.z * k.z);
+  T ct = k.z / ka, st = pt / ka;
+  T cp = T(1), sp = T(0);
+  if (pt > T(0)) {
+    cp = k.x / pt;
+    sp = k.y / pt;
+  }
+  const T r2 = T(0.70710678118654752440);
+  return wf_v<T>{ct * cp * r2, ct * sp * r2, st * r2, sp * r2, cp * r2};
+}
+template <typename T>
+ME_HD c4<T> polvec_of(const wf_v<T>& w, int lam, bool outgoing) {
+  // eps = (-lam e1 - i e2)/sqrt(2), as polvec
+  c4<T> e;
+  e.v[0] = cx<T>{T(0), T(0)};
+  e.v[1] = cx<T>{lam > 0 ? -w.ccp : w.ccp, w.sp};
+  e.v[2] = cx<T>{lam > 0 ? -w.csp : w.csp, -w.cp};
+  e.v[3] = cx<T>{lam > 0 ? w.st : -w.st, T(0)};
+  if (outgoing) {
+#pragma unroll
+    for (int i = 1; i < 4; ++i) e.v[i] = conj(e.v[i]);
+  }
+  return e;
+}
+
 // ---------------------------------------------------------------- Dirac algebra
 // row spinor times Vslash (V complex, upper index)
 template <typename T>
@@ -204,6 +289,26 @@ ME_HD c4<T> row_slash(const c4<T>& r, const c4<T>& V) {
   o.v[1] = r.v[2] * c + r.v[3] * a;
   o.v[2] = r.v[0] * a - r.v[1] * d;
   o.v[3] = -(r.v[0] * c) + r.v[1] * b;
+  return o;
+}
+// Vslash in the chiral representation is fixed by four combinations of V: a = V0 - V3,
+// b = V0 + V3, c = V1 - i V2, d = V1 + i V2.  A vector that is slashed against many rows
+// is converted once.
+template <typename T>
+struct sl4 {
+  cx<T> a, b, c, d;
+};
+template <typename T>
+ME_HD sl4<T> slashed(const c4<T>& V) {
+  return sl4<T>{V.v[0] - V.v[3], V.v[0] + V.v[3], V.v[1] - times_i(V.v[2]), V.v[1] + times_i(V.v[2])};
+}
+template <typename T>
+ME_HD c4<T> row_slash(const c4<T>& r, const sl4<T>& S) {
+  c4<T> o;
+  o.v[0] = r.v[2] * S.b + r.v[3] * S.d;
+  o.v[1] = r.v[2] * S.c + r.v[3] * S.a;
+  o.v[2] = r.v[0] * S.a - r.v[1] * S.d;
+  o.v[3] = -(r.v[0] * S.c) + r.v[1] * S.b;
   return o;
 }
 // Vslash times column spinor

@@ -76,6 +76,8 @@ struct KinTT {
   r4<T> q[NG];          // outgoing gluon momenta
   T ig[1 << NG];
   T iq[1 << NG];
+  wf_v<T> wg[NG];       // polarisation ingredients of the gluons (legs 0, 1, 4, 5)
+  wf_f<T> wt, wtb;      // spinor ingredients of the top and the antitop
 };
 
 template <typename T, int NG>
@@ -87,20 +89,31 @@ ME_HD KinTT<T, NG> prep_tt(const r4<double>* p, const Couplings& cp) {
   for (int i = 0; i < NG; ++i) {
     const int l = i < 2 ? i : i + 2;
     q[i] = l < 2 ? -p[l] : p[l];
-    K.q[i] = cast4<T>(q[i]);
+    K.q[i] = l < 2 ? -K.pl[l] : K.pl[l];
+    K.wg[i] = wf_vector(K.pl[l]);
   }
-  const double m2 = cp.mt * cp.mt;
+  K.wt = wf_fermion(K.pl[2], (T)cp.mt);
+  K.wtb = wf_fermion(K.pl[3], (T)cp.mt);
+  // The gluons are massless and the top on shell, so every subset invariant is a sum of
+  // pairwise products (float64):  Q_S^2 = 2 sum_{i<j in S} q_i.q_j,
+  // (p_t + Q_S)^2 - m^2 = 2 sum_{i in S} p_t.q_i + Q_S^2.
+  double qq[NG][NG], tq[NG];
+  for (int i = 0; i < NG; ++i) {
+    tq[i] = mdot(p[2], q[i]);
+    for (int j = i + 1; j < NG; ++j) qq[i][j] = mdot(q[i], q[j]);
+  }
   for (int S = 1; S < (1 << NG); ++S) {
-    r4<double> Q{0.0, 0.0, 0.0, 0.0};
+    double s2 = 0.0, st = 0.0;
     int cnt = 0;
     for (int i = 0; i < NG; ++i)
       if (S >> i & 1) {
-        Q = Q + q[i];
+        st += tq[i];
         ++cnt;
+        for (int j = i + 1; j < NG; ++j)
+          if (S >> j & 1) s2 += qq[i][j];
       }
-    K.ig[S] = cnt >= 2 ? T(1) / (T)mdot(Q, Q) : T(0);
-    const r4<double> P = p[2] + Q;
-    K.iq[S] = cnt <= NG - 1 ? T(1) / (T)(mdot(P, P) - m2) : T(0);
+    K.ig[S] = cnt >= 2 ? T(1) / (T)(2.0 * s2) : T(0);
+    K.iq[S] = cnt <= NG - 1 ? T(1) / (T)(2.0 * (st + s2)) : T(0);
   }
   K.ig[0] = K.iq[0] = T(0);
   return K;
@@ -324,23 +337,24 @@ ME_HD void amp_tt2_block(const KinTT<T, 2>& K, int hb, const Couplings& cp, cons
                          F&& consume) {
   const T g = (T)cp.gs, mt = (T)cp.mt;
   const r4<T> k0 = K.q[0], k1 = K.q[1], kt = K.pl[2];
-  const c4<T> e0 = (ov != nullptr && ov_leg == 0) ? *ov : polvec(K.pl[0], hel_of(hb, 0), false);
-  const c4<T> e1 = (ov != nullptr && ov_leg == 1) ? *ov : polvec(K.pl[1], hel_of(hb, 1), false);
+  const c4<T> e0 = (ov != nullptr && ov_leg == 0) ? *ov : polvec_of(K.wg[0], hel_of(hb, 0), false);
+  const c4<T> e1 = (ov != nullptr && ov_leg == 1) ? *ov : polvec_of(K.wg[1], hel_of(hb, 1), false);
   c4<T> J01 = vvv(e0, e1, -k0, -k1);
   cscale(J01, -g * K.ig[3]);
+  const sl4<T> s0 = slashed(e0), s1 = slashed(e1), s01 = slashed(J01);
   const r4<T> Q0 = kt + k0, Q1 = kt + k1;
-  const c4<T> v[2] = {spinor_v(K.pl[3], mt, -1), spinor_v(K.pl[3], mt, 1)};
+  const c4<T> v[2] = {spinor_v_of(K.wtb, -1), spinor_v_of(K.wtb, 1)};
 #pragma unroll
   for (int ht = 0; ht < 2; ++ht) {
-    const c4<T> ub = dbar(spinor_u(kt, mt, ht ? 1 : -1));
-    const c4<T> S = row_slash(ub, J01);
-    c4<T> U0 = row_prop(row_slash(ub, e0), Q0, mt);
+    const c4<T> ub = dbar(spinor_u_of(K.wt, ht ? 1 : -1));
+    const c4<T> S = row_slash(ub, s01);
+    c4<T> U0 = row_prop(row_slash(ub, s0), Q0, mt);
     cscale(U0, -g * K.iq[1]);
-    c4<T> U1 = row_prop(row_slash(ub, e1), Q1, mt);
+    c4<T> U1 = row_prop(row_slash(ub, s1), Q1, mt);
     cscale(U1, -g * K.iq[2]);
-    c4<T> R0 = row_slash(U0, e1);
+    c4<T> R0 = row_slash(U0, s1);
     cadd(R0, S);
-    c4<T> R1 = row_slash(U1, e0);
+    c4<T> R1 = row_slash(U1, s0);
     csub(R1, S);
 #pragma unroll
     for (int hv = 0; hv < 2; ++hv) {
@@ -357,9 +371,9 @@ template <typename T, class F>
 ME_HD void amp_tt3_block(const KinTT<T, 3>& K, int hb, const Couplings& cp, F&& consume) {
   const T g = (T)cp.gs, mt = (T)cp.mt;
   const r4<T> k0 = K.q[0], k1 = K.q[1], k2 = K.q[2], kt = K.pl[2];
-  const c4<T> e0 = polvec(K.pl[0], hel_of(hb, 0), false);
-  const c4<T> e1 = polvec(K.pl[1], hel_of(hb, 1), false);
-  const c4<T> e2 = polvec(K.pl[4], hel_of(hb, 4), true);
+  const c4<T> e0 = polvec_of(K.wg[0], hel_of(hb, 0), false);
+  const c4<T> e1 = polvec_of(K.wg[1], hel_of(hb, 1), false);
+  const c4<T> e2 = polvec_of(K.wg[2], hel_of(hb, 4), true);
   c4<T> J01 = vvv(e0, e1, -k0, -k1);
   cscale(J01, -g * K.ig[3]);
   c4<T> J02 = vvv(e0, e2, -k0, -k2);
@@ -379,71 +393,74 @@ ME_HD void amp_tt3_block(const KinTT<T, 3>& K, int hb, const Couplings& cp, F&& 
   cadd(F2, vvv(e2, J01, -k2, -(k0 + k1)));    // = vvv(-J01, e2, ...)
   cscale(F2, c3);
   caxpy(F2, cx<T>{c4g, T(0)}, vvvv_ordered(e1, e0, e2));
-  const c4<T> v[2] = {spinor_v(K.pl[3], mt, -1), spinor_v(K.pl[3], mt, 1)};
+  const sl4<T> se0 = slashed(e0), se1 = slashed(e1), se2 = slashed(e2);
+  const sl4<T> sJ01 = slashed(J01), sJ02 = slashed(J02), sJ12 = slashed(J12);
+  const sl4<T> sF0 = slashed(F0), sF1 = slashed(F1), sF2 = slashed(F2);
+  const c4<T> v[2] = {spinor_v_of(K.wtb, -1), spinor_v_of(K.wtb, 1)};
   const r4<T> Q0 = kt + k0, Q1 = kt + k1, Q2 = kt + k2;
   const r4<T> Q01 = Q0 + k1, Q02 = Q0 + k2, Q12 = Q1 + k2;
   const T c01 = -g * K.iq[3], c02 = -g * K.iq[5], c12 = -g * K.iq[6];
 #pragma unroll
   for (int ht = 0; ht < 2; ++ht) {
-    const c4<T> ub = dbar(spinor_u(kt, mt, ht ? 1 : -1));
+    const c4<T> ub = dbar(spinor_u_of(K.wt, ht ? 1 : -1));
     c4<T> R[6];
-    R[0] = row_slash(ub, F0);  // orderings 012, 021, 102, 120, 201, 210
-    R[1] = row_slash(ub, F1);
-    R[2] = row_slash(ub, F2);
+    R[0] = row_slash(ub, sF0);  // orderings 012, 021, 102, 120, 201, 210
+    R[1] = row_slash(ub, sF1);
+    R[2] = row_slash(ub, sF2);
     R[3] = R[1];
     R[4] = R[2];
     R[5] = R[0];
-    const c4<T> S01 = row_slash(ub, J01), S02 = row_slash(ub, J02), S12 = row_slash(ub, J12);
+    const c4<T> S01 = row_slash(ub, sJ01), S02 = row_slash(ub, sJ02), S12 = row_slash(ub, sJ12);
     {  // first gluon 0: orderings 012, 021
-      c4<T> U = row_prop(row_slash(ub, e0), Q0, mt);
+      c4<T> U = row_prop(row_slash(ub, se0), Q0, mt);
       cscale(U, -g * K.iq[1]);
-      const c4<T> t = row_slash(U, J12);
+      const c4<T> t = row_slash(U, sJ12);
       cadd(R[0], t);
       csub(R[1], t);
-      c4<T> r = row_slash(U, e1);
+      c4<T> r = row_slash(U, se1);
       cadd(r, S01);
       c4<T> W = row_prop(r, Q01, mt);
       cscale(W, c01);
-      cadd(R[0], row_slash(W, e2));
-      r = row_slash(U, e2);
+      cadd(R[0], row_slash(W, se2));
+      r = row_slash(U, se2);
       cadd(r, S02);
       W = row_prop(r, Q02, mt);
       cscale(W, c02);
-      cadd(R[1], row_slash(W, e1));
+      cadd(R[1], row_slash(W, se1));
     }
     {  // first gluon 1: orderings 102, 120
-      c4<T> U = row_prop(row_slash(ub, e1), Q1, mt);
+      c4<T> U = row_prop(row_slash(ub, se1), Q1, mt);
       cscale(U, -g * K.iq[2]);
-      const c4<T> t = row_slash(U, J02);
+      const c4<T> t = row_slash(U, sJ02);
       cadd(R[2], t);
       csub(R[3], t);
-      c4<T> r = row_slash(U, e0);
+      c4<T> r = row_slash(U, se0);
       csub(r, S01);
       c4<T> W = row_prop(r, Q01, mt);
       cscale(W, c01);
-      cadd(R[2], row_slash(W, e2));
-      r = row_slash(U, e2);
+      cadd(R[2], row_slash(W, se2));
+      r = row_slash(U, se2);
       cadd(r, S12);
       W = row_prop(r, Q12, mt);
       cscale(W, c12);
-      cadd(R[3], row_slash(W, e0));
+      cadd(R[3], row_slash(W, se0));
     }
     {  // first gluon 2: orderings 201, 210
-      c4<T> U = row_prop(row_slash(ub, e2), Q2, mt);
+      c4<T> U = row_prop(row_slash(ub, se2), Q2, mt);
       cscale(U, -g * K.iq[4]);
-      const c4<T> t = row_slash(U, J01);
+      const c4<T> t = row_slash(U, sJ01);
       cadd(R[4], t);
       csub(R[5], t);
-      c4<T> r = row_slash(U, e0);
+      c4<T> r = row_slash(U, se0);
       csub(r, S02);
       c4<T> W = row_prop(r, Q02, mt);
       cscale(W, c02);
-      cadd(R[4], row_slash(W, e1));
-      r = row_slash(U, e1);
+      cadd(R[4], row_slash(W, se1));
+      r = row_slash(U, se1);
       csub(r, S12);
       W = row_prop(r, Q12, mt);
       cscale(W, c12);
-      cadd(R[5], row_slash(W, e0));
+      cadd(R[5], row_slash(W, se0));
     }
 #pragma unroll
     for (int hv = 0; hv < 2; ++hv) {
@@ -537,7 +554,7 @@ ME_HD KinUU<T> prep_uu(const r4<double>* p, const Couplings& cp) {
   for (int l = 0; l < NEXT; ++l) {
     K.pl[l] = cast4<T>(p[l]);
     q[l] = l < 2 ? -p[l] : p[l];
-    K.q[l] = cast4<T>(q[l]);
+    K.q[l] = l < 2 ? -K.pl[l] : K.pl[l];
   }
   const double m2 = cp.mt * cp.mt;
   const r4<double> s01 = q[0] + q[1];
@@ -668,7 +685,7 @@ ME_HD void amp_tt4_block(const KinTT<T, 4>& K, int hb, const Couplings& cp, F&& 
   constexpr int LEG[4] = {0, 1, 4, 5};
   c4<T> e[4];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) e[i] = polvec(K.pl[LEG[i]], hel_of(hb, LEG[i]), LEG[i] >= 2);
+  for (int i = 0; i < 4; ++i) e[i] = polvec_of(K.wg[i], hel_of(hb, LEG[i]), LEG[i] >= 2);
   const r4<T>* q = K.q;
   // pair currents, index pidx(x, y) for x < y
   c4<T> J2[6];
@@ -748,11 +765,11 @@ ME_HD void amp_tt4_block(const KinTT<T, 4>& K, int hb, const Couplings& cp, F&& 
         }
     return -1;
   };
-  const c4<T> v[2] = {spinor_v(K.pl[3], mt, -1), spinor_v(K.pl[3], mt, 1)};
+  const c4<T> v[2] = {spinor_v_of(K.wtb, -1), spinor_v_of(K.wtb, 1)};
   const r4<T> kt = K.pl[2];
 #pragma unroll 1
   for (int ht = 0; ht < 2; ++ht) {
-    const c4<T> ub = dbar(spinor_u(kt, mt, ht ? 1 : -1));
+    const c4<T> ub = dbar(spinor_u_of(K.wt, ht ? 1 : -1));
     cx<T> A[2][24];
     int f = 0;
 #pragma unroll

@@ -7,14 +7,22 @@
 // on the host, so staging, launches and completions of different requests proceed in
 // parallel and their kernels overlap on the GPU.  Completion is detected by polling a
 // CUDA event (never a device-side wait).
+// After one ordinary request of a (process, kind, weights) key, a slot captures that
+// key's launch sequence -- main kernel, float64 rescue, reduction, with the batch size
+// read on the device -- in a CUDA graph once, and replays it for every later request of
+// the key (momenta copied with the slot's fixed stride).
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
+#include <map>
 #include <chrono>
 #include <condition_variable>
+#include <cstdio>
 #include <cstring>
 #include <deque>
 #include <mutex>
+#include <shared_mutex>
 #include <string>
 #include <thread>
 #include <unordered_map>
@@ -43,17 +51,35 @@ struct Req {
   bool done = false;
 };
 
+// captured launch sequence of one (process, kind, weights) key on one slot
+struct Prog {
+  cudaGraphExec_t exec = nullptr;
+  bool warmed = false;  // an ordinary request of the key ran (lane layouts chosen)
+  bool tried = false;   // capture attempted at the current capacity
+};
+
 struct Slot {
   cudaStream_t st = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   double *d_p = nullptr, *d_w = nullptr, *d_out = nullptr;
   double *h_p = nullptr, *h_w = nullptr, *h_out = nullptr;
   int* h_resc = nullptr;
+  int* d_n = nullptr;  // batch size read by the graph's kernels
+  int* h_n = nullptr;
   size_t cap = 0;   // points
   int cap_ext = 6;  // legs the buffers are sized for
   me_handle* handles[16] = {};
+  std::map<int, Prog> progs;
   Req* cur = nullptr;
 };
+
+void drop_graphs(Slot& s) {
+  for (auto& kv : s.progs) {
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    kv.second.exec = nullptr;
+    kv.second.tried = false;
+  }
+}
 
 }  // namespace
 
@@ -68,6 +94,11 @@ struct me_server {
   bool stop = false;
   int64_t mem_in_use = 0;
   uint64_t next_ticket = 1;
+  std::atomic<int64_t> graph_runs{0}, plain_runs{0};
+  // slot threads hold this shared while they call into CUDA and exclusively while they
+  // capture a graph, so that no allocation, free or synchronisation of another slot
+  // runs concurrently with a stream capture
+  std::shared_mutex cuda_mu;
 };
 
 static int sfail(int code, const std::string& m) { return me_internal_fail(code, m.c_str()); }
@@ -75,6 +106,7 @@ static int sfail(int code, const std::string& m) { return me_internal_fail(code,
 static int slot_reserve(Slot& s, int64_t n, int n_ext) {
   if ((size_t)n <= s.cap && n_ext <= s.cap_ext) return ME_OK;
   size_t c = std::max<size_t>((size_t)n, 4096);
+  drop_graphs(s);  // captured with the old buffers and stride
   cudaFree(s.d_p);
   cudaFree(s.d_w);
   cudaFree(s.d_out);
@@ -92,9 +124,39 @@ static int slot_reserve(Slot& s, int64_t n, int n_ext) {
   return ME_OK;
 }
 
+// Capture the launch sequence of the request's key once (slot thread, with the server's
+// CUDA lock held exclusively).  A failed capture leaves the ordinary launches.
+static void capture(me_server* sv, Slot& s, Req* r) {
+  me_handle* h = s.handles[r->pid];
+  Prog& pg = s.progs[r->pid * 8 + r->kind * 2 + (r->w ? 1 : 0)];
+  if (!h || !sv->prm.use_graphs || !pg.warmed || pg.tried || pg.exec) return;
+  pg.tried = true;
+  cudaStreamSynchronize(s.st);
+  if (me_internal_prepare_counted(h, r->kind, (int64_t)s.cap) == ME_OK) {
+    cudaGraph_t g = nullptr;
+    cudaGetLastError();
+    if (cudaStreamBeginCapture(s.st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      const int lrc = me_internal_launch_counted(h, r->kind, s.d_p, r->w ? s.d_w : nullptr, (int64_t)s.cap, s.d_n,
+                                                 s.d_out);
+      const cudaError_t e = cudaStreamEndCapture(s.st, &g);
+      if (lrc == ME_OK && e == cudaSuccess && g && cudaGraphInstantiate(&pg.exec, g, 0) != cudaSuccess)
+        pg.exec = nullptr;
+      if (g) cudaGraphDestroy(g);
+    }
+  }
+  cudaGetLastError();
+}
+
+static bool wants_capture(me_server* sv, Slot& s, Req* r) {
+  if (!sv->prm.use_graphs || !s.handles[r->pid] || (size_t)r->n > s.cap || r->n_ext > s.cap_ext) return false;
+  auto it = s.progs.find(r->pid * 8 + r->kind * 2 + (r->w ? 1 : 0));
+  return it != s.progs.end() && it->second.warmed && !it->second.tried && !it->second.exec;
+}
+
 // stage and launch one admitted request on its slot (slot thread, without the lock)
 static int start(me_server* sv, Slot& s, Req* r) {
   cudaSetDevice(sv->prm.device);
+  (void)cudaGetLastError();  // each call below is checked on its own
   int rc = slot_reserve(s, r->n, r->n_ext);
   if (rc != ME_OK) return rc;
   me_handle*& h = s.handles[r->pid];
@@ -107,18 +169,41 @@ static int start(me_server* sv, Slot& s, Req* r) {
   const size_t pb = (size_t)r->n * 4 * r->n_ext * sizeof(double);
   std::memcpy(s.h_p, r->p, pb);
   if (r->w) std::memcpy(s.h_w, r->w, (size_t)r->n * 8);
-  cudaEventRecord(s.e0, s.st);
-  cudaMemcpyAsync(s.d_p, s.h_p, pb, cudaMemcpyHostToDevice, s.st);
-  if (r->w) cudaMemcpyAsync(s.d_w, s.h_w, (size_t)r->n * 8, cudaMemcpyHostToDevice, s.st);
-  const double* dw = r->w ? s.d_w : nullptr;
-  if (r->kind == ME_KIND_BORN) rc = me_eval_born(h, s.d_p, dw, r->n, s.d_out);
-  else if (r->kind == ME_KIND_REAL_SUBTRACTED) rc = me_eval_real_subtracted(h, s.d_p, dw, r->n, s.d_out);
-  else rc = me_eval_nbody_nlo(h, s.d_p, dw, r->n, s.d_out);
-  if (rc != ME_OK) return rc;
-  me_internal_rescued_async(h, s.h_resc);
-  cudaMemcpyAsync(s.h_out, s.d_out, (size_t)r->n * 8, cudaMemcpyDeviceToHost, s.st);
-  cudaEventRecord(s.e1, s.st);
-  if (cudaGetLastError() != cudaSuccess) return ME_ERR_CUDA;
+  Prog& pg = s.progs[r->pid * 8 + r->kind * 2 + (r->w ? 1 : 0)];
+  if (cudaEventRecord(s.e0, s.st) != cudaSuccess) return sfail(ME_ERR_CUDA, "event record failed");
+  if (pg.exec) {
+    // momenta rows (4 x n_ext rows of n points) at the slot's stride, then the count
+    cudaError_t e = cudaMemcpy2DAsync(s.d_p, s.cap * sizeof(double), s.h_p, (size_t)r->n * sizeof(double),
+                                      (size_t)r->n * sizeof(double), (size_t)4 * r->n_ext, cudaMemcpyHostToDevice, s.st);
+    if (e == cudaSuccess && r->w) e = cudaMemcpyAsync(s.d_w, s.h_w, (size_t)r->n * 8, cudaMemcpyHostToDevice, s.st);
+    *s.h_n = (int)r->n;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s.d_n, s.h_n, sizeof(int), cudaMemcpyHostToDevice, s.st);
+    if (e == cudaSuccess) e = cudaGraphLaunch(pg.exec, s.st);
+    if (e == cudaSuccess) {
+      sv->graph_runs.fetch_add(1);
+    } else {  // retire the graph; this request and later ones take the ordinary launches
+      std::fprintf(stderr, "me_server: graph replay failed (%s); ordinary launches from now on\n", cudaGetErrorString(e));
+      cudaGetLastError();
+      cudaGraphExecDestroy(pg.exec);
+      pg.exec = nullptr;
+    }
+  }
+  if (!pg.exec) {
+    cudaError_t e = cudaMemcpyAsync(s.d_p, s.h_p, pb, cudaMemcpyHostToDevice, s.st);
+    if (e == cudaSuccess && r->w) e = cudaMemcpyAsync(s.d_w, s.h_w, (size_t)r->n * 8, cudaMemcpyHostToDevice, s.st);
+    if (e != cudaSuccess) return sfail(ME_ERR_CUDA, std::string("staging: ") + cudaGetErrorString(e));
+    const double* dw = r->w ? s.d_w : nullptr;
+    if (r->kind == ME_KIND_BORN) rc = me_eval_born(h, s.d_p, dw, r->n, s.d_out);
+    else if (r->kind == ME_KIND_REAL_SUBTRACTED) rc = me_eval_real_subtracted(h, s.d_p, dw, r->n, s.d_out);
+    else rc = me_eval_nbody_nlo(h, s.d_p, dw, r->n, s.d_out);
+    if (rc != ME_OK) return rc;
+    pg.warmed = true;
+    sv->plain_runs.fetch_add(1);
+  }
+  if ((rc = me_internal_rescued_async(h, s.h_resc)) != ME_OK) return rc;
+  cudaError_t e = cudaMemcpyAsync(s.h_out, s.d_out, (size_t)r->n * 8, cudaMemcpyDeviceToHost, s.st);
+  if (e == cudaSuccess) e = cudaEventRecord(s.e1, s.st);
+  if (e != cudaSuccess) return sfail(ME_ERR_CUDA, std::string("result copy: ") + cudaGetErrorString(e));
   return ME_OK;
 }
 
@@ -185,8 +270,22 @@ static void slot_loop(me_server* sv, int si) {
     }
     lk.unlock();
     s.cur = r;
-    int rc = start(sv, s, r);
-    if (rc == ME_OK && wait_event(s.e1) != cudaSuccess) rc = ME_ERR_CUDA;
+    if (wants_capture(sv, s, r)) {
+      std::unique_lock<std::shared_mutex> cx(sv->cuda_mu);
+      capture(sv, s, r);
+    }
+    int rc;
+    {
+      std::shared_lock<std::shared_mutex> cs(sv->cuda_mu);
+      rc = start(sv, s, r);
+    }
+    if (rc == ME_OK) {
+      const cudaError_t e = wait_event(s.e1);
+      if (e != cudaSuccess) rc = sfail(ME_ERR_CUDA, std::string("completion: ") + cudaGetErrorString(e));
+    }
+    if (rc != ME_OK)
+      std::fprintf(stderr, "me_server: request %llu (%s, kind %d, n %lld) failed: %s\n",
+                   (unsigned long long)r->ticket, r->process.c_str(), r->kind, (long long)r->n, me_last_error());
     finish(r, s, rc);
     s.cur = nullptr;
     lk.lock();
@@ -207,6 +306,7 @@ void me_default_server_params(me_server_params* p) {
   p->n_slots = 4;
   p->max_queue = 4096;
   p->mem_budget_bytes = (int64_t)8 << 30;
+  p->use_graphs = 1;
   me_default_params(&p->params);
   p->params.precision = ME_PREC_MIXED;
 }
@@ -224,7 +324,8 @@ int me_server_create(const me_server_params* prm, me_server** out) {
   for (auto& s : sv->slots) {
     if (cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreate(&s.e0) != cudaSuccess || cudaEventCreate(&s.e1) != cudaSuccess ||
-        cudaMallocHost(&s.h_resc, sizeof(int)) != cudaSuccess) {
+        cudaMallocHost(&s.h_resc, sizeof(int)) != cudaSuccess || cudaMallocHost(&s.h_n, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&s.d_n, sizeof(int)) != cudaSuccess) {
       me_server_destroy(sv);
       return sfail(ME_ERR_CUDA, "me_server_create: stream/event allocation failed");
     }
@@ -287,6 +388,13 @@ int me_poll(me_server* sv, me_ticket t, me_result* out, int64_t timeout_us) {
   return ME_OK;
 }
 
+int me_server_stats(me_server* sv, int64_t* graph_runs, int64_t* plain_runs) {
+  if (!sv || !graph_runs || !plain_runs) return sfail(ME_ERR_ARG, "me_server_stats: NULL argument");
+  *graph_runs = sv->graph_runs.load();
+  *plain_runs = sv->plain_runs.load();
+  return ME_OK;
+}
+
 void me_server_destroy(me_server* sv) {
   if (!sv) return;
   {
@@ -299,6 +407,7 @@ void me_server_destroy(me_server* sv) {
   cudaSetDevice(sv->prm.device);
   for (auto& s : sv->slots) {
     if (s.st) cudaStreamSynchronize(s.st);
+    drop_graphs(s);
     for (auto* h : s.handles) me_destroy(h);
     cudaFree(s.d_p);
     cudaFree(s.d_w);
@@ -307,6 +416,8 @@ void me_server_destroy(me_server* sv) {
     cudaFreeHost(s.h_w);
     cudaFreeHost(s.h_out);
     cudaFreeHost(s.h_resc);
+    cudaFreeHost(s.h_n);
+    cudaFree(s.d_n);
     if (s.e0) cudaEventDestroy(s.e0);
     if (s.e1) cudaEventDestroy(s.e1);
     if (s.st) cudaStreamDestroy(s.st);

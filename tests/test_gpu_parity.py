@@ -155,7 +155,11 @@ def test_real_subtracted_mixed(me, name, seed):
 
 @pytest.mark.parametrize("name", ["gg_ttg", "uu_ttg"])
 def test_real_subtracted_mixed_approach_rescued(me, name):
-    """Points on soft/collinear approach sequences are re-evaluated in FP64."""
+    """On soft/collinear approach sequences, points within the thresholds (xi or 1-y
+    below 1e-3) are re-evaluated in FP64 and match the oracle to FP64 resolution; the
+    rest pass the stability test or are re-evaluated, and meet the mixed-precision target
+    (at most 0.2 % of points beyond 1e-5 of the weight, or beyond FP64 resolution where
+    that is coarser)."""
     b, lab = synth.approach_points(name, 32, 5)
     k = to_points(b.p)
     with np.errstate(all="ignore"):
@@ -163,7 +167,14 @@ def test_real_subtracted_mixed_approach_rescued(me, name):
     h = me.Handle(name, precision=me.ME_PREC_MIXED)
     got = h.real_subtracted(_dev(b.p)).cpu().numpy()
     assert h.last_rescued() >= int(0.8 * b.n)
-    _check_fp64(got, ref, mag, k)
+    near = lab["value"] < 1e-3
+    _check_fp64(got[near], ref[near], mag[near], k[near])
+    # beyond the thresholds: within 1e-5 of the weight, or within the point's FP64
+    # resolution where the cancellation puts 1e-5 of W below it (W ~ 1e-5 of the terms)
+    far = ~near & np.isfinite(ref)
+    tol64 = 1e-12 * mag * np.maximum(1.0, 1e-3 / _resolution(k))
+    bad = np.abs(got - ref)[far] > np.maximum(1e-5 * np.abs(ref), tol64)[far]
+    assert np.mean(bad) <= 0.002, np.sort((np.abs(got - ref) / np.abs(ref))[far][bad])[-4:]
 
 
 def test_nbody_nlo(me):

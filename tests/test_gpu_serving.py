@@ -105,3 +105,26 @@ def test_queue_full_and_bounded_poll(me):
     for t in extra:
         assert srv.poll(t, timeout_us=120_000_000)["status"] == me.ME_OK
     srv.close()
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_graph_replays_match_ordinary_launches(me, precision):
+    """After the first request of a (process, kind) on a slot, later ones replay the
+    slot's captured CUDA graph (batch size read on the device, momenta at the slot's
+    stride); every result equals the same request evaluated alone."""
+    prec = me.ME_PREC_MIXED if precision == "mixed" else me.ME_PREC_FP64
+    srv = me.Server(n_slots=2, precision=prec, lanes_per_event=4)
+    for proc in ("gg_ttg", "gg_ttgg", "ee_uu"):
+        kind = KIND[proc]
+        sizes = [300, 4096, 1000, 2500, 64, 3000, 777, 4096]
+        reqs = [synth.flat_points(proc, m, 50 + i) for i, m in enumerate(sizes)]
+        ts = [srv.submit(proc, kind, b.p, b.wgt) for b in reqs]
+        for b, t in zip(reqs, ts):
+            out = srv.poll(t, timeout_us=60_000_000)
+            assert out["status"] == me.ME_OK
+            ref = _alone(me, {"process": proc, "p": b.p, "w": b.wgt}, prec)
+            np.testing.assert_allclose(out["out"], ref, rtol=1e-12, atol=0)
+    st = srv.stats()
+    srv.close()
+    assert st["plain_runs"] + st["graph_runs"] == 24
+    assert st["graph_runs"] >= 24 - 2 * 3 * 2  # at most two ordinary runs per (slot, key)
