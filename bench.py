@@ -511,7 +511,9 @@ def main():
                               "reduction": t_red / max(1, ncalls)},
         "roofline": roofline,
         "roofline_other_kernel": other,
-        "e2e": {"value": n / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": {"value": n / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "path": "C-ABI call on pinned host buffers: the kernels read the inputs and write the results in "
+                        "place over the CPU-GPU link (no staging copy); the call returns with results on the host"},
         "gpu_launches": wl["launches"] * args.steps,
         "clocks": clocks,
         "cpu_baseline": cpu,

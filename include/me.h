@@ -17,10 +17,12 @@
  *  - ps_weights: optional float64[n] (NULL = all 1) multiplied into each output.
  *  - out: float64[n].
  *  - pointers may be host (pageable or pinned) or device memory of the handle's
- *    device; the kind is detected per pointer.  With any host pointer the call
- *    copies through device scratch and returns after the results are in `out`.
- *    With device pointers only, the work is enqueued on the handle's stream and the
- *    call returns without synchronising (me_synchronize waits).
+ *    device; the kind is detected per pointer.  Pinned (page-locked, mapped) host
+ *    buffers are read and written by the kernels in place, over the coherent CPU-GPU
+ *    link; pageable ones are copied through device scratch.  With any host pointer
+ *    the call returns after the results are in `out`.  With device pointers only, the
+ *    work is enqueued on the handle's stream and the call returns without
+ *    synchronising (me_synchronize waits).
  *  - ownership: the caller owns all input and output buffers and keeps them alive
  *    until the results are ready; the library owns its handles, process tables and
  *    scratch, freed by me_destroy.

@@ -413,14 +413,30 @@ static int ensure_capacity(me_handle* h, size_t n) {
   return ME_OK;
 }
 
-static bool is_device_ptr(const void* p) {
+// Address under which the kernels can use a caller's buffer, or nullptr if it has to be
+// staged: device and managed memory as is; pinned (page-locked, mapped) host memory under
+// its device address -- on GB300 the kernels then read and write it over the coherent
+// CPU-GPU link while they compute, with no staging copy.  Pageable memory is staged.
+static void* device_view(const void* p) {
+  if (!p) return nullptr;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) return const_cast<void*>(p);
+  if (at.type == cudaMemoryTypeHost && at.devicePointer) return at.devicePointer;
+  return nullptr;
+}
+
+static bool is_host_ptr(const void* p) {
   if (!p) return false;
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
-    return false;
+    return true;  // unregistered: pageable host memory
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
 }
 
 static cudaError_t dispatch(int pid, int kind, bool fp64, int lpe, const LaunchArgs& a, cudaStream_t st) {
@@ -579,22 +595,25 @@ static int run(me_handle* h, int kind, double nlo_factor, const double* momenta,
   h->last_kind = K_TREE;
   if (n == 0) return ME_OK;
   const int next = h->proc->n_ext;
-  const bool dp = is_device_ptr(momenta), dw = wgt ? is_device_ptr(wgt) : true, dout = is_device_ptr(out);
-  const bool staged = !(dp && dw && dout);
+  const double* vp = static_cast<const double*>(device_view(momenta));
+  const double* vw = wgt ? static_cast<const double*>(device_view(wgt)) : nullptr;
+  double* vo = static_cast<double*>(device_view(out));
+  // host buffers (pinned or pageable): results are in place when the call returns
+  const bool on_host = is_host_ptr(momenta) || (wgt && is_host_ptr(wgt)) || is_host_ptr(out);
   int rc = ensure_capacity(h, (size_t)n);
   if (rc != ME_OK) return rc;
-  const double* P = momenta;
-  const double* Wt = wgt;
-  double* O = out;
-  if (!dp) {
+  const double* P = vp;
+  const double* Wt = wgt ? vw : nullptr;
+  double* O = vo;
+  if (!vp) {
     ME_CUDA(cudaMemcpyAsync(h->d_p, momenta, (size_t)n * 4 * next * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     P = h->d_p;
   }
-  if (wgt && !dw) {
+  if (wgt && !vw) {
     ME_CUDA(cudaMemcpyAsync(h->d_w, wgt, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     Wt = h->d_w;
   }
-  if (!dout) O = h->d_out;
+  if (!vo) O = h->d_out;
   const bool mixed = h->prm.precision == ME_PREC_MIXED;
   LaunchArgs a{};
   a.p = P;
@@ -645,8 +664,8 @@ static int run(me_handle* h, int kind, double nlo_factor, const double* momenta,
   k_finish<<<1, 32, 0, h->stream>>>(h->d_part, RED_BLOCKS, h->d_acc, n, nullptr);
   ME_CUDA(cudaGetLastError());
   if (timed) ME_CUDA(cudaEventRecord(ev[3], h->stream));
-  if (!dout) ME_CUDA(cudaMemcpyAsync(out, O, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-  if (staged) ME_CUDA(cudaStreamSynchronize(h->stream));
+  if (!vo) ME_CUDA(cudaMemcpyAsync(out, O, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  if (on_host) ME_CUDA(cudaStreamSynchronize(h->stream));
   return ME_OK;
 }
 
