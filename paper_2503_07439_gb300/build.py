@@ -77,6 +77,22 @@ def build(verbose: bool = False, extra_flags=()) -> str:
     return LIB
 
 
+def block_check_tool() -> str:
+    """Build (if out of date) the host program that compares helicity-block and
+    single-helicity evaluations (csrc/me_blockcheck.cu), linked against the library."""
+    build()
+    tool = os.path.join(BUILD, "me_blockcheck")
+    src = os.path.join(CSRC, "me_blockcheck.cu")
+    newest = max([os.path.getmtime(src), os.path.getmtime(LIB)] + [os.path.getmtime(h) for h in _headers()])
+    if not os.path.exists(tool) or os.path.getmtime(tool) < newest:
+        r = subprocess.run([_nvcc(), "-O1", "-std=c++17", "-diag-suppress", "20014,20013", "-I", INCLUDE, "-x", "cu", src,
+                            "-o", tool, "-L", PKG, "-lme_gb300", "-Xlinker", "-rpath=" + PKG],
+                           capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("block-check tool failed to build:\n" + r.stdout + r.stderr)
+    return tool
+
+
 def op_counts() -> dict:
     """Algorithmic operation counts per helicity / event (see csrc/me_flops.cu)."""
     import json
