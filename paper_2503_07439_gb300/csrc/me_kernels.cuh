@@ -107,68 +107,30 @@ __device__ __forceinline__ void load_event(const double* __restrict__ p, long n,
 // ---------------------------------------------------------------- tree |M|^2
 // out[i] = wgt[i] * |M|^2(p_i) * nlo_factor.  `count` (optional): the number of events,
 // read on the device; `idx` (optional): the list of events to process (its length in
-// `count`).  Momenta have stride n either way.
-// g g -> t tbar g g in float32 does its 24-flow colour sums on the tensor cores: each
-// lane holds one (event, helicity) row, the warp contracts its 32 rows with the colour
-// matrix in one bf16 mma sequence (me_tc.cuh).  All lanes then run the same number of
-// helicity blocks; lanes past the end of the batch compute a fixed finite configuration
-// whose sums are discarded.
+// `count`).  Momenta have stride n either way.  (g g -> t tbar g g in float32 runs
+// k_tree_tc4 below instead.)
 template <int PID, typename T, int LPE>
 __global__ void __launch_bounds__(128, ME_MINB) k_tree(const double* __restrict__ p, const double* __restrict__ wgt,
                                                        long n, double* __restrict__ out, KParams kp,
                                                        const int* __restrict__ idx, const int* __restrict__ count) {
+  static_assert(!(PID == P_GG_TTGG && std::is_same<T, float>::value), "float g g -> t tbar g g runs k_tree_tc4");
   constexpr int NEXT = Proc<PID>::NEXT;
-  constexpr bool TC = (PID == P_GG_TTGG) && std::is_same<T, float>::value;
   const long gid = ((long)blockIdx.x * blockDim.x + threadIdx.x) / LPE;
   const int lane = threadIdx.x % LPE;
   const long nev = count ? (long)*count : n;
-  if constexpr (!TC) {
-    if (gid >= nev) return;
-    const long ev = idx ? (long)idx[gid] : gid;
-    r4<double> k[NEXT];
-    load_event<NEXT>(p, n, ev, k);
-    const Kin<PID, T> K = prepare<PID, T>(k, kp.cp);
-    T acc = T(0);
-    for (int b = lane; b < n_live_blocks<PID>(); b += LPE)
-      amplitude_block<PID, T>(K, live_block_hel<PID>(b), kp.cp,
-                              [&](int, const cx<T>* J) { acc += colour_sum<PID, T>(kp.tab, J); });
-    const double tot = 2.0 * (double)group_sum<LPE>(acc, group_mask<LPE>());
-    if (lane == 0) {
-      const double w = wgt ? wgt[ev] : 1.0;
-      out[ev] = w * tot * kp.avg_inv * kp.nlo_factor;
-    }
-  } else {
-    __shared__ __align__(16) unsigned char smem[4 * TC_SMEM_PER_WARP];
-    unsigned char* wsm = smem + (threadIdx.x >> 5) * TC_SMEM_PER_WARP;
-    const bool active = gid < nev;
-    const long ev = active ? (idx ? (long)idx[gid] : gid) : 0;
-    r4<double> k[NEXT];
-    if (active) {
-      load_event<NEXT>(p, n, ev, k);
-    } else {  // a fixed finite configuration: the lane still joins every warp-wide colour sum
-      const double d[6][4] = {{1000, 0, 0, 1000},     {1000, 0, 0, -1000},     {600, 100, 200, 300},
-                              {700, -150, -100, 200}, {400, 30, -80, -300}, {300, 20, -20, -200}};
-#pragma unroll
-      for (int l = 0; l < NEXT; ++l) k[l] = r4<double>{d[l][0], d[l][1], d[l][2], d[l][3]};
-    }
-    const TcColourB cb = tc_load_colour(kp.tab->C[PID]);
-    const Kin<PID, float> K = prepare<PID, float>(k, kp.cp);
-    constexpr int NB = n_live_blocks<PID>();
-    float acc = 0.0f;
-    // every lane runs the same number of blocks (a lane past the last block repeats one
-    // and discards it), so the warp-wide tensor-core calls stay converged
-    for (int it = 0; it < (NB + LPE - 1) / LPE; ++it) {
-      const int b = lane + it * LPE;
-      const float use = (active && b < NB) ? 1.0f : 0.0f;
-      amplitude_block<PID, float>(K, live_block_hel<PID>(b % NB), kp.cp, [&](int, const cx<float>* J) {
-        acc += use * tc_colour_sum(J, cb, wsm);
-      });
-    }
-    const double tot = 2.0 * (double)group_sum<LPE>(acc, group_mask<LPE>());
-    if (active && lane == 0) {
-      const double w = wgt ? wgt[ev] : 1.0;
-      out[ev] = w * tot * kp.avg_inv * kp.nlo_factor;
-    }
+  if (gid >= nev) return;
+  const long ev = idx ? (long)idx[gid] : gid;
+  r4<double> k[NEXT];
+  load_event<NEXT>(p, n, ev, k);
+  const Kin<PID, T> K = prepare<PID, T>(k, kp.cp);
+  T acc = T(0);
+  for (int b = lane; b < n_live_blocks<PID>(); b += LPE)
+    amplitude_block<PID, T>(K, live_block_hel<PID>(b), kp.cp,
+                            [&](int, const cx<T>* J) { acc += colour_sum<PID, T>(kp.tab, J); });
+  const double tot = 2.0 * (double)group_sum<LPE>(acc, group_mask<LPE>());
+  if (lane == 0) {
+    const double w = wgt ? wgt[ev] : 1.0;
+    out[ev] = w * tot * kp.avg_inv * kp.nlo_factor;
   }
 }
 
