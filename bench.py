@@ -444,6 +444,27 @@ def main():
     fp64_ms = f0.elapsed_time(f1) / args.fp64_steps
     fp64_value = n / (fp64_ms * 1e-3)
 
+    # the same step with the points generated on the device every step (Philox4x32-10 +
+    # RAMBO, me_generate_flat), for the workloads drawn from flat RAMBO points
+    devgen = None
+    if all(proc != "gg_tt" for proc, _, _ in calls):
+        def gen_step(step_no):
+            for (_, _, seed), (_, _, bb), (hh, f, pd, wd, od) in zip(wl["calls"], calls, handles):
+                hh.generate_flat(n, seed, bb.sqrt_s, first_point=(rank + world * step_no) * n, out=(pd, wd))
+                f(pd, wd, od)
+        gen_step(0)
+        torch.cuda.synchronize()
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for k_ in range(args.steps):
+            gen_step(k_ + 1)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        gms = g0.elapsed_time(g1) / args.steps
+        devgen = {"value": n / (gms * 1e-3), "unit": UNIT, "ms_per_step": gms,
+                  "note": "momenta and weights generated on the device each step, then evaluated"}
+
     # end to end through the C ABI with pinned host buffers (copies inside the timed region)
     hosts = []
     for (proc, entry, bb), (hh, f, *_rest) in zip(calls, handles):
@@ -514,6 +535,7 @@ def main():
         "e2e": {"value": n / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "path": "C-ABI call on pinned host buffers: the kernels read the inputs and write the results in "
                         "place over the CPU-GPU link (no staging copy); the call returns with results on the host"},
+        "device_generated": devgen,
         "gpu_launches": wl["launches"] * args.steps,
         "clocks": clocks,
         "cpu_baseline": cpu,

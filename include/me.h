@@ -166,6 +166,19 @@ int me_set_stream(me_handle* h, void* cuda_stream);
 /* Wait until all work enqueued on the handle's stream has finished. */
 int me_synchronize(me_handle* h);
 
+/* Flat phase-space points of the handle's process generated on the device (the
+ * multi-event input of Sec. 4.4 produced where it is evaluated): points first_point ..
+ * first_point + n - 1 of the counter-based stream (seed, stream) -- Philox4x32-10 with
+ * counter (point lo, point hi, stream, block) and key (seed lo, seed hi), uniforms
+ * ((w0 >> 5) 2^26 + (w1 >> 6) + 1/2) 2^-53 -- turned into momenta by RAMBO (massless
+ * directions and energies -log(u u'), boosted and scaled to sqrt_s) with the massive
+ * rescaling for the top quarks (mass params.mt).  Beams: massless along +z and -z.
+ * momenta: device float64 [4][n_ext][n] (layout as above); ps_weights: device float64[n]
+ * (the phase-space weight of each point) or NULL.  Enqueued on the handle's stream.
+ * ME_ERR_ARG for host pointers, n < 0 or sqrt_s not above the final-state masses. */
+int me_generate_flat(me_handle* h, uint64_t seed, uint32_t stream, int64_t first_point, double sqrt_s, int64_t n,
+                     double* momenta, double* ps_weights);
+
 /* Release the handle and its device scratch (waits for its stream).  NULL is a no-op. */
 void me_destroy(me_handle* h);
 

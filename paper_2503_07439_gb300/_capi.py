@@ -93,6 +93,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "me_poll": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.POINTER(MEResult), i64]),
         "me_server_destroy": (None, [vp]),
         "me_server_stats": (ctypes.c_int, [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
+        "me_generate_flat": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.c_uint32, i64, ctypes.c_double, i64, vp, vp]),
         "me_eval_real_subtracted_noalloc": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(MEParams), vp, vp, i64,
                                                            vp, vp]),
     }
@@ -189,6 +190,21 @@ class Handle:
 
     def real_subtracted(self, p, w=None, out=None):
         return self._call(self.lib.me_eval_real_subtracted, p, w, out)
+
+    def generate_flat(self, n: int, seed: int, sqrt_s: float, first_point: int = 0, stream: int = 0, out=None):
+        """Flat phase-space points of this process generated on the device (torch tensors
+        momenta [4][n_ext][n] and weights [n] on the handle's device, or `out` = (p, w))."""
+        import torch
+        if out is None:
+            p = torch.empty((4, self.n_ext, n), dtype=torch.float64, device=f"cuda:{self.params.device}")
+            w = torch.empty(n, dtype=torch.float64, device=p.device)
+        else:
+            p, w = out
+        _check(self.lib.me_generate_flat(self.h, seed, stream, first_point, float(sqrt_s), n,
+                                         ctypes.c_void_p(p.data_ptr()), ctypes.c_void_p(w.data_ptr())))
+        if self.sync:
+            _check(self.lib.me_synchronize(self.h))
+        return p, w
 
     def last_rescued(self) -> int:
         v = ctypes.c_int64()

@@ -842,6 +842,18 @@ int me_internal_launch_counted(me_handle* h, int me_kind, const double* d_p, con
   return ME_OK;
 }
 
+int me_internal_final_masses(me_handle* h, double* masses, int* n_out, cudaStream_t* stream) {
+  if (!h || !masses || !n_out || !stream) return fail(ME_ERR_ARG, "NULL argument");
+  const int pid = h->proc->pid;
+  const int nout = h->proc->n_ext - 2;
+  const bool tops = pid == P_GG_TT || pid == P_GG_TTG || pid == P_GG_TTGG || pid == P_UU_TT || pid == P_UU_TTG;
+  for (int j = 0; j < nout; ++j) masses[j] = (tops && j < 2) ? h->prm.mt : 0.0;
+  *n_out = nout;
+  *stream = h->stream;
+  ME_CUDA(cudaSetDevice(h->device));
+  return ME_OK;
+}
+
 int me_internal_rescued_async(me_handle* h, int* dst) {
   if (!h || !dst) return fail(ME_ERR_ARG, "NULL argument");
   if (h->prm.precision != ME_PREC_MIXED || h->last_kind != K_REAL) {

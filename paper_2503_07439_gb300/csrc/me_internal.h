@@ -16,6 +16,9 @@ int me_internal_rescued_async(me_handle* h, int* dst);
 int me_internal_prepare_counted(me_handle* h, int me_kind, int64_t cap);
 int me_internal_launch_counted(me_handle* h, int me_kind, const double* d_p, const double* d_w, int64_t cap,
                                const int* d_n, double* d_out);
+// Final-state masses of the handle's process (outgoing legs in order; at most 4), their
+// number, and the handle's stream.
+int me_internal_final_masses(me_handle* h, double* masses, int* n_out, cudaStream_t* stream);
 // Process id (index into the library's process table) of a name, or -1.
 int me_internal_process_id(const char* name);
 // Record the thread-local message returned by me_last_error(); returns `code`.
