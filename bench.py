@@ -72,24 +72,23 @@ def traffic_per_launch(workload: str, stage: str, points: int):
     if t is None or kernel_sources_sha() != KERNEL_SOURCES_SHA:
         return None
     return t["bytes"] * points / t["points"]  # scales with the points of the launch
-# launches per step: main kernel (+ FP64 rescue for the subtracted real) + 2 reduction kernels
 WORKLOADS = {
     "c2": {"calls": [("gg_ttg", "real_subtracted", SEED)], "n": N_POINTS, "metric": METRIC, "workload": WORKLOAD,
-           "kernel": "k_real_sub<gg_ttg, float>", "launches": 4, "l2": "inputs 168 MB per batch > 129 MB L2 (no flush)"},
+           "kernel": "k_real_sub<gg_ttg, float>", "l2": "inputs 168 MB per batch > 129 MB L2 (no flush)"},
     "c0": {"calls": [("ee_uu", "nbody_nlo", 1), ("ee_uug", "real_subtracted", 2)], "n": 65536,
            "metric": "e+e- -> u ubar NLO events/s (n-body + real-minus-counterterm, 1 GB300)",
            "workload": "e+e- -> u ubar (g) at sqrt(s)=100 GeV: 65536 Born points (n-body NLO weight) + 65536 "
                        "real points (FKS final-state sectors), mixed precision",
-           "kernel": "k_tree<ee_uu, float>", "launches": 7, "l2": "inputs 15 MB (< L2; compute-bound kernels)"},
+           "kernel": "k_tree<ee_uu, float>", "l2": "inputs 15 MB (< L2; compute-bound kernels)"},
     "c1": {"calls": [("gg_tt", "born", 3)], "n": N_POINTS,
            "metric": "gg -> t tbar LO events/s (1 GB300)",
            "workload": "gg -> t tbar LO, sqrt(s_hat) ~ U[400,2000] GeV, 2^20 points, float32 amplitudes",
-           "kernel": "k_tree<gg_tt, float>", "launches": 3, "l2": "inputs 134 MB per batch > 129 MB L2 (no flush)"},
+           "kernel": "k_tree<gg_tt, float>", "l2": "inputs 134 MB per batch > 129 MB L2 (no flush)"},
     "c3": {"calls": [("gg_ttgg", "born", 6)], "n": 1 << 18,
            "metric": "gg -> t tbar g g tree events/s (tensor-core colour sum, 1 GB300)",
            "workload": "gg -> t tbar g g tree at sqrt(s)=2 TeV, 2^18 flat massive-RAMBO points, float32 "
                        "amplitudes, 24-flow colour sum on tensor cores (bf16 x3 split, f32 accumulate)",
-           "kernel": "k_tree_tc4 (gg_ttgg, float; four lanes per event, mma.sync bf16 colour sum)", "launches": 3,
+           "kernel": "k_tree_tc4 (gg_ttgg, float; four lanes per event, mma.sync bf16 colour sum)",
            "l2": "inputs 50 MB (< L2; compute-bound kernel)"},
 }
 
@@ -344,6 +343,9 @@ def main():
     ap.add_argument("--lanes-per-event", type=int, default=0,
                     help="pin the lane layout of every handle (0: autotune; profiling runs pin it, "
                          "since launch timing under a profiler misleads the tuner)")
+    ap.add_argument("--queued-rescue", action="store_true",
+                    help="time the queued one-launch rescue kernel instead of the two launches (float32, then "
+                         "float64 over the compacted list)")
     ap.add_argument("--workload", default="c2", choices=["c0", "c1", "c2", "c3"],
                     help="c2 (default): gg->ttg real-minus-CT; c0: e+e- NLO (n-body + real-minus-CT); "
                          "c1: gg->tt LO; c3: gg->ttgg tree with the tensor-core colour sum")
@@ -384,10 +386,11 @@ def main():
         calls.append((proc, entry, bb))
     stream = torch.cuda.Stream()
 
-    def make(prec):
+    def make(prec, queued=args.queued_rescue):
         hs = []
         for proc, entry, bb in calls:
-            hh = me.Handle(proc, precision=prec, device=local, lanes_per_event=args.lanes_per_event)
+            hh = me.Handle(proc, precision=prec, device=local, lanes_per_event=args.lanes_per_event,
+                           queued_rescue=int(queued))
             hh.set_stream(stream.cuda_stream)
             hs.append((hh, getattr(hh, entry), torch.from_numpy(bb.p).cuda(), torch.from_numpy(bb.wgt).cuda(),
                        torch.empty(n, dtype=torch.float64, device="cuda")))
@@ -430,19 +433,29 @@ def main():
     ms, events = reduce_replicas(ms, float(n * args.steps), dist, device="cuda")
     value = events / (ms * 1e-3)
 
+    def time_steps(hs, k):
+        step(hs)  # first call: lane-layout tuning, scratch sizing
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(k):
+            step(hs)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        return f0.elapsed_time(f1) / k
+
     # plain float64 GPU path on the same batches
-    h64 = make(me.ME_PREC_FP64)
-    step(h64)
-    torch.cuda.synchronize()
-    f0 = torch.cuda.Event(enable_timing=True)
-    f1 = torch.cuda.Event(enable_timing=True)
-    f0.record(stream)
-    for _ in range(args.fp64_steps):
-        step(h64)
-    f1.record(stream)
-    torch.cuda.synchronize()
-    fp64_ms = f0.elapsed_time(f1) / args.fp64_steps
+    fp64_ms = time_steps(make(me.ME_PREC_FP64), args.fp64_steps)
     fp64_value = n / (fp64_ms * 1e-3)
+    # the other rescue organisation, for comparison (same batches, same results)
+    has_real = any(entry == "real_subtracted" for _, entry, _ in calls)
+    alt = None
+    if has_real:
+        alt_ms = time_steps(make(me.ME_PREC_MIXED, queued=not args.queued_rescue), max(3, args.fp64_steps))
+        alt = {"value": n / (alt_ms * 1e-3), "unit": UNIT, "ms_per_step": alt_ms,
+               "rescue": "float32 launch, then float64 launch over the compacted list" if args.queued_rescue else
+                         "queued one-launch kernel"}
 
     # the same step with the points generated on the device every step (Philox4x32-10 +
     # RAMBO, me_generate_flat), for the workloads drawn from flat RAMBO points
@@ -498,25 +511,45 @@ def main():
     main_ms = t_main / max(1, ncalls)
     resc_ms = t_resc / max(1, ncalls)
     resc_pts = handles[0][0].last_rescued()
+    queued0 = entry0 == "real_subtracted" and args.queued_rescue
     peak32 = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
     peak64 = SM_COUNT * FP64_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    note32 = ("fp32 FMA peak 152 SMs x 128 lanes x 2 flops x 2070 MHz (nominal units at max clock; "
+              "MEASURED_PEAKS.json has no fp32 figure)")
+    note64 = ("fp64 peak 152 SMs x 2 DFMA/clk x 2 flops x 2070 MHz (nominal units at max clock; "
+              "MEASURED_PEAKS.json has no fp64 figure)")
     # roofline of the dominant kernel of the step (by its CUDA-event time)
     rl_main = {"bound": "alu", "achieved": flops_event * n / (main_ms * 1e-3) / 1e12, "peak": peak32,
                "unit": "TFLOP/s", "traffic": traffic_per_launch(args.workload, "main", n), "kernel": wl["kernel"],
-               "peak_note": "fp32 FMA peak 152 SMs x 128 lanes x 2 flops x 2070 MHz (nominal units at max clock; "
-                            "MEASURED_PEAKS.json has no fp32 figure)",
-               "flops_per_event": flops_event, "ms_per_launch": main_ms}
+               "peak_note": note32, "flops_per_event": flops_event, "ms_per_launch": main_ms}
     rl_main["frac"] = rl_main["achieved"] / peak32
     roofline, other = rl_main, None
-    if resc_pts > 0 and resc_ms > main_ms:
+    if queued0 and resc_pts > 0:
+        # one kernel: float32 pass over every point + float64 re-evaluation of the flagged
+        # ones; the float64 unit limits it, so the fraction is taken against the fp64 peak
+        # and counts only the float64 work of the re-evaluated points (the float64 maps of
+        # the float32 pass are not counted: a lower bound)
+        roofline = {"bound": "alu", "achieved": flops_event * resc_pts / (main_ms * 1e-3) / 1e12, "peak": peak64,
+                    "unit": "TFLOP/s", "traffic": traffic_per_launch(args.workload, "queued", n),
+                    "kernel": wl["kernel"].replace("k_real_sub<", "k_real_sub_queued<").replace(", float>", ">")
+                    + " (float32 pass over all points + queued float64 re-evaluation of the flagged points)",
+                    "peak_note": note64, "flops_per_event": flops_event, "points_per_launch": n,
+                    "fp64_points_per_launch": resc_pts, "ms_per_launch": main_ms,
+                    "fp32_pass": {"achieved": flops_event * n / (main_ms * 1e-3) / 1e12, "peak": peak32,
+                                  "frac": flops_event * n / (main_ms * 1e-3) / 1e12 / peak32}}
+        roofline["frac"] = roofline["achieved"] / peak64
+    elif resc_pts > 0 and resc_ms > main_ms:
         rl_resc = {"bound": "alu", "achieved": flops_event * resc_pts / (resc_ms * 1e-3) / 1e12, "peak": peak64,
                    "unit": "TFLOP/s", "traffic": traffic_per_launch(args.workload, "rescue", resc_pts),
                    "kernel": wl["kernel"].replace("float", "double") + " (float64 rescue of the flagged points)",
-                   "peak_note": "fp64 peak 152 SMs x 2 DFMA/clk x 2 flops x 2070 MHz (nominal units at max clock; "
-                                "MEASURED_PEAKS.json has no fp64 figure)",
-                   "flops_per_event": flops_event, "points_per_launch": resc_pts, "ms_per_launch": resc_ms}
+                   "peak_note": note64, "flops_per_event": flops_event, "points_per_launch": resc_pts,
+                   "ms_per_launch": resc_ms}
         rl_resc["frac"] = rl_resc["achieved"] / peak64
         roofline, other = rl_resc, rl_main
+    # kernels per step: per call the main kernel, the float64 rescue launch (two-launch
+    # mixed subtracted real only) and the two reduction kernels
+    launches_per_step = sum(1 + (1 if entry == "real_subtracted" and not args.queued_rescue else 0) + 2
+                            for _, entry, _ in calls)
     clocks = clk.summary()
     line = {
         "metric": wl["metric"], "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -527,6 +560,7 @@ def main():
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "fp64_path": {"value": fp64_value, "unit": UNIT, "ms_per_step": fp64_ms,
                       "mixed_over_fp64": value / world / fp64_value},
+        "other_rescue_path": alt,
         "rescued_per_step": rescued,
         "stage_ms_per_step": {"main_kernel": main_ms, "rescue_kernel": t_resc / max(1, ncalls),
                               "reduction": t_red / max(1, ncalls)},
@@ -536,7 +570,7 @@ def main():
                 "path": "C-ABI call on pinned host buffers: the kernels read the inputs and write the results in "
                         "place over the CPU-GPU link (no staging copy); the call returns with results on the host"},
         "device_generated": devgen,
-        "gpu_launches": wl["launches"] * args.steps,
+        "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
         "cpu_baseline": cpu,
         "serving": serve,

@@ -47,7 +47,7 @@ extern "C" {
 #define ME_ERR_CUDA (-5)     /* a CUDA call failed; see me_last_error() */
 #define ME_ERR_BUSY (-6)     /* request rejected: queue full or over the memory budget */
 
-#define ME_PARAMS_VERSION 1u
+#define ME_PARAMS_VERSION 2u
 #define ME_PREC_FP64 0   /* every amplitude in float64 */
 #define ME_PREC_MIXED 1  /* float32 amplitudes; float64 FKS maps, combination and rescue */
 
@@ -71,7 +71,16 @@ extern "C" {
  *   device           CUDA device ordinal the handle runs on
  *   lanes_per_event  lanes sharing one point (1, 2, 4, 8 or 16; at most 8 for
  *                    "gg_ttgg"; 0 = autotune: each candidate is timed on the
- *                    handle's first call of each kind and precision)
+ *                    handle's first call of each kind and precision).  The queued
+ *                    mixed-precision subtracted real always runs one lane per point.
+ *   queued_rescue    mixed-precision subtracted real: 0 (default) = a float32 launch
+ *                    that lists the unstable points, then a float64 launch over the
+ *                    list; 1 = one launch in which each block queues its unstable
+ *                    points in shared memory and re-evaluates them in float64
+ *                    whenever the queue holds 128, next to other blocks' float32
+ *                    work.  Both give the same results to float64 rounding; on GB300
+ *                    the two launches are faster (the float64 unit needs several
+ *                    warps per scheduler to stay busy).
  */
 typedef struct me_params {
   uint32_t version;
@@ -87,13 +96,14 @@ typedef struct me_params {
   double me_eps;
   int32_t device;
   int32_t lanes_per_event;
+  int32_t queued_rescue;
 } me_params;
 
 typedef struct me_handle me_handle;
 
 /* Fill `p` with the defaults: FP64, alpha = 1/132.507, alpha_s = 0.118, mt = 173,
  * xi_cut = 0.5, delta = 1, xi_thr = 1e-3, y_thr = 1e-3, tol = 1e-5, me_eps = 4e-7,
- * device 0, lanes_per_event 0.  Never fails. */
+ * device 0, lanes_per_event 0, queued_rescue 0.  Never fails. */
 void me_default_params(me_params* p);
 
 /*

@@ -16,7 +16,7 @@ ME_ERR_CUDA = -5
 ME_ERR_BUSY = -6
 ME_PREC_FP64 = 0
 ME_PREC_MIXED = 1
-ME_PARAMS_VERSION = 1
+ME_PARAMS_VERSION = 2
 ME_KIND_BORN = 0
 ME_KIND_REAL_SUBTRACTED = 1
 ME_KIND_NBODY_NLO = 2
@@ -38,7 +38,7 @@ class MEParams(ctypes.Structure):
                 ("alpha_s", ctypes.c_double), ("mt", ctypes.c_double), ("xi_cut", ctypes.c_double),
                 ("delta", ctypes.c_double), ("xi_thr", ctypes.c_double), ("y_thr", ctypes.c_double),
                 ("tol", ctypes.c_double), ("me_eps", ctypes.c_double), ("device", ctypes.c_int32),
-                ("lanes_per_event", ctypes.c_int32)]
+                ("lanes_per_event", ctypes.c_int32), ("queued_rescue", ctypes.c_int32)]
 
 
 class MEServerParams(ctypes.Structure):

@@ -383,7 +383,7 @@ struct me_handle {
   double* d_out = nullptr;
   size_t cap = 0;
   int* d_resc = nullptr;     // rescue index list (capacity cap)
-  int* d_nresc = nullptr;    // [0]: count
+  int* d_nresc = nullptr;    // [0]: points re-evaluated in float64, [1]: tile counter (queued kernel)
   double* d_part = nullptr;  // reduction partials
   double* d_acc = nullptr;   // accumulators (3)
   int lpe[2][2] = {{0, 0}, {0, 0}};  // [kind][fp64] chosen lanes per event
@@ -552,7 +552,7 @@ int me_init(const char* process, const me_params* params, me_handle** out) {
     return fail(ME_ERR_CUDA, "me_init: stream creation failed");
   }
   h->stream = h->own_stream;
-  if (cudaMalloc(&h->d_nresc, sizeof(int)) != cudaSuccess || cudaMalloc(&h->d_part, 2 * RED_BLOCKS * sizeof(double)) != cudaSuccess ||
+  if (cudaMalloc(&h->d_nresc, 2 * sizeof(int)) != cudaSuccess || cudaMalloc(&h->d_part, 2 * RED_BLOCKS * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&h->d_acc, 3 * sizeof(double)) != cudaSuccess) {
     me_destroy(h);
     return fail(ME_ERR_OOM, "me_init: allocation failed");
@@ -575,7 +575,7 @@ int me_init(const char* process, const me_params* params, me_handle** out) {
   // stream-ordered on the handle's own stream: no device-wide synchronisation, so a
   // handle can be created while other threads capture CUDA graphs
   if (cudaMemsetAsync(h->d_acc, 0, 3 * sizeof(double), h->own_stream) != cudaSuccess ||
-      cudaMemsetAsync(h->d_nresc, 0, sizeof(int), h->own_stream) != cudaSuccess ||
+      cudaMemsetAsync(h->d_nresc, 0, 2 * sizeof(int), h->own_stream) != cudaSuccess ||
       cudaStreamSynchronize(h->own_stream) != cudaSuccess) {
     me_destroy(h);
     return fail(ME_ERR_CUDA, "me_init: device error");
@@ -625,15 +625,19 @@ static int run(me_handle* h, int kind, double nlo_factor, const double* momenta,
   a.groups = n;
   a.resc_list = h->d_resc;
   a.resc_count = h->d_nresc;
+  a.tiles = h->d_nresc + 1;
+  const bool queued = kind == K_REAL && mixed && h->prm.queued_rescue;
   if (kind == K_REAL && mixed) {
     a.kp.flag_unstable = 1;
-    ME_CUDA(cudaMemsetAsync(h->d_nresc, 0, sizeof(int), h->stream));
+    ME_CUDA(cudaMemsetAsync(h->d_nresc, 0, 2 * sizeof(int), h->stream));
     h->last_kind = K_REAL;
   }
   // the first call per (kind, precision) times the lane layouts (synchronising);
-  // both are chosen before the launches whose results are kept
-  const int lpe64 = (kind == K_REAL && mixed) ? choose_lpe(h, kind, true, a) : 0;
-  const int lpe = choose_lpe(h, kind, !mixed, a);
+  // both are chosen before the launches whose results are kept.  The queued kernel
+  // runs one lane per point in both precisions.
+  if (queued) h->lpe[kind][0] = h->lpe[kind][1] = 1;
+  const int lpe64 = (kind == K_REAL && mixed && !queued) ? choose_lpe(h, kind, true, a) : 0;
+  const int lpe = queued ? 1 : choose_lpe(h, kind, !mixed, a);
   std::array<cudaEvent_t, 4> ev{};
   const bool timed = h->timers && h->ev_used.size() < 4096;
   if (timed) {
@@ -649,9 +653,12 @@ static int run(me_handle* h, int kind, double nlo_factor, const double* momenta,
     h->ev_used.push_back(ev);
     ME_CUDA(cudaEventRecord(ev[0], h->stream));
   }
-  ME_CUDA(dispatch(h->proc->pid, kind, !mixed, lpe, a, h->stream));
+  if (queued)
+    ME_CUDA(launch_queued(h->proc->pid, a, h->stream));
+  else
+    ME_CUDA(dispatch(h->proc->pid, kind, !mixed, lpe, a, h->stream));
   if (timed) ME_CUDA(cudaEventRecord(ev[1], h->stream));
-  if (kind == K_REAL && mixed) {
+  if (kind == K_REAL && mixed && !queued) {
     // FP64 re-evaluation of the flagged points (count read on the device)
     LaunchArgs r = a;
     r.kp.flag_unstable = 0;
@@ -822,14 +829,19 @@ int me_internal_launch_counted(me_handle* h, int me_kind, const double* d_p, con
   a.groups = cap;
   a.resc_list = h->d_resc;
   a.resc_count = h->d_nresc;
+  a.tiles = h->d_nresc + 1;
+  const bool queued = kind == K_REAL && mixed && h->prm.queued_rescue;
   h->last_kind = K_TREE;
   if (kind == K_REAL && mixed) {
     a.kp.flag_unstable = 1;
-    ME_CUDA(cudaMemsetAsync(h->d_nresc, 0, sizeof(int), h->stream));
+    ME_CUDA(cudaMemsetAsync(h->d_nresc, 0, 2 * sizeof(int), h->stream));
     h->last_kind = K_REAL;
   }
-  ME_CUDA(dispatch(h->proc->pid, kind, !mixed, lpe, a, h->stream));
-  if (kind == K_REAL && mixed) {
+  if (queued)
+    ME_CUDA(launch_queued(h->proc->pid, a, h->stream));
+  else
+    ME_CUDA(dispatch(h->proc->pid, kind, !mixed, lpe, a, h->stream));
+  if (kind == K_REAL && mixed && !queued) {
     LaunchArgs r = a;
     r.kp.flag_unstable = 0;
     r.idx = h->d_resc;

@@ -12,6 +12,8 @@
 // of the heavy pair, evaluated with shared gluon currents and quark-line rows.  Born, real, soft and collinear terms are evaluated for every point and
 // masked afterwards (Sec. 4.3, Algorithm 2), so a warp never diverges on cuts.
 #pragma once
+#include <atomic>
+
 #include "me_procs.cuh"
 #include "me_tc.cuh"
 
@@ -455,22 +457,22 @@ __device__ __forceinline__ double eik(const r4<double>& a, const r4<double>& b, 
 }
 
 // ---------------------------------------------------------------- real - counterterms
-// out[i] = wgt[i] * sum over FKS sectors of the subtracted real (ME units), see
-// the FKS formula: W_j = R S_j - [Th_s G(0,y) + Th_c G(xi,1) - Th_s Th_c G(0,1)] / (xi^2 (1-y) K).
+// One point of the subtracted real, summed over FKS sectors (ME units):
+//   W_j = R S_j - [Th_s G(0,y) + Th_c G(xi,1) - Th_s Th_c G(0,1)] / (xi^2 (1-y) K),
+// with the error scale of the stability test.  The LPE lanes of a group evaluate one
+// point together and all return the same result.
+struct RealSubOut {
+  double W;     // subtracted real, summed over sectors
+  double mag;   // error scale: |R S| + |CT_coll| + |CT_soft - CT_softcoll| per sector
+  double y[2];  // y_j of both sectors (collinear resolution of the test)
+  bool near;    // inside xi_thr / y_thr of an active counterterm
+};
+
 template <int PID, typename T, int LPE>
-__global__ void __launch_bounds__(128, ME_MINB) k_real_sub(const double* __restrict__ p, const double* __restrict__ wgt,
-                                                  long n, double* __restrict__ out, KParams kp,
-                                                  const int* __restrict__ idx, const int* __restrict__ count,
-                                                  int* __restrict__ resc_list, int* __restrict__ resc_count) {
+__device__ __forceinline__ RealSubOut real_sub_event(const double* __restrict__ p, long n, long ev, const KParams& kp,
+                                                     int lane, unsigned mask) {
   constexpr int NEXT = Proc<PID>::NEXT;
   constexpr int BPID = (PID == P_EE_UUG) ? P_EE_UU : (PID == P_GG_TTG ? P_GG_TT : P_UU_TT);
-  constexpr int BNF = Proc<BPID>::NFLOW;
-  const long gid = ((long)blockIdx.x * blockDim.x + threadIdx.x) / LPE;
-  const int lane = threadIdx.x % LPE;
-  const long nev = count ? (long)*count : n;
-  if (gid >= nev) return;
-  const long ev = idx ? (long)idx[gid] : gid;
-  const unsigned mask = group_mask<LPE>();
   r4<double> k[NEXT];
   load_event<NEXT>(p, n, ev, k);
   const double rs = k[0].e + k[1].e, s = rs * rs;
@@ -620,22 +622,99 @@ __global__ void __launch_bounds__(128, ME_MINB) k_real_sub(const double* __restr
       near |= (th_s > 0.0 && xi < kp.xi_thr) || (th_c > 0.0 && 1.0 - f.y[j] < kp.y_thr);
     }
   }
+  return RealSubOut{W, mag, {ysec[0], ysec[1]}, near};
+}
+
+// Stability test of a bulk-precision result: the error of W is ~ me_eps x (error
+// scale); the float32 amplitude error per unit scale grows towards the collinear limit,
+// as 1 + sqrt(rho_0 / rho) with rho = min_j (1 - y_j), rho_0 = 0.01.
+__device__ __forceinline__ bool unstable_point(const RealSubOut& r, const KParams& kp) {
+  const float rho = fmaxf((float)fmin(1.0 - r.y[0], 1.0 - r.y[1]), 1e-30f);
+  const double grow = 1.0 + (double)sqrtf(0.01f / rho);
+  return r.near || !(r.mag * grow * kp.me_eps <= kp.tol * fabs(r.W));
+}
+
+// out[i] = wgt[i] * W(p_i).  In the bulk precision with kp.flag_unstable set, the
+// points failing the stability test are appended to resc_list; the float64 launch over
+// that list (idx, count) re-evaluates them.
+template <int PID, typename T, int LPE>
+__global__ void __launch_bounds__(128, ME_MINB) k_real_sub(const double* __restrict__ p, const double* __restrict__ wgt,
+                                                  long n, double* __restrict__ out, KParams kp,
+                                                  const int* __restrict__ idx, const int* __restrict__ count,
+                                                  int* __restrict__ resc_list, int* __restrict__ resc_count) {
+  const long gid = ((long)blockIdx.x * blockDim.x + threadIdx.x) / LPE;
+  const int lane = threadIdx.x % LPE;
+  const long nev = count ? (long)*count : n;
+  if (gid >= nev) return;
+  const long ev = idx ? (long)idx[gid] : gid;
+  const RealSubOut r = real_sub_event<PID, T, LPE>(p, n, ev, kp, lane, group_mask<LPE>());
   if (lane == 0) {
-    const double w = wgt ? wgt[ev] : 1.0;
-    out[ev] = w * W;
-    if (kp.flag_unstable) {
-      // cancellation test: the bulk-precision error of W is ~ me_eps x (error scale); the
-      // float32 amplitude error per unit scale grows towards the collinear limit, as
-      // 1 + sqrt(rho_0 / rho) with rho = min_j (1 - y_j), rho_0 = 0.01
-      const float rho = fmaxf((float)fmin(1.0 - ysec[0], 1.0 - ysec[1]), 1e-30f);
-      const double grow = 1.0 + (double)sqrtf(0.01f / rho);
-      const bool unstable = near || !(mag * grow * kp.me_eps <= kp.tol * fabs(W));
-      if (unstable) {
-        const int slot = atomicAdd(resc_count, 1);
-        resc_list[slot] = (int)ev;
-      }
+    out[ev] = (wgt ? wgt[ev] : 1.0) * r.W;
+    if (kp.flag_unstable && unstable_point(r, kp)) {
+      const int slot = atomicAdd(resc_count, 1);
+      resc_list[slot] = (int)ev;
     }
   }
+}
+
+// Mixed-precision subtracted real in one launch, with the float64 re-evaluation queued
+// per block (the per-term queues of the event-parallel design, here for the unstable
+// points).  A persistent grid takes tiles of QT points from a device counter.  Each
+// point is evaluated in float32, one lane per point; a point that fails the stability
+// test goes to a queue in shared memory.  Whenever the queue holds QT points the block
+// re-evaluates them in float64, one lane per point with every lane busy, while the
+// SM's other blocks run float32 tiles next to it.  The remainder is drained at the
+// end.  A point's result depends only on the point, so the output does not depend on
+// which block took which tile.  `count` (optional, device): number of points.
+// `tiles` must be zero at launch; `resc_count` receives the number re-evaluated.
+constexpr int QT = 128;
+
+template <int PID>
+__global__ void __launch_bounds__(QT, ME_MINB) k_real_sub_queued(const double* __restrict__ p,
+                                                        const double* __restrict__ wgt, long n,
+                                                        double* __restrict__ out, KParams kp,
+                                                        const int* __restrict__ count, int* __restrict__ tiles,
+                                                        int* __restrict__ resc_count) {
+  __shared__ int q[2 * QT];
+  __shared__ int qn, tile;
+  const long nev = count ? (long)*count : n;
+  const long ntile = (nev + QT - 1) / QT;
+  const unsigned self = 1u << (threadIdx.x & 31u);
+  if (threadIdx.x == 0) qn = 0;
+  int done = 0;
+  for (;;) {
+    if (threadIdx.x == 0) tile = atomicAdd(tiles, 1);
+    __syncthreads();
+    const long t = tile;
+    const bool last = t >= ntile;  // uniform over the block
+    if (!last) {
+      const long ev = t * QT + threadIdx.x;
+      if (ev < nev) {
+        const RealSubOut r = real_sub_event<PID, float, 1>(p, n, ev, kp, 0, self);
+        out[ev] = (wgt ? wgt[ev] : 1.0) * r.W;
+        if (unstable_point(r, kp)) q[atomicAdd(&qn, 1)] = (int)ev;
+      }
+    }
+    __syncthreads();
+    // a full queue, or the rest once the tiles are gone (then fewer than QT are left)
+    const int qc = qn;  // uniform: qn is not written between this read and the barriers below
+    if (qc >= QT || (last && qc > 0)) {
+      const int take = qc < QT ? qc : QT;
+      if ((int)threadIdx.x < take) {
+        const int e = q[threadIdx.x];
+        const RealSubOut r = real_sub_event<PID, double, 1>(p, n, e, kp, 0, self);
+        out[e] = (wgt ? wgt[e] : 1.0) * r.W;
+      }
+      const int rest = qc - take;  // < QT: at most QT - 1 were left before this tile
+      __syncthreads();
+      if ((int)threadIdx.x < rest) q[threadIdx.x] = q[QT + threadIdx.x];
+      done += take;
+      __syncthreads();
+      if (threadIdx.x == 0) qn = rest;  // ordered before any append by the next barrier
+    }
+    if (last) break;
+  }
+  if (threadIdx.x == 0 && done > 0) atomicAdd(resc_count, done);
 }
 
 // ---------------------------------------------------------------- weight accumulation
@@ -658,6 +737,7 @@ struct LaunchArgs {
   int* resc_list;    // real kernel in bulk precision: unstable points are appended here
   int* resc_count;
   long groups;       // number of event groups to launch (n, or the list capacity)
+  int* tiles;        // queued kernel: tile counter, zero at launch
 };
 enum KernelKind : int { K_TREE = 0, K_REAL = 1 };
 
@@ -702,6 +782,36 @@ cudaError_t launch_gg(int pid, int kind, bool fp64, int lpe, const LaunchArgs& a
 cudaError_t launch_ggg(int pid, int kind, bool fp64, int lpe, const LaunchArgs& a, cudaStream_t st);
 cudaError_t launch_ggg64(int kind, int lpe, const LaunchArgs& a, cudaStream_t st);
 cudaError_t launch_uu(int pid, int kind, bool fp64, int lpe, const LaunchArgs& a, cudaStream_t st);
+// mixed-precision subtracted real with the queued float64 re-evaluation (k_real_sub_queued)
+cudaError_t launch_queued(int pid, const LaunchArgs& a, cudaStream_t st);
+cudaError_t launch_queued_gg(const LaunchArgs& a, cudaStream_t st);
+
+// One persistent launch of k_real_sub_queued: as many blocks as are resident at once
+// (occupancy x SMs, found once per device), at most one per tile.
+template <int PID>
+cudaError_t launch_queued_one(const LaunchArgs& a, cudaStream_t st) {
+  (void)cudaGetLastError();  // the launch status below must not report an earlier call's error
+  static std::atomic<int> resident[64];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  int g = resident[dev].load(std::memory_order_relaxed);
+  if (g == 0) {
+    int per = 0, sms = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_real_sub_queued<PID>, QT, 0);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    g = (per > 0 ? per : 1) * (sms > 0 ? sms : 1);
+    resident[dev].store(g, std::memory_order_relaxed);
+  }
+  const long ntile = (a.groups + QT - 1) / QT;
+  if (ntile <= 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)(ntile < g ? ntile : g);
+  k_real_sub_queued<PID><<<blocks, QT, 0, st>>>(a.p, a.wgt, a.n, a.out, a.kp, a.count, a.tiles, a.resc_count);
+  return cudaGetLastError();
+}
 
 }  // namespace me
 

@@ -34,7 +34,7 @@ def test_header_cites_the_paper_and_documents_errors():
 def test_default_params_without_gpu(lib):
     import paper_2503_07439_gb300 as me
     p = me.default_params()
-    assert p.version == 1 and p.precision == me.ME_PREC_FP64
+    assert p.version == me.ME_PARAMS_VERSION and p.precision == me.ME_PREC_FP64 and p.queued_rescue == 0
     assert abs(p.alpha_s - 0.118) < 1e-15 and abs(p.mt - 173.0) < 1e-12
 
 

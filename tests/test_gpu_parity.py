@@ -235,3 +235,35 @@ def test_pinned_host_buffers_read_in_place(me):
     h.real_subtracted(pp.numpy(), pw.numpy(), po.numpy())
     np.testing.assert_array_equal(po.numpy(), dev)
     np.testing.assert_array_equal(pageable, dev)
+
+
+@pytest.mark.parametrize("name,seed", [("gg_ttg", 71), ("uu_ttg", 72), ("ee_uug", 73)])
+def test_queued_rescue_equals_separate_launches(me, name, seed):
+    """The one-launch kernel that queues its unstable points per block and re-evaluates
+    them in float64 gives the results, the rescued count and the accumulators of a
+    float32 launch followed by a float64 launch over the compacted list (both one lane
+    per point).  The float32 results are the same code and agree bit for bit; the
+    float64 re-evaluations are the same formulae compiled into another kernel, where
+    the compiler may fuse multiply-adds differently, so they agree to float64 rounding.
+    Sizes: many tiles per block of the persistent grid with a ragged tail, one partial
+    tile, and an empty batch."""
+    hq = me.Handle(name, precision=me.ME_PREC_MIXED, queued_rescue=1)
+    hs = me.Handle(name, precision=me.ME_PREC_MIXED, lanes_per_event=1)
+    for n in (200000 + 77, 50, 0):
+        b = synth.flat_points(name, max(n, 1), seed)
+        p, w = b.p[:, :, :n], b.wgt[:n]
+        hq.set_accumulators((0.0, 0.0, 0.0))
+        hs.set_accumulators((0.0, 0.0, 0.0))
+        q = hq.real_subtracted(_dev(p), _dev(w)).cpu().numpy()
+        s = hs.real_subtracted(_dev(p), _dev(w)).cpu().numpy()
+        nq, ns = hq.last_rescued(), hs.last_rescued()
+        assert nq == ns
+        if n > 100000:
+            assert nq > 1000
+        if n:
+            rel = np.abs(q - s) / np.maximum(np.abs(s), 1e-300)
+            assert np.mean(rel > 0) <= 1.2 * nq / n + 1e-9  # only re-evaluated points differ at all
+            assert rel.max() <= 1e-9, np.sort(rel)[-3:]
+        aq, as_ = np.asarray(hq.accumulators()), np.asarray(hs.accumulators())
+        assert aq[2] == as_[2] == n
+        np.testing.assert_allclose(aq[:2], as_[:2], rtol=1e-9, atol=0)
