@@ -61,10 +61,22 @@ template <typename T> ME_HD r4<T> scale(T s, r4<T> a) { return {s * a.e, s * a.x
 template <typename T> ME_HD T mdot(r4<T> a, r4<T> b) { return a.e * b.e - a.x * b.x - a.y * b.y - a.z * b.z; }
 template <typename U, typename T> ME_HD r4<U> cast4(r4<T> a) { return {(U)a.e, (U)a.x, (U)a.y, (U)a.z}; }
 
+// Sums of complex products are written as one left-to-right chain of real products, so
+// that the compiler fuses every product after the first into the running sum (one
+// fused multiply-add per real product).  Written as sums of complex temporaries, each
+// complex product would end in a separate add: on GB300 float64 runs at 1/64 of the
+// float32 rate, so the float64 path pays for every such add.
+template <typename T> ME_HD cx<T> cmac(cx<T> acc, cx<T> a, cx<T> b) {  // acc + a b
+  return {acc.re + a.re * b.re - a.im * b.im, acc.im + a.re * b.im + a.im * b.re};
+}
+template <typename T> ME_HD cx<T> cmsb(cx<T> acc, cx<T> a, cx<T> b) {  // acc - a b
+  return {acc.re - a.re * b.re + a.im * b.im, acc.im - a.re * b.im - a.im * b.re};
+}
+
 // complex-vector . complex-vector (Minkowski, no conjugation)
 template <typename T>
 ME_HD cx<T> cdot(const c4<T>& a, const c4<T>& b) {
-  return a.v[0] * b.v[0] - a.v[1] * b.v[1] - a.v[2] * b.v[2] - a.v[3] * b.v[3];
+  return cmsb(cmsb(cmsb(a.v[0] * b.v[0], a.v[1], b.v[1]), a.v[2], b.v[2]), a.v[3], b.v[3]);
 }
 // real-vector . complex-vector
 template <typename T>
@@ -84,7 +96,20 @@ ME_HD void csub(c4<T>& acc, const c4<T>& x) {
 template <typename T>
 ME_HD void caxpy(c4<T>& acc, cx<T> a, const c4<T>& x) {
 #pragma unroll
-  for (int i = 0; i < 4; ++i) acc.v[i] = acc.v[i] + a * x.v[i];
+  for (int i = 0; i < 4; ++i) acc.v[i] = cmac(acc.v[i], a, x.v[i]);
+}
+// acc + s x, s real
+template <typename T>
+ME_HD void caxpy(c4<T>& acc, T s, const c4<T>& x) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) acc.v[i] = cx<T>{acc.v[i].re + s * x.v[i].re, acc.v[i].im + s * x.v[i].im};
+}
+template <typename T>
+ME_HD c4<T> cneg(const c4<T>& x) {
+  c4<T> o;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) o.v[i] = -x.v[i];
+  return o;
 }
 template <typename T>
 ME_HD void cscale(c4<T>& x, cx<T> a) {
@@ -285,10 +310,10 @@ ME_HD c4<T> row_slash(const c4<T>& r, const c4<T>& V) {
   cx<T> c = V.v[1] - times_i(V.v[2]);  // V1 - i V2
   cx<T> d = V.v[1] + times_i(V.v[2]);  // V1 + i V2
   c4<T> o;
-  o.v[0] = r.v[2] * b + r.v[3] * d;
-  o.v[1] = r.v[2] * c + r.v[3] * a;
-  o.v[2] = r.v[0] * a - r.v[1] * d;
-  o.v[3] = -(r.v[0] * c) + r.v[1] * b;
+  o.v[0] = cmac(r.v[2] * b, r.v[3], d);
+  o.v[1] = cmac(r.v[2] * c, r.v[3], a);
+  o.v[2] = cmsb(r.v[0] * a, r.v[1], d);
+  o.v[3] = cmsb(r.v[1] * b, r.v[0], c);
   return o;
 }
 // Vslash in the chiral representation is fixed by four combinations of V: a = V0 - V3,
@@ -305,11 +330,19 @@ ME_HD sl4<T> slashed(const c4<T>& V) {
 template <typename T>
 ME_HD c4<T> row_slash(const c4<T>& r, const sl4<T>& S) {
   c4<T> o;
-  o.v[0] = r.v[2] * S.b + r.v[3] * S.d;
-  o.v[1] = r.v[2] * S.c + r.v[3] * S.a;
-  o.v[2] = r.v[0] * S.a - r.v[1] * S.d;
-  o.v[3] = -(r.v[0] * S.c) + r.v[1] * S.b;
+  o.v[0] = cmac(r.v[2] * S.b, r.v[3], S.d);
+  o.v[1] = cmac(r.v[2] * S.c, r.v[3], S.a);
+  o.v[2] = cmsb(r.v[0] * S.a, r.v[1], S.d);
+  o.v[3] = cmsb(r.v[1] * S.b, r.v[0], S.c);
   return o;
+}
+// acc + r Sslash, accumulated in place
+template <typename T>
+ME_HD void row_slash_acc(c4<T>& acc, const c4<T>& r, const sl4<T>& S) {
+  acc.v[0] = cmac(cmac(acc.v[0], r.v[2], S.b), r.v[3], S.d);
+  acc.v[1] = cmac(cmac(acc.v[1], r.v[2], S.c), r.v[3], S.a);
+  acc.v[2] = cmsb(cmac(acc.v[2], r.v[0], S.a), r.v[1], S.d);
+  acc.v[3] = cmac(cmsb(acc.v[3], r.v[0], S.c), r.v[1], S.b);
 }
 // Vslash times column spinor
 template <typename T>
@@ -318,10 +351,10 @@ ME_HD c4<T> slash_col(const c4<T>& V, const c4<T>& s) {
   cx<T> c = V.v[1] - times_i(V.v[2]);
   cx<T> d = V.v[1] + times_i(V.v[2]);
   c4<T> o;
-  o.v[0] = a * s.v[2] - c * s.v[3];
-  o.v[1] = -(d * s.v[2]) + b * s.v[3];
-  o.v[2] = b * s.v[0] + c * s.v[1];
-  o.v[3] = d * s.v[0] + a * s.v[1];
+  o.v[0] = cmsb(a * s.v[2], c, s.v[3]);
+  o.v[1] = cmsb(b * s.v[3], d, s.v[2]);
+  o.v[2] = cmac(b * s.v[0], c, s.v[1]);
+  o.v[3] = cmac(d * s.v[0], a, s.v[1]);
   return o;
 }
 // row spinor times (Qslash + m), Q real
@@ -330,10 +363,32 @@ ME_HD c4<T> row_prop(const c4<T>& r, const r4<T>& Q, T m) {
   T a = Q.e - Q.z, b = Q.e + Q.z;
   cx<T> c = cx<T>{Q.x, -Q.y}, d = cx<T>{Q.x, Q.y};
   c4<T> o;
-  o.v[0] = b * r.v[2] + r.v[3] * d + m * r.v[0];
-  o.v[1] = r.v[2] * c + a * r.v[3] + m * r.v[1];
-  o.v[2] = a * r.v[0] - r.v[1] * d + m * r.v[2];
-  o.v[3] = -(r.v[0] * c) + b * r.v[1] + m * r.v[3];
+  o.v[0] = cmac(b * r.v[2] + m * r.v[0], r.v[3], d);
+  o.v[1] = cmac(a * r.v[3] + m * r.v[1], r.v[2], c);
+  o.v[2] = cmsb(a * r.v[0] + m * r.v[2], r.v[1], d);
+  o.v[3] = cmsb(b * r.v[1] + m * r.v[3], r.v[0], c);
+  return o;
+}
+// s (Qslash + m) for rows, Q real: the combinations row_prop uses, formed once for a
+// propagator that closes several rows (the scale s, a coupling times the reciprocal
+// denominator, is folded in here instead of into every row)
+template <typename T>
+struct prop4 {
+  T a, b, m;
+  cx<T> c, d;
+};
+template <typename T>
+ME_HD prop4<T> scaled_prop(const r4<T>& Q, T m, T s) {
+  const T sx = s * Q.x, sy = s * Q.y;
+  return prop4<T>{s * (Q.e - Q.z), s * (Q.e + Q.z), s * m, cx<T>{sx, -sy}, cx<T>{sx, sy}};
+}
+template <typename T>
+ME_HD c4<T> row_prop(const c4<T>& r, const prop4<T>& P) {
+  c4<T> o;
+  o.v[0] = cmac(P.b * r.v[2] + P.m * r.v[0], r.v[3], P.d);
+  o.v[1] = cmac(P.a * r.v[3] + P.m * r.v[1], r.v[2], P.c);
+  o.v[2] = cmsb(P.a * r.v[0] + P.m * r.v[2], r.v[1], P.d);
+  o.v[3] = cmsb(P.b * r.v[1] + P.m * r.v[3], r.v[0], P.c);
   return o;
 }
 // (-Qslash + m) times column spinor, Q real
@@ -342,25 +397,25 @@ ME_HD c4<T> col_prop(const r4<T>& Q, T m, const c4<T>& s) {
   T a = Q.e - Q.z, b = Q.e + Q.z;
   cx<T> c = cx<T>{Q.x, -Q.y}, d = cx<T>{Q.x, Q.y};
   c4<T> o;
-  o.v[0] = m * s.v[0] - (a * s.v[2] - c * s.v[3]);
-  o.v[1] = m * s.v[1] - (-(d * s.v[2]) + b * s.v[3]);
-  o.v[2] = m * s.v[2] - (b * s.v[0] + c * s.v[1]);
-  o.v[3] = m * s.v[3] - (d * s.v[0] + a * s.v[1]);
+  o.v[0] = cmac(m * s.v[0] - a * s.v[2], c, s.v[3]);
+  o.v[1] = cmac(m * s.v[1] - b * s.v[3], d, s.v[2]);
+  o.v[2] = cmsb(m * s.v[2] - b * s.v[0], c, s.v[1]);
+  o.v[3] = cmsb(m * s.v[3] - a * s.v[1], d, s.v[0]);
   return o;
 }
 // vector current J^mu = r gamma^mu s
 template <typename T>
 ME_HD c4<T> vcurrent(const c4<T>& r, const c4<T>& s) {
   c4<T> J;
-  J.v[0] = r.v[0] * s.v[2] + r.v[1] * s.v[3] + r.v[2] * s.v[0] + r.v[3] * s.v[1];
-  J.v[1] = (r.v[0] * s.v[3] + r.v[1] * s.v[2]) - (r.v[2] * s.v[1] + r.v[3] * s.v[0]);
-  J.v[2] = times_i((r.v[1] * s.v[2] - r.v[0] * s.v[3]) - (r.v[3] * s.v[0] - r.v[2] * s.v[1]));
-  J.v[3] = (r.v[0] * s.v[2] - r.v[1] * s.v[3]) - (r.v[2] * s.v[0] - r.v[3] * s.v[1]);
+  J.v[0] = cmac(cmac(cmac(r.v[0] * s.v[2], r.v[1], s.v[3]), r.v[2], s.v[0]), r.v[3], s.v[1]);
+  J.v[1] = cmsb(cmsb(cmac(r.v[0] * s.v[3], r.v[1], s.v[2]), r.v[2], s.v[1]), r.v[3], s.v[0]);
+  J.v[2] = times_i(cmac(cmsb(cmsb(r.v[1] * s.v[2], r.v[0], s.v[3]), r.v[3], s.v[0]), r.v[2], s.v[1]));
+  J.v[3] = cmac(cmsb(cmsb(r.v[0] * s.v[2], r.v[1], s.v[3]), r.v[2], s.v[0]), r.v[3], s.v[1]);
   return J;
 }
 template <typename T>
 ME_HD cx<T> spdot(const c4<T>& r, const c4<T>& s) {
-  return r.v[0] * s.v[0] + r.v[1] * s.v[1] + r.v[2] * s.v[2] + r.v[3] * s.v[3];
+  return cmac(cmac(cmac(r.v[0] * s.v[0], r.v[1], s.v[1]), r.v[2], s.v[2]), r.v[3], s.v[3]);
 }
 
 // ---------------------------------------------------------------- gluon vertices
@@ -374,11 +429,40 @@ ME_HD c4<T> vvv(const c4<T>& J1, const c4<T>& J2, const r4<T>& k1, const r4<T>& 
   cx<T> b = rdot(k3 - k1, J2);
   r4<T> d = k1 - k2;
   c4<T> W;
-  W.v[0] = d.e * j12 + a * J2.v[0] + b * J1.v[0];
-  W.v[1] = d.x * j12 + a * J2.v[1] + b * J1.v[1];
-  W.v[2] = d.y * j12 + a * J2.v[2] + b * J1.v[2];
-  W.v[3] = d.z * j12 + a * J2.v[3] + b * J1.v[3];
+  W.v[0] = cmac(cmac(d.e * j12, a, J2.v[0]), b, J1.v[0]);
+  W.v[1] = cmac(cmac(d.x * j12, a, J2.v[1]), b, J1.v[1]);
+  W.v[2] = cmac(cmac(d.y * j12, a, J2.v[2]), b, J1.v[2]);
+  W.v[3] = cmac(cmac(d.z * j12, a, J2.v[3]), b, J1.v[3]);
   return W;
+}
+// s W(J1, J2), and acc + s W(J1, J2): the scale goes into the three scalar coefficients
+template <typename T>
+ME_HD c4<T> vvv(const c4<T>& J1, const c4<T>& J2, const r4<T>& k1, const r4<T>& k2, T s) {
+  r4<T> k3 = -(k1 + k2);
+  const cx<T> j12 = s * cdot(J1, J2);
+  const cx<T> a = s * rdot(k2 - k3, J1);
+  const cx<T> b = s * rdot(k3 - k1, J2);
+  r4<T> d = k1 - k2;
+  c4<T> W;
+  W.v[0] = cmac(cmac(d.e * j12, a, J2.v[0]), b, J1.v[0]);
+  W.v[1] = cmac(cmac(d.x * j12, a, J2.v[1]), b, J1.v[1]);
+  W.v[2] = cmac(cmac(d.y * j12, a, J2.v[2]), b, J1.v[2]);
+  W.v[3] = cmac(cmac(d.z * j12, a, J2.v[3]), b, J1.v[3]);
+  return W;
+}
+template <typename T>
+ME_HD void vvv_acc(c4<T>& acc, const c4<T>& J1, const c4<T>& J2, const r4<T>& k1, const r4<T>& k2, T s) {
+  r4<T> k3 = -(k1 + k2);
+  const cx<T> j12 = s * cdot(J1, J2);
+  const cx<T> a = s * rdot(k2 - k3, J1);
+  const cx<T> b = s * rdot(k3 - k1, J2);
+  r4<T> d = k1 - k2;
+  const T dd[4] = {d.e, d.x, d.y, d.z};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const cx<T> t{acc.v[i].re + dd[i] * j12.re, acc.v[i].im + dd[i] * j12.im};
+    acc.v[i] = cmac(cmac(t, a, J2.v[i]), b, J1.v[i]);
+  }
 }
 // colour-ordered four-gluon structure: 2(L.R) M - (L.M) R - (M.R) L
 template <typename T>
@@ -387,7 +471,7 @@ ME_HD c4<T> vvvv_ordered(const c4<T>& L, const c4<T>& M, const c4<T>& R) {
   cx<T> two_lr = lr + lr;
   c4<T> o;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) o.v[i] = two_lr * M.v[i] - lm * R.v[i] - mr * L.v[i];
+  for (int i = 0; i < 4; ++i) o.v[i] = cmsb(cmsb(two_lr * M.v[i], lm, R.v[i]), mr, L.v[i]);
   return o;
 }
 

@@ -339,23 +339,20 @@ ME_HD void amp_tt2_block(const KinTT<T, 2>& K, int hb, const Couplings& cp, cons
   const r4<T> k0 = K.q[0], k1 = K.q[1], kt = K.pl[2];
   const c4<T> e0 = (ov != nullptr && ov_leg == 0) ? *ov : polvec_of(K.wg[0], hel_of(hb, 0), false);
   const c4<T> e1 = (ov != nullptr && ov_leg == 1) ? *ov : polvec_of(K.wg[1], hel_of(hb, 1), false);
-  c4<T> J01 = vvv(e0, e1, -k0, -k1);
-  cscale(J01, -g * K.ig[3]);
+  const c4<T> J01 = vvv(e0, e1, -k0, -k1, -g * K.ig[3]);
   const sl4<T> s0 = slashed(e0), s1 = slashed(e1), s01 = slashed(J01);
-  const r4<T> Q0 = kt + k0, Q1 = kt + k1;
+  const prop4<T> P0 = scaled_prop(kt + k0, mt, -g * K.iq[1]), P1 = scaled_prop(kt + k1, mt, -g * K.iq[2]);
   const c4<T> v[2] = {spinor_v_of(K.wtb, -1), spinor_v_of(K.wtb, 1)};
 #pragma unroll
   for (int ht = 0; ht < 2; ++ht) {
     const c4<T> ub = dbar(spinor_u_of(K.wt, ht ? 1 : -1));
     const c4<T> S = row_slash(ub, s01);
-    c4<T> U0 = row_prop(row_slash(ub, s0), Q0, mt);
-    cscale(U0, -g * K.iq[1]);
-    c4<T> U1 = row_prop(row_slash(ub, s1), Q1, mt);
-    cscale(U1, -g * K.iq[2]);
-    c4<T> R0 = row_slash(U0, s1);
-    cadd(R0, S);
-    c4<T> R1 = row_slash(U1, s0);
-    csub(R1, S);
+    const c4<T> U0 = row_prop(row_slash(ub, s0), P0);
+    const c4<T> U1 = row_prop(row_slash(ub, s1), P1);
+    c4<T> R0 = S;
+    row_slash_acc(R0, U0, s1);
+    c4<T> R1 = cneg(S);
+    row_slash_acc(R1, U1, s0);
 #pragma unroll
     for (int hv = 0; hv < 2; ++hv) {
       cx<T> A[2] = {times_i(spdot(R0, v[hv])) * g, times_i(spdot(R1, v[hv])) * g};
@@ -374,32 +371,28 @@ ME_HD void amp_tt3_block(const KinTT<T, 3>& K, int hb, const Couplings& cp, F&& 
   const c4<T> e0 = polvec_of(K.wg[0], hel_of(hb, 0), false);
   const c4<T> e1 = polvec_of(K.wg[1], hel_of(hb, 1), false);
   const c4<T> e2 = polvec_of(K.wg[2], hel_of(hb, 4), true);
-  c4<T> J01 = vvv(e0, e1, -k0, -k1);
-  cscale(J01, -g * K.ig[3]);
-  c4<T> J02 = vvv(e0, e2, -k0, -k2);
-  cscale(J02, -g * K.ig[5]);
-  c4<T> J12 = vvv(e1, e2, -k1, -k2);
-  cscale(J12, -g * K.ig[6]);
+  const c4<T> J01 = vvv(e0, e1, -k0, -k1, -g * K.ig[3]);
+  const c4<T> J02 = vvv(e0, e2, -k0, -k2, -g * K.ig[5]);
+  const c4<T> J12 = vvv(e1, e2, -k1, -k2, -g * K.ig[6]);
   const T c3 = -g * K.ig[7], c4g = g * g * K.ig[7];
-  c4<T> F0 = vvv(e0, J12, -k0, -(k1 + k2));
-  cadd(F0, vvv(J01, e2, -(k0 + k1), -k2));
-  cscale(F0, c3);
-  caxpy(F0, cx<T>{c4g, T(0)}, vvvv_ordered(e0, e1, e2));
-  c4<T> F1 = vvv(J12, e0, -(k1 + k2), -k0);  // = vvv(e0, -J12, ...) by antisymmetry
-  cadd(F1, vvv(J02, e1, -(k0 + k2), -k1));
-  cscale(F1, c3);
-  caxpy(F1, cx<T>{c4g, T(0)}, vvvv_ordered(e0, e2, e1));
-  c4<T> F2 = vvv(e1, J02, -k1, -(k0 + k2));
-  cadd(F2, vvv(e2, J01, -k2, -(k0 + k1)));    // = vvv(-J01, e2, ...)
-  cscale(F2, c3);
-  caxpy(F2, cx<T>{c4g, T(0)}, vvvv_ordered(e1, e0, e2));
+  c4<T> F0 = vvv(e0, J12, -k0, -(k1 + k2), c3);
+  vvv_acc(F0, J01, e2, -(k0 + k1), -k2, c3);
+  caxpy(F0, c4g, vvvv_ordered(e0, e1, e2));
+  c4<T> F1 = vvv(J12, e0, -(k1 + k2), -k0, c3);  // = vvv(e0, -J12, ...) by antisymmetry
+  vvv_acc(F1, J02, e1, -(k0 + k2), -k1, c3);
+  caxpy(F1, c4g, vvvv_ordered(e0, e2, e1));
+  c4<T> F2 = vvv(e1, J02, -k1, -(k0 + k2), c3);
+  vvv_acc(F2, e2, J01, -k2, -(k0 + k1), c3);  // = vvv(-J01, e2, ...)
+  caxpy(F2, c4g, vvvv_ordered(e1, e0, e2));
   const sl4<T> se0 = slashed(e0), se1 = slashed(e1), se2 = slashed(e2);
   const sl4<T> sJ01 = slashed(J01), sJ02 = slashed(J02), sJ12 = slashed(J12);
   const sl4<T> sF0 = slashed(F0), sF1 = slashed(F1), sF2 = slashed(F2);
   const c4<T> v[2] = {spinor_v_of(K.wtb, -1), spinor_v_of(K.wtb, 1)};
   const r4<T> Q0 = kt + k0, Q1 = kt + k1, Q2 = kt + k2;
-  const r4<T> Q01 = Q0 + k1, Q02 = Q0 + k2, Q12 = Q1 + k2;
-  const T c01 = -g * K.iq[3], c02 = -g * K.iq[5], c12 = -g * K.iq[6];
+  const prop4<T> P0 = scaled_prop(Q0, mt, -g * K.iq[1]), P1 = scaled_prop(Q1, mt, -g * K.iq[2]),
+                 P2 = scaled_prop(Q2, mt, -g * K.iq[4]);
+  const prop4<T> P01 = scaled_prop(Q0 + k1, mt, -g * K.iq[3]), P02 = scaled_prop(Q0 + k2, mt, -g * K.iq[5]),
+                 P12 = scaled_prop(Q1 + k2, mt, -g * K.iq[6]);
 #pragma unroll
   for (int ht = 0; ht < 2; ++ht) {
     const c4<T> ub = dbar(spinor_u_of(K.wt, ht ? 1 : -1));
@@ -412,55 +405,40 @@ ME_HD void amp_tt3_block(const KinTT<T, 3>& K, int hb, const Couplings& cp, F&& 
     R[5] = R[0];
     const c4<T> S01 = row_slash(ub, sJ01), S02 = row_slash(ub, sJ02), S12 = row_slash(ub, sJ12);
     {  // first gluon 0: orderings 012, 021
-      c4<T> U = row_prop(row_slash(ub, se0), Q0, mt);
-      cscale(U, -g * K.iq[1]);
+      const c4<T> U = row_prop(row_slash(ub, se0), P0);
       const c4<T> t = row_slash(U, sJ12);
       cadd(R[0], t);
       csub(R[1], t);
-      c4<T> r = row_slash(U, se1);
-      cadd(r, S01);
-      c4<T> W = row_prop(r, Q01, mt);
-      cscale(W, c01);
-      cadd(R[0], row_slash(W, se2));
-      r = row_slash(U, se2);
-      cadd(r, S02);
-      W = row_prop(r, Q02, mt);
-      cscale(W, c02);
-      cadd(R[1], row_slash(W, se1));
+      c4<T> r = S01;
+      row_slash_acc(r, U, se1);
+      row_slash_acc(R[0], row_prop(r, P01), se2);
+      r = S02;
+      row_slash_acc(r, U, se2);
+      row_slash_acc(R[1], row_prop(r, P02), se1);
     }
     {  // first gluon 1: orderings 102, 120
-      c4<T> U = row_prop(row_slash(ub, se1), Q1, mt);
-      cscale(U, -g * K.iq[2]);
+      const c4<T> U = row_prop(row_slash(ub, se1), P1);
       const c4<T> t = row_slash(U, sJ02);
       cadd(R[2], t);
       csub(R[3], t);
-      c4<T> r = row_slash(U, se0);
-      csub(r, S01);
-      c4<T> W = row_prop(r, Q01, mt);
-      cscale(W, c01);
-      cadd(R[2], row_slash(W, se2));
-      r = row_slash(U, se2);
-      cadd(r, S12);
-      W = row_prop(r, Q12, mt);
-      cscale(W, c12);
-      cadd(R[3], row_slash(W, se0));
+      c4<T> r = cneg(S01);
+      row_slash_acc(r, U, se0);
+      row_slash_acc(R[2], row_prop(r, P01), se2);
+      r = S12;
+      row_slash_acc(r, U, se2);
+      row_slash_acc(R[3], row_prop(r, P12), se0);
     }
     {  // first gluon 2: orderings 201, 210
-      c4<T> U = row_prop(row_slash(ub, se2), Q2, mt);
-      cscale(U, -g * K.iq[4]);
+      const c4<T> U = row_prop(row_slash(ub, se2), P2);
       const c4<T> t = row_slash(U, sJ01);
       cadd(R[4], t);
       csub(R[5], t);
-      c4<T> r = row_slash(U, se0);
-      csub(r, S02);
-      c4<T> W = row_prop(r, Q02, mt);
-      cscale(W, c02);
-      cadd(R[4], row_slash(W, se1));
-      r = row_slash(U, se1);
-      csub(r, S12);
-      W = row_prop(r, Q12, mt);
-      cscale(W, c12);
-      cadd(R[5], row_slash(W, se0));
+      c4<T> r = cneg(S02);
+      row_slash_acc(r, U, se0);
+      row_slash_acc(R[4], row_prop(r, P02), se1);
+      r = cneg(S12);
+      row_slash_acc(r, U, se1);
+      row_slash_acc(R[5], row_prop(r, P12), se0);
     }
 #pragma unroll
     for (int hv = 0; hv < 2; ++hv) {
