@@ -292,6 +292,13 @@ static int build_tables(ColourTables& tab) {
         tab.Cf[it.pid][x * nf + y] = (float)c.real();
       }
     }
+    for (int x = 0; x < nf; ++x)
+      for (int y = x; y < nf; ++y) {
+        if (tab.C[it.pid][x * nf + y] != tab.C[it.pid][y * nf + x]) return fail(ME_ERR_PROCESS, "colour matrix not symmetric");
+        const double u = (y == x ? 1.0 : 2.0) * tab.C[it.pid][x * nf + y];
+        tab.U[it.pid][x * nf + y] = u;
+        tab.Uf[it.pid][x * nf + y] = (float)u;
+      }
     // Born colour correlators C^{kl}_{xy} = sum_a <T_k^a e_x | T_l^a e_y>
     if (it.pid == P_GG_TT || it.pid == P_UU_TT) {
       const int ci = it.pid == P_GG_TT ? 0 : 1;

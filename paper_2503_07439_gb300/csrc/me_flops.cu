@@ -33,6 +33,11 @@ inline Flop msqrt(Flop a) { ++g_ops; return Flop(std::sqrt(a.v)); }  // found by
 
 using namespace me;
 
+// J^dagger C J per helicity as the kernels evaluate it (me_kernels.cuh: colour_sum): for up
+// to 6 flows the triangular form over the doubled upper triangle, 2 NF^2 + 4 NF flops;
+// beyond, the full matrix, 4 NF^2 + 4 NF
+static double colour_flops(int nf) { return nf <= 6 ? 2.0 * nf * nf + 4.0 * nf : 4.0 * nf * nf + 4.0 * nf; }
+
 // one helicity block (me_procs.cuh): amplitudes of four helicities plus their colour sums
 template <int PID>
 static double block_ops(const r4<double>* p, int hb = 1, const c4<Flop>* ov = nullptr, int ov_leg = -1) {
@@ -41,7 +46,7 @@ static double block_ops(const r4<double>* p, int hb = 1, const c4<Flop>* ov = nu
   g_ops = 0;
   int calls = 0;
   amplitude_block<PID, Flop>(K, hb, cp, [&](int, const cx<Flop>*) { ++calls; }, ov, ov_leg);
-  return (double)g_ops + calls * (4.0 * Proc<PID>::NFLOW * Proc<PID>::NFLOW + 4.0 * Proc<PID>::NFLOW);
+  return (double)g_ops + calls * colour_flops(Proc<PID>::NFLOW);
 }
 
 // per-event preparation (reciprocal denominators etc. in the amplitude's type)

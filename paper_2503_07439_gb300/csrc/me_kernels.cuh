@@ -17,9 +17,11 @@
 #include "me_procs.cuh"
 #include "me_tc.cuh"
 
-// minimum resident 128-thread blocks per SM requested from the register allocator
+// minimum resident 128-thread blocks per SM requested from the register allocator: 2
+// gives the subtracted-real kernels up to 255 registers (8 warps per SM, fewer spills);
+// measured against 3 (168 registers, 12 warps): 9.56 against 9.64 ms per c2 step
 #ifndef ME_MINB
-#define ME_MINB 3
+#define ME_MINB 2
 #endif
 
 namespace me {
@@ -30,9 +32,14 @@ constexpr int N_PAIRS = 10;  // unordered pairs (k<=l) of the 4 coloured legs of
 // Device-resident process constants (written once per device at set-up):
 // colour matrices (row-major NFLOW x NFLOW, in double and float) and the 2->2 Born
 // colour correlators C^{kl} (pair order (0,0),(0,1),..,(3,3); [0] gg->tt, [1] uu->tt).
+// U holds the upper triangle of the symmetric C with the off-diagonal entries doubled
+// (U_aa = C_aa, U_ab = 2 C_ab for b > a, zero below), so that
+// J^dagger C J = sum_a Re(J_a^* sum_{b >= a} U_ab J_b).
 struct ColourTables {
   double C[P_COUNT][MAX_FLOW * MAX_FLOW];
   float Cf[P_COUNT][MAX_FLOW * MAX_FLOW];
+  double U[P_COUNT][MAX_FLOW * MAX_FLOW];
+  float Uf[P_COUNT][MAX_FLOW * MAX_FLOW];
   double Ccorr[2][N_PAIRS][4];
 };
 
@@ -52,12 +59,32 @@ struct KParams {
 template <typename T> __device__ __forceinline__ const T* ctab(const ColourTables* t, int pid);
 template <> __device__ __forceinline__ const double* ctab<double>(const ColourTables* t, int pid) { return t->C[pid]; }
 template <> __device__ __forceinline__ const float* ctab<float>(const ColourTables* t, int pid) { return t->Cf[pid]; }
+template <typename T> __device__ __forceinline__ const T* utab(const ColourTables* t, int pid);
+template <> __device__ __forceinline__ const double* utab<double>(const ColourTables* t, int pid) { return t->U[pid]; }
+template <> __device__ __forceinline__ const float* utab<float>(const ColourTables* t, int pid) { return t->Uf[pid]; }
 
 template <int PID, typename T>
 __device__ __forceinline__ T colour_sum(const ColourTables* tab, const cx<T>* J) {
   constexpr int NF = Proc<PID>::NFLOW;
-  const T* __restrict__ Cm = ctab<T>(tab, PID);
   T s = T(0);
+  if constexpr (NF <= 6) {
+    // triangular form: NF (NF + 1) + 2 NF multiply-adds instead of 2 NF^2 + 2 NF
+    const T* __restrict__ Um = utab<T>(tab, PID);
+#pragma unroll
+    for (int a = 0; a < NF; ++a) {
+      const T d = Um[a * NF + a];
+      T zr = d * J[a].re, zi = d * J[a].im;
+#pragma unroll
+      for (int b = a + 1; b < NF; ++b) {
+        const T c = Um[a * NF + b];
+        zr += c * J[b].re;
+        zi += c * J[b].im;
+      }
+      s += J[a].re * zr + J[a].im * zi;
+    }
+    return s;
+  }
+  const T* __restrict__ Cm = ctab<T>(tab, PID);
 #pragma unroll 4
   for (int a = 0; a < NF; ++a) {
     T zr = T(0), zi = T(0);
@@ -240,9 +267,7 @@ __global__ void __launch_bounds__(TC4_THREADS, 2) k_tree_tc4(const double* __res
     for (int pp = lane; pp < 6; pp += 4) {
       const int x = pp < 3 ? 0 : (pp < 5 ? 1 : 2);
       const int y = pp < 3 ? pp + 1 : (pp < 5 ? pp - 1 : 3);
-      c4<float> J = vvv(ld_c4(cur, x), ld_c4(cur, y), -q[x], -q[y]);
-      cscale(J, -g * K.ig[(1 << x) | (1 << y)]);
-      st_c4(cur, 4 + pp, J);
+      st_c4(cur, 4 + pp, vvv(ld_c4(cur, x), ld_c4(cur, y), -q[x], -q[y], -g * K.ig[(1 << x) | (1 << y)]));
     }
     __syncwarp();
     // 3. triple currents
@@ -250,10 +275,10 @@ __global__ void __launch_bounds__(TC4_THREADS, 2) k_tree_tc4(const double* __res
       const int r = kJ3Rep[t], x = r & 15, y = (r >> 4) & 15, z = r >> 8;
       const int S = (1 << x) | (1 << y) | (1 << z);
       const c4<float> ex = ld_c4(cur, x), ey = ld_c4(cur, y), ez = ld_c4(cur, z);
-      c4<float> J = vvv(ex, ld_j2(cur, y, z), -q[x], -(q[y] + q[z]));
-      cadd(J, vvv(ld_j2(cur, x, y), ez, -(q[x] + q[y]), -q[z]));
-      cscale(J, -g * K.ig[S]);
-      caxpy(J, cx<float>{g * g * K.ig[S], 0.0f}, vvvv_ordered(ex, ey, ez));
+      const float c3 = -g * K.ig[S];
+      c4<float> J = vvv(ex, ld_j2(cur, y, z), -q[x], -(q[y] + q[z]), c3);
+      vvv_acc(J, ld_j2(cur, x, y), ez, -(q[x] + q[y]), -q[z], c3);
+      caxpy(J, g * g * K.ig[S], vvvv_ordered(ex, ey, ez));
       st_c4(cur, 10 + t, J);
     }
     __syncwarp();
@@ -262,14 +287,14 @@ __global__ void __launch_bounds__(TC4_THREADS, 2) k_tree_tc4(const double* __res
       const int r = kJ4Rep[t], w = r & 15, x = (r >> 4) & 15, y = (r >> 8) & 15, z = r >> 12;
       const c4<float> ew = ld_c4(cur, w), ez = ld_c4(cur, z);
       const c4<float> jwx = ld_j2(cur, w, x), jxy = ld_j2(cur, x, y), jyz = ld_j2(cur, y, z);
-      c4<float> J = vvv(ew, ld_c4(cur, triple_slot(x, y, z)), -q[w], -(q[x] + q[y] + q[z]));
-      cadd(J, vvv(jwx, jyz, -(q[w] + q[x]), -(q[y] + q[z])));
-      cadd(J, vvv(ld_c4(cur, triple_slot(w, x, y)), ez, -(q[w] + q[x] + q[y]), -q[z]));
-      cscale(J, -g * K.ig[15]);
+      const float c3 = -g * K.ig[15];
+      c4<float> J = vvv(ew, ld_c4(cur, triple_slot(x, y, z)), -q[w], -(q[x] + q[y] + q[z]), c3);
+      vvv_acc(J, jwx, jyz, -(q[w] + q[x]), -(q[y] + q[z]), c3);
+      vvv_acc(J, ld_c4(cur, triple_slot(w, x, y)), ez, -(q[w] + q[x] + q[y]), -q[z], c3);
       c4<float> V = vvvv_ordered(ew, ld_c4(cur, x), jyz);
       cadd(V, vvvv_ordered(ew, jxy, ez));
       cadd(V, vvvv_ordered(jwx, ld_c4(cur, y), ez));
-      caxpy(J, cx<float>{g * g * K.ig[15], 0.0f}, V);
+      caxpy(J, g * g * K.ig[15], V);
       st_c4(cur, 22 + t, J);
     }
     __syncwarp();
@@ -278,29 +303,27 @@ __global__ void __launch_bounds__(TC4_THREADS, 2) k_tree_tc4(const double* __res
     for (int ht = 0; ht < 2; ++ht) {
       const c4<float> ub = dbar(spinor_u_of(K.wt, ht ? 1 : -1));
       const int row0 = (wl & ~3) + 2 * ht;  // rows of (this event, ht, hv = 0 / 1)
-      c4<float> U1 = row_prop(row_slash(ub, ld_c4(cur, w)), kt + q[w], mt);
-      cscale(U1, -g * K.iq[1 << w]);
+      const c4<float> U1 = row_prop(row_slash(ub, ld_c4(cur, w)), scaled_prop(kt + q[w], mt, -g * K.iq[1 << w]));
       int f = 6 * w;
       for (int x = 0; x < 4; ++x) {
         if (x == w) continue;
         c4<float> r2 = row_slash(ub, ld_j2(cur, w, x));
-        cadd(r2, row_slash(U1, ld_c4(cur, x)));
-        c4<float> U2 = row_prop(r2, kt + q[w] + q[x], mt);
-        cscale(U2, -g * K.iq[(1 << w) | (1 << x)]);
+        row_slash_acc(r2, U1, ld_c4(cur, x));
+        const c4<float> U2 = row_prop(r2, scaled_prop(kt + q[w] + q[x], mt, -g * K.iq[(1 << w) | (1 << x)]));
         for (int y = 0; y < 4; ++y) {
           if (y == w || y == x) continue;
           const int z = 6 - w - x - y;
           c4<float> r3 = row_slash(ub, ld_c4(cur, triple_slot(w, x, y)));
-          cadd(r3, row_slash(U1, ld_j2(cur, x, y)));
-          cadd(r3, row_slash(U2, ld_c4(cur, y)));
-          c4<float> U3 = row_prop(r3, kt + q[w] + q[x] + q[y], mt);
-          cscale(U3, -g * K.iq[(1 << w) | (1 << x) | (1 << y)]);
+          row_slash_acc(r3, U1, ld_j2(cur, x, y));
+          row_slash_acc(r3, U2, ld_c4(cur, y));
+          const c4<float> U3 =
+              row_prop(r3, scaled_prop(kt + q[w] + q[x] + q[y], mt, -g * K.iq[(1 << w) | (1 << x) | (1 << y)]));
           const int s4 = kJ4OfOrdering[f];
           c4<float> R = row_slash(ub, ld_c4(cur, 22 + (s4 > 0 ? s4 : -s4) - 1));
-          if (s4 < 0) cscale(R, -1.0f);
-          cadd(R, row_slash(U1, ld_c4(cur, triple_slot(x, y, z))));
-          cadd(R, row_slash(U2, ld_j2(cur, y, z)));
-          cadd(R, row_slash(U3, ld_c4(cur, z)));
+          if (s4 < 0) R = cneg(R);
+          row_slash_acc(R, U1, ld_c4(cur, triple_slot(x, y, z)));
+          row_slash_acc(R, U2, ld_j2(cur, y, z));
+          row_slash_acc(R, U3, ld_c4(cur, z));
 #pragma unroll
           for (int hv = 0; hv < 2; ++hv) {
             const cx<float> a = times_i(spdot(R, v[hv])) * g;

@@ -344,6 +344,10 @@ ME_HD void row_slash_acc(c4<T>& acc, const c4<T>& r, const sl4<T>& S) {
   acc.v[2] = cmsb(cmac(acc.v[2], r.v[0], S.a), r.v[1], S.d);
   acc.v[3] = cmac(cmsb(acc.v[3], r.v[0], S.c), r.v[1], S.b);
 }
+template <typename T>
+ME_HD void row_slash_acc(c4<T>& acc, const c4<T>& r, const c4<T>& V) {
+  row_slash_acc(acc, r, slashed(V));
+}
 // Vslash times column spinor
 template <typename T>
 ME_HD c4<T> slash_col(const c4<T>& V, const c4<T>& s) {

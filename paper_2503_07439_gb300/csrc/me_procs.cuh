@@ -672,9 +672,7 @@ ME_HD void amp_tt4_block(const KinTT<T, 4>& K, int hb, const Couplings& cp, F&& 
   for (int x = 0; x < 4; ++x)
 #pragma unroll
     for (int y = x + 1; y < 4; ++y) {
-      c4<T> J = vvv(e[x], e[y], -q[x], -q[y]);
-      cscale(J, -g * K.ig[(1 << x) | (1 << y)]);
-      J2[pidx(x, y)] = J;
+      J2[pidx(x, y)] = vvv(e[x], e[y], -q[x], -q[y], -g * K.ig[(1 << x) | (1 << y)]);
     }
   auto j2 = [&](int x, int y) {  // ordered pair current, J(yx) = -J(xy)
     c4<T> J = J2[x < y ? pidx(x, y) : pidx(y, x)];
@@ -698,10 +696,10 @@ ME_HD void amp_tt4_block(const KinTT<T, 4>& K, int hb, const Couplings& cp, F&& 
       for (int z = x + 1; z < 4; ++z) {
         if (y == x || y == z) continue;
         const int S = (1 << x) | (1 << y) | (1 << z);
-        c4<T> J = vvv(e[x], j2(y, z), -q[x], -(q[y] + q[z]));
-        cadd(J, vvv(j2(x, y), e[z], -(q[x] + q[y]), -q[z]));
-        cscale(J, -g * K.ig[S]);
-        caxpy(J, cx<T>{g * g * K.ig[S], T(0)}, vvvv_ordered(e[x], e[y], e[z]));
+        const T c3 = -g * K.ig[S], c4g = g * g * K.ig[S];
+        c4<T> J = vvv(e[x], j2(y, z), -q[x], -(q[y] + q[z]), c3);
+        vvv_acc(J, j2(x, y), e[z], -(q[x] + q[y]), -q[z], c3);
+        caxpy(J, c4g, vvvv_ordered(e[x], e[y], e[z]));
         J3[tidx(x, y, z)] = J;
       }
   auto j3 = [&](int x, int y, int z) { return J3[tidx(x, y, z)]; };
@@ -718,14 +716,13 @@ ME_HD void amp_tt4_block(const KinTT<T, 4>& K, int hb, const Couplings& cp, F&& 
         const int z = 6 - w - x - y;
         if (z < w) continue;
         const T c3 = -g * K.ig[15], c4g = g * g * K.ig[15];
-        c4<T> J = vvv(e[w], j3(x, y, z), -q[w], -(q[x] + q[y] + q[z]));
-        cadd(J, vvv(j2(w, x), j2(y, z), -(q[w] + q[x]), -(q[y] + q[z])));
-        cadd(J, vvv(j3(w, x, y), e[z], -(q[w] + q[x] + q[y]), -q[z]));
-        cscale(J, c3);
+        c4<T> J = vvv(e[w], j3(x, y, z), -q[w], -(q[x] + q[y] + q[z]), c3);
+        vvv_acc(J, j2(w, x), j2(y, z), -(q[w] + q[x]), -(q[y] + q[z]), c3);
+        vvv_acc(J, j3(w, x, y), e[z], -(q[w] + q[x] + q[y]), -q[z], c3);
         c4<T> V = vvvv_ordered(e[w], e[x], j2(y, z));
         cadd(V, vvvv_ordered(e[w], j2(x, y), e[z]));
         cadd(V, vvvv_ordered(j2(w, x), e[y], e[z]));
-        caxpy(J, cx<T>{c4g, T(0)}, V);
+        caxpy(J, c4g, V);
         J4[n4++] = J;
       }
   // rank of the quadruple current of ordering wxyz among those with first < last
@@ -752,30 +749,28 @@ ME_HD void amp_tt4_block(const KinTT<T, 4>& K, int hb, const Couplings& cp, F&& 
     int f = 0;
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
-      c4<T> U1 = row_prop(row_slash(ub, e[w]), kt + q[w], mt);
-      cscale(U1, -g * K.iq[1 << w]);
+      const c4<T> U1 = row_prop(row_slash(ub, e[w]), scaled_prop(kt + q[w], mt, -g * K.iq[1 << w]));
 #pragma unroll
       for (int x = 0; x < 4; ++x) {
         if (x == w) continue;
         c4<T> r2 = row_slash(ub, j2(w, x));
-        cadd(r2, row_slash(U1, e[x]));
-        c4<T> U2 = row_prop(r2, kt + q[w] + q[x], mt);
-        cscale(U2, -g * K.iq[(1 << w) | (1 << x)]);
+        row_slash_acc(r2, U1, e[x]);
+        const c4<T> U2 = row_prop(r2, scaled_prop(kt + q[w] + q[x], mt, -g * K.iq[(1 << w) | (1 << x)]));
 #pragma unroll
         for (int y = 0; y < 4; ++y) {
           if (y == w || y == x) continue;
           const int z = 6 - w - x - y;
           c4<T> r3 = row_slash(ub, j3(w, x, y));
-          cadd(r3, row_slash(U1, j2(x, y)));
-          cadd(r3, row_slash(U2, e[y]));
-          c4<T> U3 = row_prop(r3, kt + q[w] + q[x] + q[y], mt);
-          cscale(U3, -g * K.iq[(1 << w) | (1 << x) | (1 << y)]);
+          row_slash_acc(r3, U1, j2(x, y));
+          row_slash_acc(r3, U2, e[y]);
+          const c4<T> U3 =
+              row_prop(r3, scaled_prop(kt + q[w] + q[x] + q[y], mt, -g * K.iq[(1 << w) | (1 << x) | (1 << y)]));
           c4<T> J = z > w ? J4[q4(w, x, y)] : J4[q4(z, y, x)];
           if (z < w) cscale(J, T(-1));
           c4<T> R = row_slash(ub, J);
-          cadd(R, row_slash(U1, j3(x, y, z)));
-          cadd(R, row_slash(U2, j2(y, z)));
-          cadd(R, row_slash(U3, e[z]));
+          row_slash_acc(R, U1, j3(x, y, z));
+          row_slash_acc(R, U2, j2(y, z));
+          row_slash_acc(R, U3, e[z]);
 #pragma unroll
           for (int hv = 0; hv < 2; ++hv) A[hv][f] = times_i(spdot(R, v[hv])) * g;
           ++f;
