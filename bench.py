@@ -44,13 +44,13 @@ FP64_PER_SM_CLK = 2  # DFMA thread-ops per SM per clock (ncu: ..._op_dfma_pred_o
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu --set full
 # capture of each kernel (summaries in profiles/), with the hash of the kernel sources they
 # were taken on; reported only while the sources still hash the same.
-KERNEL_SOURCES_SHA = "f645b829c5f73ff1"
+KERNEL_SOURCES_SHA = "f2d327abf0339ae0"
 TRAFFIC = {
-    ("c2", "rescue"): {"bytes": 0.696213e9 + 3.733541e9, "points": 188216,
+    ("c2", "rescue"): {"bytes": 0.446786e9 + 1.545072e9, "points": 188216,
                        "profile": "profiles/k_real_sub_gg_ttg_double_rescue.md"},
-    ("c2", "main"): {"bytes": 0.177500e9 + 0.286940e9, "points": 1 << 20,
+    ("c2", "main"): {"bytes": 0.176380e9 + 0.010518e9, "points": 1 << 20,
                      "profile": "profiles/k_real_sub_gg_ttg_float_2p20.md"},
-    ("c3", "main"): {"bytes": 0.052634e9 + 0.022927e9, "points": 1 << 18,
+    ("c3", "main"): {"bytes": 0.053037e9 + 0.022748e9, "points": 1 << 18,
                      "profile": "profiles/k_tree_gg_ttgg_float_tc_2p18.md"},
 }
 
@@ -101,28 +101,38 @@ def _peaks():
 
 
 class Clocks:
-    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+    """nvidia-smi sampling (every 50 ms, time-stamped) of SM clock and throttle reasons.
+
+    The sampler starts before the warm-up so that it is running when the timed region
+    begins; `mark(t0, t1)` records the wall-clock bounds of the timed region and the
+    summary keeps the samples taken inside it (if the region is shorter than the
+    sampling interval and none falls inside, the first sample after its start)."""
 
     def __init__(self, index: int):
         self.path = tempfile.mktemp(suffix=".csv")
         self.index = index
         self.proc = None
+        self.t0 = self.t1 = None
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index),
-                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "--query-gpu=timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                  "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
         return self
 
+    def mark(self, t0: float, t1: float):
+        self.t0, self.t1 = t0, t1
+
     def __exit__(self, *a):
         if self.proc:
+            time.sleep(0.1)  # let a sample after the region land
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -130,24 +140,31 @@ class Clocks:
                 self.proc.kill()
 
     def summary(self):
-        sm, mx, reasons = [], [], set()
+        import datetime
+        rows = []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         try:
             for line in open(self.path):
                 f = [x.strip() for x in line.split(",")]
-                if len(f) < 8:
+                if len(f) < 9:
                     continue
-                sm.append(float(f[0]))
-                mx.append(float(f[1]))
-                for n, v in zip(names, f[4:8]):
-                    if v.lower() == "active":
-                        reasons.add(n)
+                try:
+                    ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                except ValueError:
+                    ts = None
+                rows.append((ts, float(f[1]), float(f[2]), [n for n, v in zip(names, f[5:9]) if v.lower() == "active"]))
         except Exception:
             pass
-        if not sm:
+        inside = [r for r in rows if r[0] is not None and self.t0 is not None and self.t0 <= r[0] <= self.t1]
+        where = "timed region"
+        if not inside:
+            after = [r for r in rows if r[0] is not None and self.t0 is not None and r[0] >= self.t0]
+            inside, where = after[:1], "first sample after the start of the timed region"
+        if not inside:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return {"sm_mhz": float(np.median([r[1] for r in inside])), "sm_max_mhz": max(r[2] for r in inside),
+                "reasons": sorted({n for r in inside for n in r[3]}), "samples": len(inside), "window": where,
+                "interval_ms": 50}
 
 
 def _oracle_chunk(args):
@@ -406,6 +423,7 @@ def main():
         if dist is not None:
             dist.barrier()
 
+    clk = Clocks(local).__enter__()  # sampling runs from before the warm-up
     for _ in range(warmup):
         step(handles)
     torch.cuda.synchronize()
@@ -414,15 +432,18 @@ def main():
         hh.enable_stage_timers(True)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    with Clocks(local) as clk:
-        barrier()
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(args.steps):
-            step(handles)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        barrier()
+    barrier()
+    torch.cuda.synchronize()
+    w0 = time.time()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(handles)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    w1 = time.time()
+    barrier()
+    clk.mark(w0, w1)
+    clk.__exit__()
     ms = e0.elapsed_time(e1)
     # the dominant kernel is the first call's main kernel
     stages = [hh.stage_times() for hh, *_ in handles]

@@ -123,7 +123,10 @@ __global__ void k_rambo(uint64_t seed, uint32_t stream, long long first, double 
       }
       const double dx = fs / df;
       xs -= dx;
-      if (fabs(dx) < 1e-16) break;
+      // Newton converges quadratically: a step below 1e-15 of xs leaves xs exact to
+      // rounding (an absolute 1e-16 would sit below the rounding of xs ~ 1 and run
+      // all 60 steps)
+      if (fabs(dx) <= 1e-15 * xs) break;
     }
     double sk = 0.0, prod = 1.0, sk2e = 0.0;
 #pragma unroll
