@@ -499,6 +499,21 @@ def main():
         devgen = {"value": n / (gms * 1e-3), "unit": UNIT, "ms_per_step": gms,
                   "note": "momenta and weights generated on the device each step, then evaluated"}
 
+    # unweighted events from the step's subtracted-real weights (me_unweight: accept/reject
+    # against the batch maximum of |w|, on the device; synchronous, so timed on the host)
+    unw = None
+    if calls[0][1] == "real_subtracted":
+        hh0, _, _, _, od0 = handles[0]
+        hh0.unweight(od0, seed=SEED, stream=9)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        reps = 5
+        for _ in range(reps):
+            kept, _, wm, _ = hh0.unweight(od0, seed=SEED, stream=9)
+        uw_s = (time.perf_counter() - t0) / reps
+        unw = {"points_per_s": n / uw_s, "ms_per_call": uw_s * 1e3, "events_kept": int(kept.shape[0]),
+               "w_max": wm, "note": "accept/reject of the c2 weights against max |w| (me_unweight, host-timed)"}
+
     # end to end through the C ABI with pinned host buffers (copies inside the timed region)
     hosts = []
     for (proc, entry, bb), (hh, f, *_rest) in zip(calls, handles):
@@ -591,6 +606,7 @@ def main():
                 "path": "C-ABI call on pinned host buffers: the kernels read the inputs and write the results in "
                         "place over the CPU-GPU link (no staging copy); the call returns with results on the host"},
         "device_generated": devgen,
+        "unweighting": unw,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
         "cpu_baseline": cpu,

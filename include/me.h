@@ -189,6 +189,30 @@ int me_synchronize(me_handle* h);
 int me_generate_flat(me_handle* h, uint64_t seed, uint32_t stream, int64_t first_point, double sqrt_s, int64_t n,
                      double* momenta, double* ps_weights);
 
+/*
+ * Unweighted events from weighted points: the accept/reject step that turns a sample
+ * weighted by the integrand into events distributed like it (Sec. 3.1), for signed NLO
+ * weights.  Point i is kept iff u_i * w_max < |w_i|, where u_i in (0,1) is the first
+ * uniform of Philox4x32-10 (key = seed) at counter (lo and hi words of first_point + i,
+ * stream, 0), mapped as in me_generate_flat: ((x0 >> 5) 2^26 + (x1 >> 6) + 1/2) 2^-53.
+ * A kept point carries the event weight sign(w_i) * max(w_max, |w_i|), so the expected
+ * event weight of every point is w_i; points with |w_i| > w_max (overweight) are always
+ * kept with their own weight.  Use a `stream` other than the one that generated the
+ * points.  NaN weights are never kept.
+ *   weights       device float64[n]
+ *   w_max         > 0: used as given; <= 0: the maximum of |w_i| over the batch
+ *   kept          device int32[n]: the indices of the kept points, in increasing order
+ *   kept_weights  device float64[n] or NULL: their event weights
+ *   n_kept        host: number of kept points (entries written to kept, kept_weights)
+ *   w_max_used    host or NULL: the w_max applied
+ *   n_over        host or NULL: number of overweight points (all kept)
+ * Runs on the handle's stream and returns when the results are in place.  ME_ERR_ARG for
+ * host buffers, n outside [0, 2^31), first_point < 0 or a NaN w_max.
+ */
+int me_unweight(me_handle* h, const double* weights, int64_t n, double w_max, uint64_t seed, uint32_t stream,
+                int64_t first_point, int32_t* kept, double* kept_weights, int64_t* n_kept, double* w_max_used,
+                int64_t* n_over);
+
 /* Release the handle and its device scratch (waits for its stream).  NULL is a no-op. */
 void me_destroy(me_handle* h);
 

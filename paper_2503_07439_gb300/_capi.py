@@ -94,6 +94,9 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "me_server_destroy": (None, [vp]),
         "me_server_stats": (ctypes.c_int, [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
         "me_generate_flat": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.c_uint32, i64, ctypes.c_double, i64, vp, vp]),
+        "me_unweight": (ctypes.c_int, [vp, vp, i64, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint32, i64, vp, vp,
+                                       ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_int64)]),
         "me_eval_real_subtracted_noalloc": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(MEParams), vp, vp, i64,
                                                            vp, vp]),
     }
@@ -205,6 +208,21 @@ class Handle:
         if self.sync:
             _check(self.lib.me_synchronize(self.h))
         return p, w
+
+    def unweight(self, w, w_max: float = 0.0, seed: int = 0, stream: int = 1, first_point: int = 0):
+        """Unweighted events from the device weights `w` (torch float64 CUDA tensor):
+        (indices of the kept points, their event weights, w_max applied, overweight count).
+        w_max <= 0 takes the batch maximum of |w|."""
+        import torch
+        n = int(w.shape[0])
+        kept = torch.empty(max(n, 1), dtype=torch.int32, device=w.device)
+        kw = torch.empty(max(n, 1), dtype=torch.float64, device=w.device)
+        nk, wm, no = ctypes.c_int64(), ctypes.c_double(), ctypes.c_int64()
+        wp, _keep = _ptr(w)
+        _check(self.lib.me_unweight(self.h, wp, n, float(w_max), seed, stream, first_point,
+                                    ctypes.c_void_p(kept.data_ptr()), ctypes.c_void_p(kw.data_ptr()),
+                                    ctypes.byref(nk), ctypes.byref(wm), ctypes.byref(no)))
+        return kept[:nk.value], kw[:nk.value], wm.value, no.value
 
     def last_rescued(self) -> int:
         v = ctypes.c_int64()

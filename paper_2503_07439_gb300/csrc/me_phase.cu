@@ -17,6 +17,7 @@
 
 #include <cmath>
 #include <cstdint>
+#include <cstring>
 #include <string>
 
 #include "../../include/me.h"
@@ -158,6 +159,143 @@ __global__ void k_rambo(uint64_t seed, uint32_t stream, long long first, double 
   if (wgt) wgt[i] = w;
 }
 
+// ---------------------------------------------------------------- unweighting
+// Hit-or-miss unweighting of signed weights: point i is kept iff u_i w_max < |w_i|, with
+// u_i the first uniform of Philox4x32-10 at counter (point lo, point hi, stream, 0);
+// a kept point carries sign(w_i) max(w_max, |w_i|), so that the expected event weight
+// is w_i.  The kept indices are written in increasing order: per-block counts, one
+// exclusive scan, then a scatter that recomputes the same decisions.
+constexpr int UW_THREADS = 256;
+
+struct UwArgs {
+  const double* w;
+  long n;
+  double wmax;                         // used when wmax_bits is null
+  const unsigned long long* wmax_bits; // device: bit pattern of the batch maximum of |w|
+  uint64_t seed;
+  uint32_t stream;
+  long long first;
+};
+
+__device__ __forceinline__ double uw_uniform(const UwArgs& a, long i) {
+  const unsigned long long idx = (unsigned long long)(a.first + i);
+  uint32_t c[4] = {(uint32_t)(idx & 0xFFFFFFFFull), (uint32_t)(idx >> 32), a.stream, 0u};
+  philox4x32_10(c, (uint32_t)(a.seed & 0xFFFFFFFFull), (uint32_t)(a.seed >> 32));
+  return u01(c[0], c[1]);
+}
+__device__ __forceinline__ double uw_wmax(const UwArgs& a) {
+  return a.wmax_bits ? __longlong_as_double((long long)*a.wmax_bits) : a.wmax;
+}
+
+// maximum of |w| (NaN skipped): the bit patterns of non-negative doubles order like the
+// numbers, so an integer maximum gives it, in any order of the blocks
+__global__ void k_uw_absmax(const double* __restrict__ w, long n, unsigned long long* __restrict__ out) {
+  __shared__ unsigned long long sm[UW_THREADS / 32];
+  unsigned long long m = 0;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const double x = fabs(w[i]);
+    if (x == x) {
+      const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+      m = b > m ? b : m;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long y = __shfl_xor_sync(0xffffffffu, m, o);
+    m = y > m ? y : m;
+  }
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    m = threadIdx.x < UW_THREADS / 32 ? sm[threadIdx.x] : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long y = __shfl_xor_sync(0xffffffffu, m, o);
+      m = y > m ? y : m;
+    }
+    if (threadIdx.x == 0) atomicMax(out, m);
+  }
+}
+
+__global__ void __launch_bounds__(UW_THREADS) k_uw_count(UwArgs a, int* __restrict__ counts,
+                                                          unsigned long long* __restrict__ n_over) {
+  const long i = (long)blockIdx.x * UW_THREADS + threadIdx.x;
+  const double wmax = uw_wmax(a);
+  bool keep = false, over = false;
+  if (i < a.n) {
+    const double aw = fabs(a.w[i]);
+    keep = uw_uniform(a, i) * wmax < aw;
+    over = aw > wmax;
+  }
+  const int c = __syncthreads_count(keep);
+  const int o = __syncthreads_count(over);
+  if (threadIdx.x == 0) {
+    counts[blockIdx.x] = c;
+    if (o) atomicAdd(n_over, (unsigned long long)o);
+  }
+}
+
+// exclusive scan of the per-block counts (one block of 1024 threads), total to *total
+__global__ void __launch_bounds__(1024) k_uw_scan(int* __restrict__ counts, long nb, unsigned long long* __restrict__ total) {
+  __shared__ int warp_sum[32];
+  __shared__ long long carry;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (long base = 0; base < nb; base += 1024) {
+    const long i = base + threadIdx.x;
+    const int v = i < nb ? counts[i] : 0;
+    int x = v;  // inclusive scan within the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      int s = warp_sum[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, s, o);
+        if (lane >= o) s += y;
+      }
+      warp_sum[lane] = s;  // inclusive over the warps
+    }
+    __syncthreads();
+    const int before = warp ? warp_sum[warp - 1] : 0;
+    if (i < nb) counts[i] = (int)(carry + before + x - v);
+    const int chunk = warp_sum[31];
+    __syncthreads();
+    if (threadIdx.x == 0) carry += chunk;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *total = (unsigned long long)carry;
+}
+
+__global__ void __launch_bounds__(UW_THREADS) k_uw_scatter(UwArgs a, const int* __restrict__ offsets,
+                                                            int* __restrict__ kept, double* __restrict__ kept_w) {
+  __shared__ int warp_cnt[UW_THREADS / 32];
+  const long i = (long)blockIdx.x * UW_THREADS + threadIdx.x;
+  const double wmax = uw_wmax(a);
+  bool keep = false;
+  double wi = 0.0;
+  if (i < a.n) {
+    wi = a.w[i];
+    keep = uw_uniform(a, i) * wmax < fabs(wi);
+  }
+  const unsigned bal = __ballot_sync(0xffffffffu, keep);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) warp_cnt[warp] = __popc(bal);
+  __syncthreads();
+  if (keep) {
+    int pos = offsets[blockIdx.x] + __popc(bal & ((1u << lane) - 1u));
+    for (int k = 0; k < warp; ++k) pos += warp_cnt[k];
+    kept[pos] = (int)i;
+    if (kept_w) kept_w[pos] = fabs(wi) > wmax ? wi : copysign(wmax, wi);
+  }
+}
+
 bool on_device(const void* ptr) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
@@ -205,5 +343,66 @@ extern "C" int me_generate_flat(me_handle* h, uint64_t seed, uint32_t stream, in
   }
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return me_internal_fail(ME_ERR_CUDA, (std::string("me_generate_flat: ") + cudaGetErrorString(e)).c_str());
+  return ME_OK;
+}
+
+extern "C" int me_unweight(me_handle* h, const double* weights, int64_t n, double w_max, uint64_t seed, uint32_t stream,
+                           int64_t first_point, int32_t* kept, double* kept_weights, int64_t* n_kept, double* w_max_used,
+                           int64_t* n_over) {
+  if (!h || !n_kept) return me_internal_fail(ME_ERR_ARG, "me_unweight: NULL handle or n_kept");
+  if (n < 0 || n > (int64_t)INT32_MAX || first_point < 0 || !(w_max == w_max))
+    return me_internal_fail(ME_ERR_ARG, "me_unweight: bad n, first_point or w_max");
+  *n_kept = 0;
+  if (n_over) *n_over = 0;
+  if (w_max_used) *w_max_used = w_max > 0.0 ? w_max : 0.0;
+  if (n == 0) return ME_OK;
+  if (!weights || !kept || !on_device(weights) || !on_device(kept) || (kept_weights && !on_device(kept_weights)))
+    return me_internal_fail(ME_ERR_ARG, "me_unweight: weights, kept and kept_weights must be device memory");
+  double masses[4];
+  int nout = 0;
+  cudaStream_t st = nullptr;
+  const int rc = me_internal_final_masses(h, masses, &nout, &st);  // the handle's device and stream
+  if (rc != ME_OK) return rc;
+  const long nb = (long)((n + UW_THREADS - 1) / UW_THREADS);
+  int* d_counts = nullptr;
+  unsigned long long* d_u64 = nullptr;  // [0] max |w| bits, [1] overweight count, [2] kept count
+  auto cuda_fail = [&](cudaError_t e) {
+    cudaFreeAsync(d_counts, st);
+    cudaFreeAsync(d_u64, st);
+    return me_internal_fail(ME_ERR_CUDA, (std::string("me_unweight: ") + cudaGetErrorString(e)).c_str());
+  };
+  cudaError_t e = cudaMallocAsync(&d_counts, nb * sizeof(int), st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&d_u64, 3 * sizeof(unsigned long long), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_u64, 0, 3 * sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  UwArgs a{weights, (long)n, w_max, nullptr, seed, stream, (long long)first_point};
+  if (!(w_max > 0.0)) {
+    const unsigned g = (unsigned)(nb < 4096 ? nb : 4096);
+    k_uw_absmax<<<g, UW_THREADS, 0, st>>>(weights, (long)n, d_u64);
+    a.wmax_bits = d_u64;
+  }
+  k_uw_count<<<(unsigned)nb, UW_THREADS, 0, st>>>(a, d_counts, d_u64 + 1);
+  k_uw_scan<<<1, 1024, 0, st>>>(d_counts, nb, d_u64 + 2);
+  k_uw_scatter<<<(unsigned)nb, UW_THREADS, 0, st>>>(a, d_counts, kept, kept_weights);
+  e = cudaGetLastError();
+  unsigned long long host[3] = {0, 0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host, d_u64, sizeof host, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaFreeAsync(d_counts, st);
+  if (e == cudaSuccess) {
+    d_counts = nullptr;
+    e = cudaFreeAsync(d_u64, st);
+  }
+  if (e == cudaSuccess) {
+    d_u64 = nullptr;
+    e = cudaStreamSynchronize(st);
+  }
+  if (e != cudaSuccess) return cuda_fail(e);
+  *n_kept = (int64_t)host[2];
+  if (n_over) *n_over = (int64_t)host[1];
+  if (w_max_used) {
+    double wm = w_max;
+    if (!(w_max > 0.0)) std::memcpy(&wm, &host[0], sizeof wm);
+    *w_max_used = wm;
+  }
   return ME_OK;
 }
