@@ -214,6 +214,24 @@ __device__ __forceinline__ c4<float> ld_j2(const float* b, int x, int y) {
   if (x > y) cscale(J, -1.0f);
   return J;
 }
+// the same eight floats read as the chiral combinations (V0 - V3, V0 + V3, V1 - i V2,
+// V1 + i V2) once a slot has been converted in place for the quark lines
+__device__ __forceinline__ sl4<float> ld_sl4(const float* b, int slot) {
+  const float4* p = reinterpret_cast<const float4*>(b + 8 * slot);
+  const float4 a = p[0], c = p[1];
+  return sl4<float>{{a.x, a.y}, {a.z, a.w}, {c.x, c.y}, {c.z, c.w}};
+}
+__device__ __forceinline__ void slash_in_place(float* b, int slot) {
+  const sl4<float> S = slashed(ld_c4(b, slot));
+  float4* p = reinterpret_cast<float4*>(b + 8 * slot);
+  p[0] = make_float4(S.a.re, S.a.im, S.b.re, S.b.im);
+  p[1] = make_float4(S.c.re, S.c.im, S.d.re, S.d.im);
+}
+__device__ __forceinline__ sl4<float> ld_sj2(const float* b, int x, int y) {
+  sl4<float> S = ld_sl4(b, pair_slot(x < y ? x : y, x < y ? y : x));
+  if (x > y) S = sl4<float>{-S.a, -S.b, -S.c, -S.d};
+  return S;
+}
 __device__ __forceinline__ int triple_slot(int x, int y, int z) {  // any order: J(zyx) = J(xyz)
   const int miss = 6 - x - y - z;
   const int a = miss == 0 ? 1 : 0, c = miss == 3 ? 2 : 3;
@@ -298,32 +316,43 @@ __global__ void __launch_bounds__(TC4_THREADS, 2) k_tree_tc4(const double* __res
       st_c4(cur, 22 + t, J);
     }
     __syncwarp();
+    // the quark lines only slash the 34 vectors against rows: convert them in place
+    for (int sl = lane; sl < 34; sl += 4) slash_in_place(cur, sl);
+    __syncwarp();
     // 5. quark line for the orderings starting with gluon w = lane
     const int w = lane;
     for (int ht = 0; ht < 2; ++ht) {
       const c4<float> ub = dbar(spinor_u_of(K.wt, ht ? 1 : -1));
       const int row0 = (wl & ~3) + 2 * ht;  // rows of (this event, ht, hv = 0 / 1)
-      const c4<float> U1 = row_prop(row_slash(ub, ld_c4(cur, w)), scaled_prop(kt + q[w], mt, -g * K.iq[1 << w]));
+      const c4<float> U1 = row_prop(row_slash(ub, ld_sl4(cur, w)), scaled_prop(kt + q[w], mt, -g * K.iq[1 << w]));
+      // every lane runs the same 3 x 2 iterations (no lane idles on a skipped index):
+      // x is the kx-th gluon other than w, y the ky-th other than w and x, in increasing
+      // order, so f counts the orderings w x y z as the ordering tables do
       int f = 6 * w;
-      for (int x = 0; x < 4; ++x) {
-        if (x == w) continue;
-        c4<float> r2 = row_slash(ub, ld_j2(cur, w, x));
-        row_slash_acc(r2, U1, ld_c4(cur, x));
+#pragma unroll
+      for (int kx = 0; kx < 3; ++kx) {
+        const int x = kx + (kx >= w ? 1 : 0);
+        c4<float> r2 = row_slash(ub, ld_sj2(cur, w, x));
+        row_slash_acc(r2, U1, ld_sl4(cur, x));
         const c4<float> U2 = row_prop(r2, scaled_prop(kt + q[w] + q[x], mt, -g * K.iq[(1 << w) | (1 << x)]));
-        for (int y = 0; y < 4; ++y) {
-          if (y == w || y == x) continue;
+        const int lo = w < x ? w : x, hi = w < x ? x : w;
+#pragma unroll
+        for (int ky = 0; ky < 2; ++ky) {
+          int y = ky;
+          if (y >= lo) ++y;
+          if (y >= hi) ++y;
           const int z = 6 - w - x - y;
-          c4<float> r3 = row_slash(ub, ld_c4(cur, triple_slot(w, x, y)));
-          row_slash_acc(r3, U1, ld_j2(cur, x, y));
-          row_slash_acc(r3, U2, ld_c4(cur, y));
+          c4<float> r3 = row_slash(ub, ld_sl4(cur, triple_slot(w, x, y)));
+          row_slash_acc(r3, U1, ld_sj2(cur, x, y));
+          row_slash_acc(r3, U2, ld_sl4(cur, y));
           const c4<float> U3 =
               row_prop(r3, scaled_prop(kt + q[w] + q[x] + q[y], mt, -g * K.iq[(1 << w) | (1 << x) | (1 << y)]));
           const int s4 = kJ4OfOrdering[f];
-          c4<float> R = row_slash(ub, ld_c4(cur, 22 + (s4 > 0 ? s4 : -s4) - 1));
+          c4<float> R = row_slash(ub, ld_sl4(cur, 22 + (s4 > 0 ? s4 : -s4) - 1));
           if (s4 < 0) R = cneg(R);
-          row_slash_acc(R, U1, ld_c4(cur, triple_slot(x, y, z)));
-          row_slash_acc(R, U2, ld_j2(cur, y, z));
-          row_slash_acc(R, U3, ld_c4(cur, z));
+          row_slash_acc(R, U1, ld_sl4(cur, triple_slot(x, y, z)));
+          row_slash_acc(R, U2, ld_sj2(cur, y, z));
+          row_slash_acc(R, U3, ld_sl4(cur, z));
 #pragma unroll
           for (int hv = 0; hv < 2; ++hv) {
             const cx<float> a = times_i(spdot(R, v[hv])) * g;
