@@ -59,15 +59,24 @@ __global__ void k_partials(const double* __restrict__ w, long n, double* __restr
   }
 }
 
+// One warp: lane l adds the partials l, l + 32, ... in order, then a fixed butterfly adds
+// the lanes.  The order is fixed, so the result is reproducible; a single thread adding
+// all partials in a dependent chain would take tens of microseconds of float64 latency.
 __global__ void k_finish(const double* __restrict__ part, int nblk, double* __restrict__ acc, long n,
                          const int* __restrict__ cnt) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
+  if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+  double a = 0.0, b = 0.0;
+  for (int i = (int)threadIdx.x; i < nblk; i += 32) {
+    a += part[2 * i];
+    b += part[2 * i + 1];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if (threadIdx.x == 0) {
     if (cnt) n = *cnt;
-    double a = 0.0, b = 0.0;
-    for (int i = 0; i < nblk; ++i) {
-      a += part[2 * i];
-      b += part[2 * i + 1];
-    }
     acc[0] += a;
     acc[1] += b;
     acc[2] += (double)n;
@@ -424,26 +433,20 @@ static int ensure_capacity(me_handle* h, size_t n) {
 // staged: device and managed memory as is; pinned (page-locked, mapped) host memory under
 // its device address -- on GB300 the kernels then read and write it over the coherent
 // CPU-GPU link while they compute, with no staging copy.  Pageable memory is staged.
-static void* device_view(const void* p) {
-  if (!p) return nullptr;
+struct PtrView {
+  void* dev;  // address the kernels use, or nullptr if the buffer has to be staged
+  bool host;  // host memory (pinned or pageable): results are in place when the call returns
+};
+static PtrView view_of(const void* p) {
+  if (!p) return {nullptr, false};
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
-    return nullptr;
+    return {nullptr, true};  // unregistered: pageable host memory
   }
-  if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) return const_cast<void*>(p);
-  if (at.type == cudaMemoryTypeHost && at.devicePointer) return at.devicePointer;
-  return nullptr;
-}
-
-static bool is_host_ptr(const void* p) {
-  if (!p) return false;
-  cudaPointerAttributes at;
-  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-    cudaGetLastError();
-    return true;  // unregistered: pageable host memory
-  }
-  return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
+  if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) return {const_cast<void*>(p), false};
+  if (at.type == cudaMemoryTypeHost) return {at.devicePointer, true};
+  return {nullptr, at.type == cudaMemoryTypeUnregistered};
 }
 
 static cudaError_t dispatch(int pid, int kind, bool fp64, int lpe, const LaunchArgs& a, cudaStream_t st) {
@@ -602,11 +605,12 @@ static int run(me_handle* h, int kind, double nlo_factor, const double* momenta,
   h->last_kind = K_TREE;
   if (n == 0) return ME_OK;
   const int next = h->proc->n_ext;
-  const double* vp = static_cast<const double*>(device_view(momenta));
-  const double* vw = wgt ? static_cast<const double*>(device_view(wgt)) : nullptr;
-  double* vo = static_cast<double*>(device_view(out));
+  const PtrView pv = view_of(momenta), wv = view_of(wgt), ov = view_of(out);
+  const double* vp = static_cast<const double*>(pv.dev);
+  const double* vw = static_cast<const double*>(wv.dev);
+  double* vo = static_cast<double*>(ov.dev);
   // host buffers (pinned or pageable): results are in place when the call returns
-  const bool on_host = is_host_ptr(momenta) || (wgt && is_host_ptr(wgt)) || is_host_ptr(out);
+  const bool on_host = pv.host || wv.host || ov.host;
   int rc = ensure_capacity(h, (size_t)n);
   if (rc != ME_OK) return rc;
   const double* P = vp;
