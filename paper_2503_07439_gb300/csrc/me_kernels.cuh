@@ -411,7 +411,11 @@ constexpr double CA_ = 3.0;
 struct IsrKin {
   double xi, y[2], S[2], K, K0;
   r4<double> soft[4];     // soft Born: beams, heavy pair at sqrt(s) along n*
-  r4<double> coll[2][4];  // collinear Born of sector j: beam j scaled by (1-xi)
+  // collinear Born of sector 1: beam 1 scaled by z = 1 - xi.  That of sector 2 (beam 2
+  // scaled) is the same 2 -> 2 configuration boosted along the beam axis, and everything
+  // evaluated there -- the unpolarised Born and the Born with a gluon polarised along the
+  // transverse direction (0, cos phi, sin phi, 0) -- is invariant under that boost.
+  r4<double> coll[4];
   double qdir[3];         // gluon direction
   double cphi, sphi;      // gluon azimuth
 };
@@ -452,15 +456,12 @@ __device__ __forceinline__ void isr_map(const r4<double>* k, double mass, IsrKin
   const double eQ = 0.5 * M, pQ = 0.5 * M * bQ;
   const r4<double> tr{eQ, pQ * n[0], pQ * n[1], pQ * n[2]};
   const r4<double> tbr{eQ, -pQ * n[0], -pQ * n[1], -pQ * n[2]};
-#pragma unroll
-  for (int j = 0; j < 2; ++j) {
-    o.coll[j][0] = j == 0 ? scale(z, k[0]) : k[0];
-    o.coll[j][1] = j == 1 ? scale(z, k[1]) : k[1];
-    const r4<double> Qc = o.coll[j][0] + o.coll[j][1];
-    const double Mc2 = mdot(Qc, Qc), iMc = rsqrt(Mc2);
-    o.coll[j][2] = boost_by(tr, Qc, iMc, Mc2 * iMc, 1.0);
-    o.coll[j][3] = boost_by(tbr, Qc, iMc, Mc2 * iMc, 1.0);
-  }
+  o.coll[0] = scale(z, k[0]);
+  o.coll[1] = k[1];
+  const r4<double> Qc = o.coll[0] + o.coll[1];
+  const double Mc2 = mdot(Qc, Qc), iMc = rsqrt(Mc2);
+  o.coll[2] = boost_by(tr, Qc, iMc, Mc2 * iMc, 1.0);
+  o.coll[3] = boost_by(tbr, Qc, iMc, Mc2 * iMc, 1.0);
   constexpr double i64pi3 = 1.0 / (64.0 * PI * PI * PI);
   o.K = s * bQ * i64pi3 / beta;
   o.K0 = s * i64pi3;
@@ -618,7 +619,7 @@ __device__ __forceinline__ RealSubOut real_sub_event(const double* __restrict__ 
         });
     }
     {
-      const Kin<BPID, T> KB = prepare<BPID, T>(f.coll[0], kp.cp);
+      const Kin<BPID, T> KB = prepare<BPID, T>(f.coll, kp.cp);
       for (int b = lane; b < n_live_blocks<BPID>(); b += LPE)
         amplitude_block<BPID, T>(KB, live_block_hel<BPID>(b), kp.cp,
                                  [&](int, const cx<T>* J) { aC += colour_sum<BPID, T>(kp.tab, J); });
@@ -627,13 +628,11 @@ __device__ __forceinline__ RealSubOut real_sub_event(const double* __restrict__ 
         if (lane == 0)
           amplitude_block<BPID, T>(
               KB, 2, kp.cp, [&](int, const cx<T>* J) { aP[0] += colour_sum<BPID, T>(kp.tab, J); }, &eperp, 0);
-      }
-    }
-    if constexpr (BPID == P_GG_TT) {
-      if (lane == 1 % LPE) {  // polarised gluon 1; gluon 0 fixed to +
-        const Kin<BPID, T> KB = prepare<BPID, T>(f.coll[1], kp.cp);
-        amplitude_block<BPID, T>(
-            KB, 1, kp.cp, [&](int, const cx<T>* J) { aP[1] += colour_sum<BPID, T>(kp.tab, J); }, &eperp, 1);
+        // polarised gluon 1, gluon 0 fixed to +: sector 2's spin-correlated Born, at the
+        // same kinematics (invariant under the boost that relates the two sectors)
+        if (lane == 1 % LPE)
+          amplitude_block<BPID, T>(
+              KB, 1, kp.cp, [&](int, const cx<T>* J) { aP[1] += colour_sum<BPID, T>(kp.tab, J); }, &eperp, 1);
       }
     }
     // every sum ran over one helicity of each flipped pair (|M(h)|^2 = |M(-h)|^2)
