@@ -75,10 +75,10 @@ int main() {
   for (int i = 0; i < 4; ++i) e.v[i] = cx<Flop>{Flop(0.5), Flop(0.0)};
   const double quad2 = 10.0;  // J^dagger E J for the 2x2 eikonal-weighted correlator matrix
   // subtracted real: real blocks + Born tasks (soft with the eikonal form, collinear,
-  // spin-correlated for g g)
+  // spin-correlated for g g: both polarised gluons at the one collinear kinematics)
   const double real_ee = born_ops<P_EE_UUG>(p) + 2 * born_ops<P_EE_UU>(p);
   const double real_gg = born_ops<P_GG_TTG>(p) + born_ops<P_GG_TT>(p) + 8 * quad2 + born_ops<P_GG_TT>(p) +
-                         block_ops<P_GG_TT>(p, 2, &e, 0) + prep_ops<P_GG_TT>(p) + block_ops<P_GG_TT>(p, 1, &e, 1);
+                         block_ops<P_GG_TT>(p, 2, &e, 0) + block_ops<P_GG_TT>(p, 1, &e, 1);
   const double real_uu = born_ops<P_UU_TTG>(p) + born_ops<P_UU_TT>(p) + 8 * quad2 + born_ops<P_UU_TT>(p);
   const double b[7] = {born_ops<P_EE_UU>(p),  born_ops<P_EE_UUG>(p), born_ops<P_GG_TT>(p), born_ops<P_GG_TTG>(p),
                        born_ops<P_GG_TTGG>(p), born_ops<P_UU_TT>(p), born_ops<P_UU_TTG>(p)};
