@@ -236,3 +236,22 @@ def test_kfactor_monte_carlo():
     pb = to_points(bb.p)
     np.testing.assert_allclose(nlo_ee.nbody_nlo(pb), me.me2("ee_uu", pb) * (1 + a_s * nlo_ee.nbody_coefficient(0.5, 1)),
                                rtol=1e-14)
+
+
+def test_isr_sector_collinear_borns_are_related_by_a_beam_boost():
+    """The collinear counter-kinematics of the two ISR sectors (beam 1 or beam 2 scaled by
+    1 - xi) differ by a boost along the beam axis: the unpolarised Born and the Born with
+    either gluon polarised along the transverse direction (0, cos phi, sin phi, 0) take the
+    same values at both.  The kernels rely on this to evaluate both sectors' collinear
+    pieces at one kinematics."""
+    rng = np.random.default_rng(9)
+    n = 30
+    k = _isr_points(n, rng.uniform(0.01, 0.85, n), rng.uniform(-1, 1, n), seed=9)
+    k1, k2 = fks.isr_map(k, 4, 0, 173.0), fks.isr_map(k, 4, 1, 173.0)
+    np.testing.assert_allclose(k1.e_perp, k2.e_perp, atol=0)
+    np.testing.assert_allclose(me.me2("gg_tt", k2.born_coll), me.me2("gg_tt", k1.born_coll), rtol=1e-12)
+    for leg in (0, 1):
+        np.testing.assert_allclose(me.spin_correlated("gg_tt", k2.born_coll, leg, k2.e_perp),
+                                   me.spin_correlated("gg_tt", k1.born_coll, leg, k1.e_perp), rtol=1e-12)
+    # not a property of any two kinematics: the soft Born (at sqrt(s)) differs
+    assert np.median(np.abs(me.me2("gg_tt", k1.born_soft) / me.me2("gg_tt", k1.born_coll) - 1)) > 1e-2
