@@ -147,7 +147,10 @@ int me_eval_nbody_nlo(me_handle* h, const double* momenta, const double* ps_weig
  *                                    - Th_s Th_c G(0,1)) / (xi^2 (1-y) K) ].
  * Defined for "ee_uug" (final-state sectors) and "gg_ttg", "uu_ttg" (initial-state
  * sectors).  In ME_PREC_MIXED, points failing the stability test are recomputed in
- * float64 before the call's results are complete.  Adds to the accumulators.
+ * float64 before the call's results are complete.  Points on the boundary of the FKS
+ * domain (xi = 0 or 1, or the emission exactly along a sector's reference direction)
+ * have measure zero and no defined subtracted weight: out[i] = 0 for them.  Adds to the
+ * accumulators.
  */
 int me_eval_real_subtracted(me_handle* h, const double* momenta, const double* ps_weights, int64_t n, double* out);
 

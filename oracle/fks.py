@@ -216,6 +216,7 @@ def real_subtracted(real: str, k: np.ndarray, fp: FKSParams = FKSParams(),
     # Algorithm 2: evaluate every term for every point, then mask
     R = me2(real, k, cp)
     total = np.zeros(k.shape[0])
+    inside = np.ones(k.shape[0], dtype=bool)
     parts = []
     for isec, (j, kind) in enumerate(partners):
         if kind == "fsr":
@@ -241,6 +242,12 @@ def real_subtracted(real: str, k: np.ndarray, fp: FKSParams = FKSParams(),
         th_c = (y > 1.0 - fp.delta).astype(float)
         W = (G - th_s * G_soft - th_c * G_coll + th_s * th_c * G_sc) / (xi * xi * (1.0 - y) * kin.K)
         total += W
+        with np.errstate(invalid="ignore"):
+            inside &= (xi > 0.0) & (xi < 1.0) & (1.0 - y > 0.0)
         parts.append(dict(xi=xi, y=y, G=G, G_soft=G_soft, G_coll=G_coll, G_sc=G_sc, W=W,
                           S=S[isec], K=kin.K, RS=R * S[isec]))
+    # the boundary of the FKS domain (xi = 0 or 1, or the emission exactly along a
+    # sector's reference direction) has measure zero, and the subtracted weight with its
+    # 1 / (xi^2 (1 - y)) is not defined there: such points carry weight 0
+    total = np.where(inside, total, 0.0)
     return (total, parts) if detail else total

@@ -543,12 +543,14 @@ __device__ __forceinline__ RealSubOut real_sub_event(const double* __restrict__ 
 
   double W = 0.0, mag = 0.0;
   double ysec[2] = {-1.0, -1.0};  // y_j of both sectors (collinear resolution of the flag)
+  double xi_pt = 0.0;             // the emission's energy fraction
   bool near = false;
   if constexpr (PID == P_EE_UUG) {
     FsrKin f;
     fsr_map(k, f);
     ysec[0] = f.y[0];
     ysec[1] = f.y[1];
+    xi_pt = f.xi;
     T aB[2] = {T(0), T(0)};
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
@@ -582,6 +584,7 @@ __device__ __forceinline__ RealSubOut real_sub_event(const double* __restrict__ 
     isr_map(k, kp.cp.mt, f);
     ysec[0] = f.y[0];
     ysec[1] = f.y[1];
+    xi_pt = f.xi;
     // eikonal-weighted colour-correlation matrix E = sum_{k,l} w_kl C^{kl} (2x2)
     const int ci = (BPID == P_GG_TT) ? 0 : 1;
     double E[4] = {0.0, 0.0, 0.0, 0.0};
@@ -672,6 +675,15 @@ __device__ __forceinline__ RealSubOut real_sub_event(const double* __restrict__ 
       mag += fabs(rsj) + fabs(th_c * Gc * iden[j]) + fabs(th_s * (Gs - th_c * Gsc) * iden[j]);
       near |= (th_s > 0.0 && xi < kp.xi_thr) || (th_c > 0.0 && 1.0 - f.y[j] < kp.y_thr);
     }
+  }
+  // A point on the boundary of the FKS domain -- no emitted energy (xi = 0), all of it
+  // (xi = 1), or the emission exactly along a sector's reference direction (y_j = 1) --
+  // has measure zero and no defined subtracted weight (1 / (xi^2 (1 - y)) diverges):
+  // weight 0, and it is not re-evaluated.  The comparisons are false for NaN.
+  if (!(xi_pt > 0.0 && xi_pt < 1.0 && 1.0 - ysec[0] > 0.0 && 1.0 - ysec[1] > 0.0)) {
+    W = 0.0;
+    mag = 0.0;
+    near = false;
   }
   return RealSubOut{W, mag, {ysec[0], ysec[1]}, near};
 }

@@ -267,3 +267,23 @@ def test_queued_rescue_equals_separate_launches(me, name, seed):
         aq, as_ = np.asarray(hq.accumulators()), np.asarray(hs.accumulators())
         assert aq[2] == as_[2] == n
         np.testing.assert_allclose(aq[:2], as_[:2], rtol=1e-6, atol=0)
+
+
+def test_domain_boundary_points(me):
+    """Points on the boundary of the FKS domain (no emitted energy, or the gluon exactly
+    along a beam) carry weight 0 in both precisions, as in the oracle; they are not
+    re-evaluated, and the accumulators stay finite."""
+    xi = np.array([0.3, 0.0, 0.3, 0.3])
+    cb = np.array([0.2, 0.2, 1.0, -1.0])
+    p = synth.emission_points(1000.0, 173.0, xi, cb, np.full(4, 0.4), np.full(4, 0.3), np.full(4, 1.1))
+    with np.errstate(all="ignore"):
+        ref = fks.real_subtracted("gg_ttg", to_points(p))
+    for prec in (me.ME_PREC_FP64, me.ME_PREC_MIXED):
+        h = me.Handle("gg_ttg", precision=prec)
+        got = h.real_subtracted(_dev(p)).cpu().numpy()
+        assert list(got[1:]) == [0.0, 0.0, 0.0]
+        assert abs(got[0] / ref[0] - 1) <= (1e-12 if prec == me.ME_PREC_FP64 else 1e-5)
+        acc = h.accumulators()
+        assert np.all(np.isfinite(acc)) and acc[2] == 4
+        if prec == me.ME_PREC_MIXED:
+            assert h.last_rescued() <= 1

@@ -255,3 +255,24 @@ def test_isr_sector_collinear_borns_are_related_by_a_beam_boost():
                                    me.spin_correlated("gg_tt", k1.born_coll, leg, k1.e_perp), rtol=1e-12)
     # not a property of any two kinematics: the soft Born (at sqrt(s)) differs
     assert np.median(np.abs(me.me2("gg_tt", k1.born_soft) / me.me2("gg_tt", k1.born_coll) - 1)) > 1e-2
+
+
+def _boundary_points():
+    """Four g g -> t tbar g points: an ordinary one, one with no emitted energy (xi = 0
+    exactly), and two with the gluon exactly along a beam (y = 1 in sector 1 or 2)."""
+    xi = np.array([0.3, 0.0, 0.3, 0.3])
+    cb = np.array([0.2, 0.2, 1.0, -1.0])
+    return synth.emission_points(1000.0, 173.0, xi, cb, np.full(4, 0.4), np.full(4, 0.3), np.full(4, 1.1))
+
+
+def test_domain_boundary_points_carry_zero_weight():
+    """Points on the boundary of the FKS domain have measure zero and no defined subtracted
+    weight: the oracle gives them weight 0, and the other points of the batch are
+    unaffected."""
+    p = _boundary_points()
+    with np.errstate(all="ignore"):
+        w = fks.real_subtracted("gg_ttg", to_points(p))
+        w0 = fks.real_subtracted("gg_ttg", to_points(p[:, :, :1]))
+    assert np.all(np.isfinite(w))
+    assert list(w[1:]) == [0.0, 0.0, 0.0]
+    assert w[0] == w0[0] and w[0] != 0.0
