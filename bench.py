@@ -109,7 +109,8 @@ class Clocks:
     sampling interval and none falls inside, the first sample after its start)."""
 
     def __init__(self, index: int):
-        self.path = tempfile.mktemp(suffix=".csv")
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
         self.index = index
         self.proc = None
         self.t0 = self.t1 = None
@@ -144,7 +145,13 @@ class Clocks:
         rows = []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         try:
-            for line in open(self.path):
+            with open(self.path) as fh:
+                lines = fh.readlines()
+            os.unlink(self.path)
+        except OSError:
+            lines = []
+        try:
+            for line in lines:
                 f = [x.strip() for x in line.split(",")]
                 if len(f) < 9:
                     continue
