@@ -52,6 +52,8 @@ TRAFFIC = {
                      "profile": "profiles/k_real_sub_gg_ttg_float_2p20.md"},
     ("c3", "main"): {"bytes": 0.052588e9 + 0.026265e9, "points": 1 << 18,
                      "profile": "profiles/k_tree_gg_ttgg_float_tc_2p18.md"},
+    ("c1", "main"): {"bytes": 0.142653e9 + 0.006809e9, "points": 1 << 20,
+                     "profile": "profiles/k_tree_gg_tt_float_2p20.md"},
 }
 
 
