@@ -35,7 +35,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import colour
-from .dirac import GAMMA, bar, dot, polarisation, slash, spinor_u, spinor_v
+from .dirac import GAMMA, bar, ctype, dot, polarisation, slash, spinor_u, spinor_v
 
 # ------------------------------------------------------------------ model
 FERMIONS = {
@@ -155,7 +155,7 @@ class Diagrams:
         rest = frozenset(range(self.n - 1))
         self.terms = list(self._currents(rest, (comp, rt[1])))
         self.root = root
-        self._ctensors = None
+        self._ctensors = {}
 
     # number of Feynman diagrams (the three four-gluon structures count once)
     @property
@@ -223,8 +223,8 @@ class Diagrams:
         return out
 
     # -------------------------------------------------------------- colour
-    def _colour_vertex(self, nd: Node) -> np.ndarray:
-        T = colour.T
+    def _colour_vertex(self, nd: Node, dtype) -> np.ndarray:
+        T, f, _ = colour.generators(dtype)
         proc = self.proc
         if nd.kind in ("ffv_row", "ffv_col", "ffv_vec"):
             flav = nd.ltype[1] if nd.kind != "ffv_vec" else nd.kids[0].ltype[1]
@@ -233,36 +233,35 @@ class Diagrams:
                 X = T  # [a, l, l']
             else:
                 d = 3 if qc else 1
-                X = np.eye(d, dtype=complex)[None]  # [0, l, l']
+                X = np.eye(d, dtype=dtype)[None]  # [0, l, l']
             if nd.kind == "ffv_row":      # out[l'] = R[l] X[a,l,l'] V[a]
                 return np.transpose(X, (1, 0, 2))       # [l, a, l']
             if nd.kind == "ffv_col":      # out[l] = X[a,l,l'] V[a] C[l']
                 return np.transpose(X, (0, 2, 1))       # [a, l', l]
             return np.transpose(X, (1, 2, 0))           # [l, l', a]
         if nd.kind == "vvv":
-            return colour.F.astype(complex)             # [a, b, c]
+            return f.astype(dtype)                      # [a, b, c]
         if nd.kind == "vvvv":
-            f = colour.F
             if nd.chan == 0:
                 X = np.einsum("abe,cde->abcd", f, f)
             elif nd.chan == 1:
                 X = np.einsum("ace,bde->abcd", f, f)
             else:
                 X = np.einsum("ade,bce->abcd", f, f)
-            return X.astype(complex)
+            return X.astype(dtype)
         raise ValueError(nd.kind)
 
-    def _colour(self, nd: Node, memo: dict):
+    def _colour(self, nd: Node, memo: dict, dtype=complex):
         """Colour tensor of a current: axes (line, *legs in increasing order)."""
         if id(nd) in memo:
             return memo[id(nd)]
         if nd.kind == "ext":
             d = self.proc.colour_dim(nd.leg)
-            t = np.eye(d, dtype=complex)
+            t = np.eye(d, dtype=dtype)
             memo[id(nd)] = t
             return t
-        kids = [self._colour(k, memo) for k in nd.kids]
-        X = self._colour_vertex(nd)
+        kids = [self._colour(k, memo, dtype) for k in nd.kids]
+        X = self._colour_vertex(nd, dtype)
         letters = iter("ABCDEFGH")
         kid_lines = [next(letters) for _ in kids]
         new_line = "Z"
@@ -277,39 +276,41 @@ class Diagrams:
         memo[id(nd)] = t
         return t
 
-    def colour_tensors(self) -> np.ndarray:
-        """(n_terms, prod of leg colour dims): full colour tensor of every term."""
-        if self._ctensors is None:
+    def colour_tensors(self, dtype=complex) -> np.ndarray:
+        """(n_terms, prod of leg colour dims): full colour tensor of every term, in the
+        given complex type (complex128, or that of np.longdouble)."""
+        key = np.dtype(dtype)
+        if key not in self._ctensors:
             memo = {}
             rows = []
             for t in self.terms:
-                c = self._colour(t, memo)  # axes: line(=root leg), legs 0..n-2
+                c = self._colour(t, memo, key)  # axes: line(=root leg), legs 0..n-2
                 c = np.moveaxis(c, 0, -1)  # root leg is the last leg
                 rows.append(c.reshape(-1))
-            self._ctensors = np.array(rows)
-        return self._ctensors
+            self._ctensors[key] = np.array(rows)
+        return self._ctensors[key]
 
     def colour_shape(self):
         return tuple(self.proc.colour_dim(i) for i in range(self.n))
 
-    def gram(self) -> np.ndarray:
-        C = self.colour_tensors()
+    def gram(self, dtype=complex) -> np.ndarray:
+        C = self.colour_tensors(dtype)
         return C.conj() @ C.T
 
-    def charge_on_leg(self, leg: int) -> np.ndarray:
+    def charge_on_leg(self, leg: int, dtype=complex) -> np.ndarray:
         """(8, n_terms, D): T_leg^a applied to every term's colour tensor."""
         kind = self.proc.colour_kind(leg)
-        M = colour.charge_matrices(kind)
-        C = self.colour_tensors().reshape((-1,) + self.colour_shape())
+        M = colour.charge_matrices(kind, dtype)
+        C = self.colour_tensors(dtype).reshape((-1,) + self.colour_shape())
         Cm = np.moveaxis(C, leg + 1, -1)              # (t, ..., d)
         res = np.einsum("aij,t...j->at...i", M, Cm)   # (a, t, ..., d)
         res = np.moveaxis(res, -1, leg + 2)
         return res.reshape(8, C.shape[0], -1)
 
-    def gram_correlated(self, k: int, l: int) -> np.ndarray:
+    def gram_correlated(self, k: int, l: int, dtype=complex) -> np.ndarray:
         """G^{kl}_{t t'} = sum_a sum_colours conj(T_k^a c_t) (T_l^a c_t')."""
-        Tk = self.charge_on_leg(k)
-        Tl = Tk if k == l else self.charge_on_leg(l)
+        Tk = self.charge_on_leg(k, dtype)
+        Tl = Tk if k == l else self.charge_on_leg(l, dtype)
         return np.einsum("atd,asd->ts", Tk.conj(), Tl)
 
     # -------------------------------------------------------------- kinematics
@@ -323,7 +324,7 @@ class Diagrams:
         wfs = []
         for i in range(self.n):
             if override and i in override:
-                w = np.asarray(override[i], dtype=complex)[:, None, :]
+                w = np.asarray(override[i], dtype=ctype(p))[:, None, :]
                 wfs.append(np.broadcast_to(w, (p.shape[0], hel.shape[0], 4)))
                 continue
             kind, flav, anti = PARTICLES[proc.legs[i]]
@@ -424,7 +425,7 @@ class Diagrams:
 
         root_wf = wfs[self.root]
         rt = proc.line_type(self.root)[0]
-        out = np.empty((N, hel.shape[0], len(self.terms)), dtype=complex)
+        out = np.empty((N, hel.shape[0], len(self.terms)), dtype=ctype(p))
         for it, t in enumerate(self.terms):
             X = ev(t, amputate=True)
             if rt == "row":      # root ubar / vbar on the left of a column current

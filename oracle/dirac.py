@@ -13,7 +13,10 @@ Conventions (standard QFT, e.g. Peskin & Schroeder; the paper fixes none):
     chi_+ = (0,1), chi_- = (-1,0) are used;
   * polarisation vectors eps(k,l) = (-l e1 - i e2)/sqrt(2) with
     e1 = (0, cos(th)cos(ph), cos(th)sin(ph), -sin(th)), e2 = (0, -sin(ph), cos(ph), 0).
-All arrays broadcast over leading (point) axes.
+All arrays broadcast over leading (point) axes.  The working precision follows the
+momenta: float64 momenta give float64/complex128 results (the oracle proper);
+np.longdouble momenta carry every step in extended precision, which the tests use to
+arbitrate between two float64 evaluations that differ.
 """
 from __future__ import annotations
 
@@ -41,6 +44,11 @@ GAMMA = np.stack([
 GAMMA5 = 1j * GAMMA[0] @ GAMMA[1] @ GAMMA[2] @ GAMMA[3]
 
 
+def ctype(x) -> np.dtype:
+    """Complex dtype of the precision of array x (complex128 for float64 input)."""
+    return np.result_type(np.asarray(x).dtype, np.complex64)
+
+
 def dot(a, b):
     """Minkowski product a.b over the last axis (works for complex arrays, no conjugation)."""
     return a[..., 0] * b[..., 0] - a[..., 1] * b[..., 1] - a[..., 2] * b[..., 2] - a[..., 3] * b[..., 3]
@@ -63,7 +71,7 @@ def _chi(p, lam):
     s = pa + pz
     ok = s > 0.0  # p exactly along -z: explicit limits below
     den = np.sqrt(np.where(ok, 2.0 * pa * s, 1.0))
-    out = np.zeros(p.shape[:-1] + (2,), dtype=complex)
+    out = np.zeros(p.shape[:-1] + (2,), dtype=ctype(p))
     if lam > 0:
         out[..., 0] = np.where(ok, s / den, 0.0)
         out[..., 1] = np.where(ok, (px + 1j * py) / den, 1.0)
@@ -124,4 +132,4 @@ def polarisation(k, lam):
     zero = np.zeros_like(ka)
     e1 = np.stack([zero, ct * cp, ct * sp, -st], axis=-1)
     e2 = np.stack([zero, -sp, cp, zero], axis=-1)
-    return (-lam * e1 - 1j * e2) / np.sqrt(2.0)
+    return (-lam * e1 - 1j * e2) / np.sqrt(ka.dtype.type(2))

@@ -127,7 +127,7 @@ def fsr_map(k: np.ndarray, i_fks: int, j: int, other: int) -> SectorKinematics:
     e_perp = np.zeros_like(k[:, 0])
     e_perp[:, 1:] = ni - y[:, None] * nj
     e_perp[:, 1:] = _unit(e_perp[:, 1:])
-    q = np.concatenate([np.ones((k.shape[0], 1)), ni], axis=1)
+    q = np.concatenate([np.ones((k.shape[0], 1), dtype=k.dtype), ni], axis=1)
     return SectorKinematics(xi, y, phi, born, born, q, K, K0, K1, e_perp)
 
 
@@ -156,7 +156,7 @@ def isr_map(k: np.ndarray, i_fks: int, j: int, mass: float) -> SectorKinematics:
     Qc = coll[:, 0] + coll[:, 1]
     M = np.sqrt(s * (1.0 - xi))
     betaQ = np.sqrt(np.maximum(0.0, 1.0 - 4.0 * mass * mass / (s * (1.0 - xi))))
-    t_rest = np.zeros((N, 4))
+    t_rest = np.zeros((N, 4), dtype=k.dtype)
     t_rest[:, 0] = 0.5 * M
     t_rest[:, 1:] = 0.5 * (M * betaQ)[:, None] * nstar
     tb_rest = t_rest.copy()
@@ -166,10 +166,10 @@ def isr_map(k: np.ndarray, i_fks: int, j: int, mass: float) -> SectorKinematics:
     coll[:, 3] = _boost(tb_rest, bc)
     K = s * betaQ / (64.0 * math.pi ** 3 * beta)
     K0 = s / (64.0 * math.pi ** 3) * np.ones_like(xi)
-    e_perp = np.zeros((N, 4))
+    e_perp = np.zeros((N, 4), dtype=k.dtype)
     e_perp[:, 1] = np.cos(phi)
     e_perp[:, 2] = np.sin(phi)
-    q = np.concatenate([np.ones((N, 1)), ni], axis=1)
+    q = np.concatenate([np.ones((N, 1), dtype=k.dtype), ni], axis=1)
     return SectorKinematics(xi, y, phi, soft, coll, q, K, K0, K.copy(), e_perp)
 
 
@@ -177,7 +177,7 @@ def soft_limit(born: str, pb: np.ndarray, q: np.ndarray, s: np.ndarray, cp: Coup
     """lim xi^2 R = -(4 g^2/s) sum_{k,l} (pb_k.pb_l)/((pb_k.q)(pb_l.q)) B_kl."""
     g2 = 4.0 * math.pi * cp.alpha_s
     Bkl = colour_correlated(born, pb, cp)
-    tot = np.zeros(pb.shape[0])
+    tot = np.zeros(pb.shape[0], dtype=pb.dtype)
     for (a, b), v in Bkl.items():
         tot += dot(pb[:, a], pb[:, b]) / (dot(pb[:, a], q) * dot(pb[:, b], q)) * v
     return -(4.0 * g2 / s) * tot
@@ -215,7 +215,7 @@ def real_subtracted(real: str, k: np.ndarray, fp: FKSParams = FKSParams(),
     S = sector_functions(k, i_fks, partners)
     # Algorithm 2: evaluate every term for every point, then mask
     R = me2(real, k, cp)
-    total = np.zeros(k.shape[0])
+    total = np.zeros(k.shape[0], dtype=k.dtype)
     inside = np.ones(k.shape[0], dtype=bool)
     parts = []
     for isec, (j, kind) in enumerate(partners):

@@ -19,6 +19,7 @@ from dataclasses import dataclass
 import numpy as np
 
 from .diagrams import Diagrams, Process, helicities
+from .dirac import ctype
 
 MT = 173.0
 _QCD_T = frozenset({("t", "g"), "ggg", "gggg"})
@@ -58,11 +59,13 @@ def diagrams(name: str) -> Diagrams:
 _GRAM_CACHE: dict = {}
 
 
-def gram(name: str, k: int | None = None, l: int | None = None) -> np.ndarray:
-    key = (name, k, l)
+def gram(name: str, k: int | None = None, l: int | None = None, dtype=complex) -> np.ndarray:
+    """Colour Gram matrix (or colour-correlated one for legs k, l) in the given complex
+    type: complex128 for the oracle proper, that of np.longdouble for extended precision."""
+    key = (name, k, l, np.dtype(dtype))
     if key not in _GRAM_CACHE:
         d = diagrams(name)
-        _GRAM_CACHE[key] = d.gram() if k is None else d.gram_correlated(k, l)
+        _GRAM_CACHE[key] = d.gram(dtype) if k is None else d.gram_correlated(k, l, dtype)
     return _GRAM_CACHE[key]
 
 
@@ -88,8 +91,8 @@ def me2(name: str, p: np.ndarray, cp: Couplings = Couplings(), grams=None,
     """
     d = diagrams(name)
     hel = helicities(d.n, fixed_hel)
-    G_list = [gram(name)] if grams is None else grams
-    out = np.zeros((len(G_list), p.shape[0]))
+    G_list = [gram(name, dtype=ctype(p))] if grams is None else grams
+    out = np.zeros((len(G_list), p.shape[0]), dtype=p.dtype)
     avg = d.proc.average()
     for sl in _chunks(p.shape[0], name):
         ov = None if override is None else {k: v[sl] for k, v in override.items()}
@@ -109,7 +112,7 @@ def colour_correlated(name: str, p: np.ndarray, cp: Couplings = Couplings()):
     """B_kl for all ordered pairs of coloured legs: dict {(k,l): (N,)}."""
     legs = coloured_legs(name)
     pairs = [(k, l) for k in legs for l in legs]
-    G = [gram(name, k, l) for k, l in pairs]
+    G = [gram(name, k, l, dtype=ctype(p)) for k, l in pairs]
     vals = me2(name, p, cp, grams=G)
     return {pr: vals[i] for i, pr in enumerate(pairs)}
 
