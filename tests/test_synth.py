@@ -32,6 +32,26 @@ def test_philox_matches_integer_restatement():
             assert [int(x) for x in out[:, i]] == ref
 
 
+# Known-answer vectors published with the generator's reference implementation
+# (Salmon et al., SC'11; Random123 distribution): (counter c0..c3, key k0 k1) -> output.
+PHILOX_KAT = [
+    ((0x00000000, 0x00000000, 0x00000000, 0x00000000), (0x00000000, 0x00000000),
+     (0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8)),
+    ((0xFFFFFFFF, 0xFFFFFFFF, 0xFFFFFFFF, 0xFFFFFFFF), (0xFFFFFFFF, 0xFFFFFFFF),
+     (0x408F276D, 0x41C83B0E, 0xA20BC7C6, 0x6D5451FD)),
+    ((0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344), (0xA4093822, 0x299F31D0),
+     (0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1)),
+]
+
+
+def test_philox_known_answer_vectors():
+    """The generator reproduces the published known answers: a misreading of the round
+    function, the multipliers, the Weyl constants or the word order fails here."""
+    for ctr, key, expect in PHILOX_KAT:
+        out = synth.philox4x32_10(np.array(ctr, dtype=np.uint32).reshape(4, 1), key)
+        assert [int(x) for x in out[:, 0]] == list(expect), [hex(int(x)) for x in out[:, 0]]
+
+
 def test_uniforms_open_interval_and_moments():
     u = synth.uniforms(7, 3, 200000, 4)
     assert np.all(u > 0) and np.all(u < 1)
