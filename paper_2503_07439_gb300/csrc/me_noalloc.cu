@@ -60,14 +60,30 @@ int setup(int dev, DeviceSlot** out) {
   return ME_OK;
 }
 
-bool on_device(const void* p) {
+// A buffer is usable when it is device memory of `dev` or managed memory; device memory
+// of another GPU is refused (without peer access the kernel could not read it).
+bool on_device(const void* p, int dev) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  return me_internal_buffer_usable((int)at.type, at.device, dev) != 0;
 }
+
+// The caller's current device is put back on every return path.
+struct CurrentDeviceGuard {
+  int prev = -1;
+  CurrentDeviceGuard() {
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+      cudaGetLastError();
+      prev = -1;
+    }
+  }
+  ~CurrentDeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
 
 cudaError_t launch(int pid, int kind, bool fp64, int lpe, const me::LaunchArgs& a, cudaStream_t st) {
   switch (pid) {
@@ -79,6 +95,15 @@ cudaError_t launch(int pid, int kind, bool fp64, int lpe, const me::LaunchArgs& 
 }
 
 }  // namespace
+
+// Pure argument rule of on_device(), exported (not part of me.h) so that the rule can be
+// checked without a second GPU: cudaMemoryTypeDevice (2) memory must belong to
+// `want_device`; cudaMemoryTypeManaged (3) memory is reachable from every device; host
+// and unregistered memory are refused.
+extern "C" int me_internal_buffer_usable(int mem_type, int mem_device, int want_device) {
+  if (mem_type == (int)cudaMemoryTypeManaged) return 1;
+  return mem_type == (int)cudaMemoryTypeDevice && mem_device == want_device;
+}
 
 extern "C" int me_eval_real_subtracted_noalloc(const char* process, const me_params* params, const double* momenta,
                                                const double* ps_weights, int64_t n, double* out, void* cuda_stream) {
@@ -94,13 +119,17 @@ extern "C" int me_eval_real_subtracted_noalloc(const char* process, const me_par
   const int lpe = params->lanes_per_event ? params->lanes_per_event : 4;
   if (lpe != 1 && lpe != 2 && lpe != 4 && lpe != 8 && lpe != 16)
     return me_internal_fail(ME_ERR_ARG, "me_eval_real_subtracted_noalloc: lanes_per_event");
+  CurrentDeviceGuard keep_current;
   if (cudaSetDevice(params->device) != cudaSuccess)
     return me_internal_fail(ME_ERR_CUDA, "me_eval_real_subtracted_noalloc: cudaSetDevice failed");
   DeviceSlot* slot = nullptr;
   if ((rc = setup(params->device, &slot)) != ME_OK) return rc;
   if (n == 0) return ME_OK;
-  if (!momenta || !out || !on_device(momenta) || !on_device(out) || (ps_weights && !on_device(ps_weights)))
-    return me_internal_fail(ME_ERR_ARG, "me_eval_real_subtracted_noalloc: buffers must be device memory");
+  const int dev = params->device;
+  if (!momenta || !out || !on_device(momenta, dev) || !on_device(out, dev) ||
+      (ps_weights && !on_device(ps_weights, dev)))
+    return me_internal_fail(ME_ERR_ARG, "me_eval_real_subtracted_noalloc: buffers must be device memory of "
+                                        "params->device (or managed memory)");
   cudaStream_t st = (cudaStream_t)cuda_stream;
   kp.tab = slot->tables;
   int* count = slot->scratch + kCountSlot;

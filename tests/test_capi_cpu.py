@@ -42,3 +42,18 @@ def test_binding_has_no_cpu_fallback():
     """The package exposes only the ctypes binding: no numpy/torch compute path."""
     src = open(os.path.join(ROOT, "paper_2503_07439_gb300", "_capi.py")).read()
     assert "oracle" not in src and "synth" not in src
+
+
+def test_noalloc_buffer_rule_refuses_other_devices(lib):
+    """The allocation-free entry point accepts device memory of the requested GPU and
+    managed memory, and refuses device memory of another GPU (no peer access is set up,
+    so its kernels could not read it) and host memory.  The rule is checked here through
+    its exported helper, so that no second GPU is needed."""
+    f = lib.me_internal_buffer_usable
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    unregistered, host, device, managed = 0, 1, 2, 3  # cudaMemoryType
+    assert f(device, 0, 0) == 1 and f(device, 3, 3) == 1
+    assert f(device, 1, 0) == 0 and f(device, 0, 1) == 0
+    assert f(managed, 0, 1) == 1
+    assert f(host, 0, 0) == 0 and f(unregistered, 0, 0) == 0
