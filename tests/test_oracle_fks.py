@@ -218,7 +218,9 @@ def test_integrated_counterterms_by_quadrature(xc, dl):
             tot += v
     X = 2 * tot * 2 * math.pi * 8 * math.pi ** 2  # both sectors, units of a_s sigma_LO
     c = nlo_ee.nbody_coefficient(xc, dl)
-    assert abs(X + c - 1.5) < 1e-5
+    # the adaptive quadrature reaches 3e-9 for three of the choices and 3e-7 for
+    # (0.1, 0.5), where the cut-offs put kinks close to the integrable singularities
+    assert abs(X + c - 1.5) < 1e-6
 
 
 def test_kfactor_monte_carlo():
@@ -230,7 +232,8 @@ def test_kfactor_monte_carlo():
     b = synth.flat_points("ee_uug", 32768, 2)
     w = fks.real_subtracted("ee_uug", to_points(b.p)) * b.wgt / (2 * s)
     ratio = 1 + a_s * nlo_ee.nbody_coefficient(0.5, 1.0) + w.mean() / sig_lo
-    assert abs(ratio - (1 + CP.alpha_s / math.pi)) < 4e-3
+    err = w.std() / math.sqrt(w.size) / sig_lo
+    assert abs(ratio - (1 + CP.alpha_s / math.pi)) < 4 * err + 1e-4, (ratio, err)
     # n-body weights from the oracle agree with B (1 + a_s c)
     bb = synth.flat_points("ee_uu", 64, 1)
     pb = to_points(bb.p)
