@@ -47,9 +47,11 @@ extern "C" {
 #define ME_ERR_CUDA (-5)     /* a CUDA call failed; see me_last_error() */
 #define ME_ERR_BUSY (-6)     /* request rejected: queue full or over the memory budget */
 
-#define ME_PARAMS_VERSION 2u
+#define ME_PARAMS_VERSION 3u
 #define ME_PREC_FP64 0   /* every amplitude in float64 */
 #define ME_PREC_MIXED 1  /* float32 amplitudes; float64 FKS maps, combination and rescue */
+#define ME_RESCUE_POINTS 0 /* mixed precision: every flagged point re-evaluated whole in float64 */
+#define ME_RESCUE_ITEMS 1  /* mixed precision: the flagged points' float64 items (see me_params) */
 
 /*
  * Run parameters.  Start from me_default_params(); `version` must equal
@@ -70,9 +72,11 @@ extern "C" {
  *                    margin) and points on soft/collinear approach sequences within tol
  *   device           CUDA device ordinal the handle runs on
  *   lanes_per_event  lanes sharing one point (1, 2, 4, 8 or 16; at most 8 for
- *                    "gg_ttgg"; 0 = autotune: each candidate is timed on the
- *                    handle's first call of each kind and precision).  The queued
- *                    mixed-precision subtracted real always runs one lane per point.
+ *                    "gg_ttgg"; 0 = autotune: each candidate is timed once per device,
+ *                    process, kind, precision and batch-size class floor(log2 n)
+ *                    (capped at 15), on the first call that meets it, and the choice is
+ *                    shared by every handle).  The queued mixed-precision subtracted real
+ *                    always runs one lane per point.
  *   queued_rescue    mixed-precision subtracted real: 0 (default) = a float32 launch
  *                    that lists the unstable points, then a float64 launch over the
  *                    list; 1 = one launch in which each block queues its unstable
@@ -81,6 +85,17 @@ extern "C" {
  *                    work.  Both give the same results to float64 rounding; on GB300
  *                    the two launches are faster (the float64 unit needs several
  *                    warps per scheduler to stay busy).
+ *   rescue           mixed-precision subtracted real with two launches (queued_rescue 0):
+ *                    ME_RESCUE_ITEMS (default) re-evaluates, per flagged point, only the
+ *                    ingredients whose float32 error the point cannot absorb.  The
+ *                    subtracted weight is linear in its matrix-element ingredients --
+ *                    the real's helicity blocks and the counterterms' Born values -- with
+ *                    float64 coefficients from the FKS maps; a flagged point takes its
+ *                    ingredients in float64, largest error scale first, until the
+ *                    float32 error left is within tol |W| / 4, and W is recombined in
+ *                    float64.  Points inside xi_thr / y_thr take every ingredient in
+ *                    float64.  ME_RESCUE_POINTS re-evaluates every flagged point whole in
+ *                    float64.  me_last_rescued counts the flagged points either way.
  */
 typedef struct me_params {
   uint32_t version;
@@ -97,13 +112,14 @@ typedef struct me_params {
   int32_t device;
   int32_t lanes_per_event;
   int32_t queued_rescue;
+  int32_t rescue;
 } me_params;
 
 typedef struct me_handle me_handle;
 
 /* Fill `p` with the defaults: FP64, alpha = 1/132.507, alpha_s = 0.118, mt = 173,
  * xi_cut = 0.5, delta = 1, xi_thr = 1e-3, y_thr = 1e-3, tol = 1e-5, me_eps = 4e-7,
- * device 0, lanes_per_event 0, queued_rescue 0.  Never fails. */
+ * device 0, lanes_per_event 0, queued_rescue 0, rescue ME_RESCUE_ITEMS.  Never fails. */
 void me_default_params(me_params* p);
 
 /*
@@ -158,6 +174,13 @@ int me_eval_real_subtracted(me_handle* h, const double* momenta, const double* p
  * (synchronises the handle's stream). */
 int me_last_rescued(me_handle* h, int64_t* n_rescued);
 
+/* Float64 work of the last me_eval_real_subtracted call in mixed precision with the item
+ * rescue: the flagged points, the real-emission helicity blocks and the sets of
+ * counterterm Born values re-evaluated in float64 (with ME_RESCUE_POINTS or the queued
+ * kernel only the points are counted; the other two are 0).  Synchronises the handle's
+ * stream. */
+int me_last_rescue_work(me_handle* h, int64_t* points, int64_t* real_blocks, int64_t* born_sets);
+
 /* Monte-Carlo accumulators of all outputs since creation or the last set:
  * out[0] = sum w, out[1] = sum w^2, out[2] = number of points (as double).
  * Synchronises the handle's stream.  me_set_accumulators restores them (resume). */
@@ -191,6 +214,26 @@ int me_synchronize(me_handle* h);
  * ME_ERR_ARG for host pointers, n < 0 or sqrt_s not above the final-state masses. */
 int me_generate_flat(me_handle* h, uint64_t seed, uint32_t stream, int64_t first_point, double sqrt_s, int64_t n,
                      double* momenta, double* ps_weights);
+
+/* Phase-space points of a real-emission process ("ee_uug", "gg_ttg", "uu_ttg") generated
+ * on the device directly in the variables of its FKS sectors (Sec. 4.2: each sector has
+ * its own kinematic parametrisation), with a density that samples the soft and collinear
+ * regions the subtraction has to handle: the emitted gluon's energy fraction xi flat
+ * (flat three-body phase space has density ~ xi there), its cosine y_j w.r.t. the
+ * sector's reference direction as y_j = 1 - 2 v^2 with v uniform (density
+ * 1 / (4 sqrt((1 - y_j)/2))), azimuth and Born direction uniform; the two sectors are
+ * channels of one multichannel density, and each weight is the phase-space measure over
+ * the summed density.  Uniforms u0..u5 of point i: Philox4x32-10 blocks 0..2 at counter
+ * (i lo, i hi, stream, block), key (seed lo, seed hi), mapped as in me_generate_flat.
+ *   initial-state sectors (gg_ttg, uu_ttg): xi = (1 - 4 mt^2/s) u0, y_j = 1 - 2 u1^2 w.r.t.
+ *     beam j (j = 0 along +z if u5 < 1/2, else the -z beam), phi = 2 pi u2, the heavy
+ *     pair's rest-frame direction (cos 2 u3 - 1, azimuth 2 pi u4);
+ *   final-state sectors (ee_uug): partner leg 2 if u0 < 1/2 else leg 3, its direction
+ *     (cos 2 u1 - 1, azimuth 2 pi u2), xi = u3, y_j = 1 - 2 u4^2, phi = 2 pi u5 about it.
+ * Layout, beams, device buffers and errors as for me_generate_flat; ME_ERR_PROCESS for a
+ * process without FKS sectors.  Enqueued on the handle's stream. */
+int me_generate_fks(me_handle* h, uint64_t seed, uint32_t stream, int64_t first_point, double sqrt_s, int64_t n,
+                    double* momenta, double* ps_weights);
 
 /*
  * Unweighted events from weighted points: the accept/reject step that turns a sample

@@ -16,7 +16,9 @@ ME_ERR_CUDA = -5
 ME_ERR_BUSY = -6
 ME_PREC_FP64 = 0
 ME_PREC_MIXED = 1
-ME_PARAMS_VERSION = 2
+ME_PARAMS_VERSION = 3
+ME_RESCUE_POINTS = 0
+ME_RESCUE_ITEMS = 1
 ME_KIND_BORN = 0
 ME_KIND_REAL_SUBTRACTED = 1
 ME_KIND_NBODY_NLO = 2
@@ -38,7 +40,8 @@ class MEParams(ctypes.Structure):
                 ("alpha_s", ctypes.c_double), ("mt", ctypes.c_double), ("xi_cut", ctypes.c_double),
                 ("delta", ctypes.c_double), ("xi_thr", ctypes.c_double), ("y_thr", ctypes.c_double),
                 ("tol", ctypes.c_double), ("me_eps", ctypes.c_double), ("device", ctypes.c_int32),
-                ("lanes_per_event", ctypes.c_int32), ("queued_rescue", ctypes.c_int32)]
+                ("lanes_per_event", ctypes.c_int32), ("queued_rescue", ctypes.c_int32),
+                ("rescue", ctypes.c_int32)]
 
 
 class MEServerParams(ctypes.Structure):
@@ -79,6 +82,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "me_eval_nbody_nlo": (ctypes.c_int, [vp, vp, vp, i64, vp]),
         "me_eval_real_subtracted": (ctypes.c_int, [vp, vp, vp, i64, vp]),
         "me_last_rescued": (ctypes.c_int, [vp, ctypes.POINTER(i64)]),
+        "me_last_rescue_work": (ctypes.c_int, [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]),
         "me_get_accumulators": (ctypes.c_int, [vp, dp]),
         "me_set_accumulators": (ctypes.c_int, [vp, dp]),
         "me_set_stream": (ctypes.c_int, [vp, vp]),
@@ -94,6 +98,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "me_server_destroy": (None, [vp]),
         "me_server_stats": (ctypes.c_int, [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
         "me_generate_flat": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.c_uint32, i64, ctypes.c_double, i64, vp, vp]),
+        "me_generate_fks": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.c_uint32, i64, ctypes.c_double, i64, vp, vp]),
         "me_unweight": (ctypes.c_int, [vp, vp, i64, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint32, i64, vp, vp,
                                        ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_int64)]),
@@ -194,20 +199,28 @@ class Handle:
     def real_subtracted(self, p, w=None, out=None):
         return self._call(self.lib.me_eval_real_subtracted, p, w, out)
 
-    def generate_flat(self, n: int, seed: int, sqrt_s: float, first_point: int = 0, stream: int = 0, out=None):
-        """Flat phase-space points of this process generated on the device (torch tensors
-        momenta [4][n_ext][n] and weights [n] on the handle's device, or `out` = (p, w))."""
+    def _generate(self, fn, n, seed, sqrt_s, first_point, stream, out):
         import torch
         if out is None:
             p = torch.empty((4, self.n_ext, n), dtype=torch.float64, device=f"cuda:{self.params.device}")
             w = torch.empty(n, dtype=torch.float64, device=p.device)
         else:
             p, w = out
-        _check(self.lib.me_generate_flat(self.h, seed, stream, first_point, float(sqrt_s), n,
-                                         ctypes.c_void_p(p.data_ptr()), ctypes.c_void_p(w.data_ptr())))
+        _check(fn(self.h, seed, stream, first_point, float(sqrt_s), n, ctypes.c_void_p(p.data_ptr()),
+                  ctypes.c_void_p(w.data_ptr())))
         if self.sync:
             _check(self.lib.me_synchronize(self.h))
         return p, w
+
+    def generate_flat(self, n: int, seed: int, sqrt_s: float, first_point: int = 0, stream: int = 0, out=None):
+        """Flat phase-space points of this process generated on the device (torch tensors
+        momenta [4][n_ext][n] and weights [n] on the handle's device, or `out` = (p, w))."""
+        return self._generate(self.lib.me_generate_flat, n, seed, sqrt_s, first_point, stream, out)
+
+    def generate_fks(self, n: int, seed: int, sqrt_s: float, first_point: int = 0, stream: int = 0, out=None):
+        """Real-emission points generated on the device in FKS-sector variables (soft and
+        collinear regions sampled more densely; multichannel weights), as generate_flat."""
+        return self._generate(self.lib.me_generate_fks, n, seed, sqrt_s, first_point, stream, out)
 
     def unweight(self, w, w_max: float = 0.0, seed: int = 0, stream: int = 1, first_point: int = 0):
         """Unweighted events from the device weights `w` (torch float64 CUDA tensor):
@@ -228,6 +241,13 @@ class Handle:
         v = ctypes.c_int64()
         _check(self.lib.me_last_rescued(self.h, ctypes.byref(v)))
         return v.value
+
+    def last_rescue_work(self) -> tuple[int, int, int]:
+        """(flagged points, real blocks, Born-value sets) re-evaluated in float64 by the
+        last subtracted-real call (item rescue)."""
+        v = [ctypes.c_int64() for _ in range(3)]
+        _check(self.lib.me_last_rescue_work(self.h, *(ctypes.byref(x) for x in v)))
+        return tuple(x.value for x in v)
 
     def accumulators(self):
         a = (ctypes.c_double * 3)()

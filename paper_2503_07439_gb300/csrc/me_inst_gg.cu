@@ -6,4 +6,5 @@ cudaError_t launch_gg(int pid, int kind, bool fp64, int lpe, const LaunchArgs& a
   if (pid == P_GG_TTG) { ME_PREC_SWITCH(P_GG_TTG) }
   return cudaErrorInvalidValue;
 }
+cudaError_t launch_items_gg(const LaunchArgs& a, cudaStream_t st) { return launch_items_one<P_GG_TTG>(a, st); }
 }  // namespace me

@@ -21,6 +21,8 @@ int me_internal_launch_counted(me_handle* h, int me_kind, const double* d_p, con
 int me_internal_final_masses(me_handle* h, double* masses, int* n_out, cudaStream_t* stream);
 // Process id (index into the library's process table) of a name, or -1.
 int me_internal_process_id(const char* name);
+// Process id of a handle, or -1 for NULL.
+int me_internal_handle_process(const me_handle* h);
 // Record the thread-local message returned by me_last_error(); returns `code`.
 int me_internal_fail(int code, const char* msg);
 

@@ -12,6 +12,7 @@
 // of the heavy pair, evaluated with shared gluon currents and quark-line rows.  Born, real, soft and collinear terms are evaluated for every point and
 // masked afterwards (Sec. 4.3, Algorithm 2), so a warp never diverges on cuts.
 #pragma once
+#include <algorithm>
 #include <atomic>
 
 #include "me_procs.cuh"
@@ -53,6 +54,8 @@ struct KParams {
   double me_eps;        // assumed relative error of a bulk-precision matrix element
   double tol;           // target relative accuracy of a weight
   int flag_unstable;    // 1: append unstable points to the rescue list
+  int item_rescue;      // with flag_unstable: records and float64 items instead of the point list
+  double item_budget;   // item rescue: residual error allowed, as a fraction of tol |W|
   const ColourTables* tab;
 };
 
@@ -522,6 +525,22 @@ __device__ __forceinline__ double eik(const r4<double>& a, const r4<double>& b, 
 //   W_j = R S_j - [Th_s G(0,y) + Th_c G(xi,1) - Th_s Th_c G(0,1)] / (xi^2 (1-y) K),
 // with the error scale of the stability test.  The LPE lanes of a group evaluate one
 // point together and all return the same result.
+//
+// W is linear in its matrix-element ingredients -- the real's helicity blocks R_b
+// (R = sum_b R_b) and the Born values of the counterterms (for initial-state sectors:
+// the eikonal-weighted soft Born E, the soft Born B_s, the collinear Born B_c and, for
+// g g, the two spin-correlated Borns B_p; for final-state sectors the Born B_j of each
+// sector) -- with float64 coefficients fixed by the FKS maps:  W = sum_i a_i v_i.  The
+// item rescue re-evaluates in float64 only the ingredients whose float32 error the
+// point's tolerance cannot absorb, and recombines W from the coefficients.
+template <int PID>
+struct RealLayout {
+  static constexpr int NB = n_live_blocks<PID>();                                   // real's blocks
+  static constexpr int NBV = PID == P_EE_UUG ? 2 : (PID == P_GG_TTG ? 5 : 3);      // Born values
+  static constexpr int NI = NB + NBV;
+};
+constexpr int MAX_ITEMS = 9;
+
 struct RealSubOut {
   double W;     // subtracted real, summed over sectors
   double mag;   // error scale: |R S| + |CT_coll| + |CT_soft - CT_softcoll| per sector
@@ -529,55 +548,160 @@ struct RealSubOut {
   bool near;    // inside xi_thr / y_thr of an active counterterm
 };
 
+// Ingredients and coefficients of one point for the item rescue (group lane 0).
+struct RealItems {
+  double a[MAX_ITEMS];  // W = sum_i a_i v_i
+  double v[MAX_ITEMS];  // bulk-precision values: R blocks, then the Born values
+  double born_scale;    // error scale of the Born values together (as in RealSubOut::mag)
+};
+
+// Born values of the initial-state counterterms: v[0] = E (eikonal-weighted soft Born,
+// multiplies -4 g^2 / s in the soft limit), v[1] = B_s (soft Born), v[2] = B_c
+// (collinear Born), v[3], v[4] = B_p (spin-correlated Borns, g g only); every sum ran
+// over one helicity of each flipped pair (|M(h)|^2 = |M(-h)|^2), hence bav.
+template <int PID, typename T, int LPE>
+__device__ __forceinline__ void isr_born_values(const IsrKin& f, const KParams& kp, int lane, unsigned mask,
+                                                double* v) {
+  constexpr int BPID = PID == P_GG_TTG ? P_GG_TT : P_UU_TT;
+  // eikonal-weighted colour-correlation matrix E = sum_{k,l} w_kl C^{kl} (2x2)
+  const int ci = (BPID == P_GG_TT) ? 0 : 1;
+  double E[4] = {0.0, 0.0, 0.0, 0.0};
+  {
+    // w_ab = (p_a.p_b) / ((p_a.q)(p_b.q)), q = (1, gluon direction): four reciprocals
+    const r4<double> qq{1.0, f.qdir[0], f.qdir[1], f.qdir[2]};
+    double iaq[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) iaq[a] = 1.0 / mdot(f.soft[a], qq);
+    int pr = 0;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = a; b < 4; ++b, ++pr) {
+        const double w = mdot(f.soft[a], f.soft[b]) * iaq[a] * iaq[b] * (a == b ? 1.0 : 2.0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) E[q] += w * kp.tab->Ccorr[ci][pr][q];
+      }
+  }
+  const T Et[4] = {(T)E[0], (T)E[1], (T)E[2], (T)E[3]};
+  c4<T> eperp;
+  eperp.v[0] = cx<T>{T(0), T(0)};
+  eperp.v[1] = cx<T>{(T)f.cphi, T(0)};
+  eperp.v[2] = cx<T>{(T)f.sphi, T(0)};
+  eperp.v[3] = cx<T>{T(0), T(0)};
+  // Born tasks: soft Born (eikonal-weighted correlators and plain), collinear Born,
+  // and for g g the spin-correlated Born of each beam (the polarised gluon's bit unused)
+  T aE = T(0), aS = T(0), aC = T(0), aP[2] = {T(0), T(0)};
+  {
+    const Kin<BPID, T> KB = prepare<BPID, T>(f.soft, kp.cp);
+    for (int b = lane; b < n_live_blocks<BPID>(); b += LPE)
+      amplitude_block<BPID, T>(KB, live_block_hel<BPID>(b), kp.cp, [&](int, const cx<T>* J) {
+        aE += quad2(Et, J);
+        aS += colour_sum<BPID, T>(kp.tab, J);
+      });
+  }
+  {
+    const Kin<BPID, T> KB = prepare<BPID, T>(f.coll, kp.cp);
+    for (int b = lane; b < n_live_blocks<BPID>(); b += LPE)
+      amplitude_block<BPID, T>(KB, live_block_hel<BPID>(b), kp.cp,
+                               [&](int, const cx<T>* J) { aC += colour_sum<BPID, T>(kp.tab, J); });
+    if constexpr (BPID == P_GG_TT) {
+      // polarised gluon 0; gluon 1 fixed to +, the heavy pair free (the flip covers the rest)
+      if (lane == 0)
+        amplitude_block<BPID, T>(
+            KB, 2, kp.cp, [&](int, const cx<T>* J) { aP[0] += colour_sum<BPID, T>(kp.tab, J); }, &eperp, 0);
+      // polarised gluon 1, gluon 0 fixed to +: sector 2's spin-correlated Born, at the
+      // same kinematics (invariant under the boost that relates the two sectors)
+      if (lane == 1 % LPE)
+        amplitude_block<BPID, T>(
+            KB, 1, kp.cp, [&](int, const cx<T>* J) { aP[1] += colour_sum<BPID, T>(kp.tab, J); }, &eperp, 1);
+    }
+  }
+  const double bav = 2.0 * kp.born_avg_inv;
+  v[0] = (double)group_sum<LPE>(aE, mask) * bav;
+  v[1] = (double)group_sum<LPE>(aS, mask) * bav;
+  v[2] = (double)group_sum<LPE>(aC, mask) * bav;
+  if constexpr (BPID == P_GG_TT) {
+    v[3] = (double)group_sum<LPE>(aP[0], mask) * bav;
+    v[4] = (double)group_sum<LPE>(aP[1], mask) * bav;
+  }
+}
+
+// Born values of the final-state counterterms: v[j] = the Born at sector j's kinematics.
+template <typename T, int LPE>
+__device__ __forceinline__ void fsr_born_values(const FsrKin& f, const KParams& kp, int lane, unsigned mask,
+                                                double* v) {
+  T aB[2] = {T(0), T(0)};
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const Kin<P_EE_UU, T> KB = prepare<P_EE_UU, T>(f.born[j], kp.cp);
+    for (int b = lane; b < n_live_blocks<P_EE_UU>(); b += LPE)
+      amplitude_block<P_EE_UU, T>(KB, live_block_hel<P_EE_UU>(b), kp.cp,
+                                  [&](int, const cx<T>* J) { aB[j] += colour_sum<P_EE_UU, T>(kp.tab, J); });
+  }
+  v[0] = 2.0 * (double)group_sum<LPE>(aB[0], mask) * kp.born_avg_inv;
+  v[1] = 2.0 * (double)group_sum<LPE>(aB[1], mask) * kp.born_avg_inv;
+}
+
+// One helicity block b of the real matrix element, colour-summed and averaged:
+// R = sum over the live blocks.
+template <int PID, typename T>
+__device__ __forceinline__ double real_block_value(const Kin<PID, T>& K, int b, const KParams& kp) {
+  T acc = T(0);
+  amplitude_block<PID, T>(K, live_block_hel<PID>(b), kp.cp, [&](int, const cx<T>* J) { acc += colour_sum<PID, T>(kp.tab, J); });
+  return 2.0 * (double)acc * kp.avg_inv;
+}
+
+// `items` (optional): filled with the coefficients and ingredient values on group lane 0
+// (every lane of the group must pass it or none).
 template <int PID, typename T, int LPE>
 __device__ __forceinline__ RealSubOut real_sub_event(const double* __restrict__ p, long n, long ev, const KParams& kp,
-                                                     int lane, unsigned mask) {
+                                                     int lane, unsigned mask, RealItems* items = nullptr) {
   constexpr int NEXT = Proc<PID>::NEXT;
-  constexpr int BPID = (PID == P_EE_UUG) ? P_EE_UU : (PID == P_GG_TTG ? P_GG_TT : P_UU_TT);
+  constexpr int NB = RealLayout<PID>::NB;
+  constexpr int NBL = (NB + LPE - 1) / LPE;  // real blocks per lane
   r4<double> k[NEXT];
   load_event<NEXT>(p, n, ev, k);
   const double rs = k[0].e + k[1].e, s = rs * rs;
   const double g2 = kp.cp.gs * kp.cp.gs;
 
-  // real matrix element
-  T accR = T(0);
+  // real matrix element; lane l holds blocks l, l + LPE, ... (one copy of the block code:
+  // the loop is not unrolled)
+  double blk[NBL];
+  double mine = 0.0;
   {
     const Kin<PID, T> K = prepare<PID, T>(k, kp.cp);
-    for (int b = lane; b < n_live_blocks<PID>(); b += LPE)
-      amplitude_block<PID, T>(K, live_block_hel<PID>(b), kp.cp,
-                              [&](int, const cx<T>* J) { accR += colour_sum<PID, T>(kp.tab, J); });
+#pragma unroll 1
+    for (int i = 0; i < NBL; ++i) {
+      const int b = lane + i * LPE;
+      const double v = b < NB ? real_block_value<PID, T>(K, b, kp) : 0.0;
+      blk[i] = v;
+      mine += v;
+    }
   }
-  const double R = 2.0 * (double)group_sum<LPE>(accR, mask) * kp.avg_inv;
+  const double R = group_sum<LPE>(mine, mask);
 
   double W = 0.0, mag = 0.0;
   double ysec[2] = {-1.0, -1.0};  // y_j of both sectors (collinear resolution of the flag)
   double xi_pt = 0.0;             // the emission's energy fraction
   bool near = false;
+  double a_R = 0.0, ab[RealLayout<PID>::NBV] = {};  // coefficients of R and of the Born values
+  double bv[RealLayout<PID>::NBV];
   if constexpr (PID == P_EE_UUG) {
     FsrKin f;
     fsr_map(k, f);
     ysec[0] = f.y[0];
     ysec[1] = f.y[1];
     xi_pt = f.xi;
-    T aB[2] = {T(0), T(0)};
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const Kin<BPID, T> KB = prepare<BPID, T>(f.born[j], kp.cp);
-      for (int b = lane; b < n_live_blocks<BPID>(); b += LPE)
-        amplitude_block<BPID, T>(KB, live_block_hel<BPID>(b), kp.cp,
-                                 [&](int, const cx<T>* J) { aB[j] += colour_sum<BPID, T>(kp.tab, J); });
-    }
-    double B[2];
-    B[0] = 2.0 * (double)group_sum<LPE>(aB[0], mask) * kp.born_avg_inv;
-    B[1] = 2.0 * (double)group_sum<LPE>(aB[1], mask) * kp.born_avg_inv;
+    fsr_born_values<T, LPE>(f, kp, lane, mask, bv);
+    const double* B = bv;
     const double th_s = f.xi < kp.xi_cut ? 1.0 : 0.0;
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
       // soft: sum_{kl} w_kl B_kl with B_23 = B_32 = -C_F B (massless diagonal terms vanish)
-      const double x2R = -(4.0 * g2 / s) * 2.0 * eik(f.born[j][2], f.born[j][3], f.qdir) * (-CF_ * B[j]);
-      const double Gs = (1.0 - f.y[j]) * 0.5 * (1.0 + f.y[j]) * f.K0 * x2R;
-      const double Gc = f.K1 * (2.0 / (s * (1.0 - f.xi))) * 2.0 * g2 * CF_ * (1.0 + (1.0 - f.xi) * (1.0 - f.xi)) * B[j];
-      const double Gsc = f.K0 * (2.0 / s) * 2.0 * g2 * 2.0 * CF_ * B[j];
+      const double cs = (1.0 - f.y[j]) * 0.5 * (1.0 + f.y[j]) * f.K0 * (-(4.0 * g2 / s) * 2.0 * eik(f.born[j][2], f.born[j][3], f.qdir) * (-CF_));
+      const double cc = f.K1 * (2.0 / (s * (1.0 - f.xi))) * 2.0 * g2 * CF_ * (1.0 + (1.0 - f.xi) * (1.0 - f.xi));
+      const double csc = f.K0 * (2.0 / s) * 2.0 * g2 * 2.0 * CF_;
+      const double Gs = cs * B[j], Gc = cc * B[j], Gsc = csc * B[j];
       const double th_c = f.y[j] > 1.0 - kp.delta ? 1.0 : 0.0;
       const double iden = 1.0 / (f.xi * f.xi * (1.0 - f.y[j]) * f.K[j]);
       const double ct = (th_s * Gs + th_c * Gc - th_s * th_c * Gsc) * iden;
@@ -586,93 +710,36 @@ __device__ __forceinline__ RealSubOut real_sub_event(const double* __restrict__ 
       // error scale: the real, the collinear term, and the soft pair (whose Borns are shared)
       mag += fabs(rsj) + fabs(th_c * Gc * iden) + fabs(th_s * (Gs - th_c * Gsc) * iden);
       near |= (th_s > 0.0 && f.xi < kp.xi_thr) || (th_c > 0.0 && 1.0 - f.y[j] < kp.y_thr);
+      a_R += f.S[j];
+      ab[j] = -(th_s * cs + th_c * cc - th_s * th_c * csc) * iden;
     }
   } else {
+    constexpr int BPID = PID == P_GG_TTG ? P_GG_TT : P_UU_TT;
     IsrKin f;
     isr_map(k, kp.cp.mt, f);
     ysec[0] = f.y[0];
     ysec[1] = f.y[1];
     xi_pt = f.xi;
-    // eikonal-weighted colour-correlation matrix E = sum_{k,l} w_kl C^{kl} (2x2)
-    const int ci = (BPID == P_GG_TT) ? 0 : 1;
-    double E[4] = {0.0, 0.0, 0.0, 0.0};
-    {
-      // w_ab = (p_a.p_b) / ((p_a.q)(p_b.q)), q = (1, gluon direction): four reciprocals
-      const r4<double> qq{1.0, f.qdir[0], f.qdir[1], f.qdir[2]};
-      double iaq[4];
-#pragma unroll
-      for (int a = 0; a < 4; ++a) iaq[a] = 1.0 / mdot(f.soft[a], qq);
-      int pr = 0;
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = a; b < 4; ++b, ++pr) {
-          const double w = mdot(f.soft[a], f.soft[b]) * iaq[a] * iaq[b] * (a == b ? 1.0 : 2.0);
-#pragma unroll
-          for (int q = 0; q < 4; ++q) E[q] += w * kp.tab->Ccorr[ci][pr][q];
-        }
-    }
-    const T Et[4] = {(T)E[0], (T)E[1], (T)E[2], (T)E[3]};
-    c4<T> eperp;
-    eperp.v[0] = cx<T>{T(0), T(0)};
-    eperp.v[1] = cx<T>{(T)f.cphi, T(0)};
-    eperp.v[2] = cx<T>{(T)f.sphi, T(0)};
-    eperp.v[3] = cx<T>{T(0), T(0)};
-    // Born tasks: soft Born (eikonal-weighted correlators and plain), collinear Born,
-    // and for g g the spin-correlated Born of each beam (the polarised gluon's bit unused)
-    T aE = T(0), aS = T(0), aC = T(0), aP[2] = {T(0), T(0)};
-    {
-      const Kin<BPID, T> KB = prepare<BPID, T>(f.soft, kp.cp);
-      for (int b = lane; b < n_live_blocks<BPID>(); b += LPE)
-        amplitude_block<BPID, T>(KB, live_block_hel<BPID>(b), kp.cp, [&](int, const cx<T>* J) {
-          aE += quad2(Et, J);
-          aS += colour_sum<BPID, T>(kp.tab, J);
-        });
-    }
-    {
-      const Kin<BPID, T> KB = prepare<BPID, T>(f.coll, kp.cp);
-      for (int b = lane; b < n_live_blocks<BPID>(); b += LPE)
-        amplitude_block<BPID, T>(KB, live_block_hel<BPID>(b), kp.cp,
-                                 [&](int, const cx<T>* J) { aC += colour_sum<BPID, T>(kp.tab, J); });
-      if constexpr (BPID == P_GG_TT) {
-        // polarised gluon 0; gluon 1 fixed to +, the heavy pair free (the flip covers the rest)
-        if (lane == 0)
-          amplitude_block<BPID, T>(
-              KB, 2, kp.cp, [&](int, const cx<T>* J) { aP[0] += colour_sum<BPID, T>(kp.tab, J); }, &eperp, 0);
-        // polarised gluon 1, gluon 0 fixed to +: sector 2's spin-correlated Born, at the
-        // same kinematics (invariant under the boost that relates the two sectors)
-        if (lane == 1 % LPE)
-          amplitude_block<BPID, T>(
-              KB, 1, kp.cp, [&](int, const cx<T>* J) { aP[1] += colour_sum<BPID, T>(kp.tab, J); }, &eperp, 1);
-      }
-    }
-    // every sum ran over one helicity of each flipped pair (|M(h)|^2 = |M(-h)|^2)
-    const double bav = 2.0 * kp.born_avg_inv;
-    const double x2R = -(4.0 * g2 / s) * (double)group_sum<LPE>(aE, mask) * bav;
-    const double Bs = (double)group_sum<LPE>(aS, mask) * bav;
-    const double Bc = (double)group_sum<LPE>(aC, mask) * bav;
-    double Bp[2] = {0.0, 0.0};
-    if constexpr (BPID == P_GG_TT) {
-      Bp[0] = (double)group_sum<LPE>(aP[0], mask) * bav;
-      Bp[1] = (double)group_sum<LPE>(aP[1], mask) * bav;
-    }
+    isr_born_values<PID, T, LPE>(f, kp, lane, mask, bv);
+    const double x2R = -(4.0 * g2 / s) * bv[0];
+    const double Bs = bv[1], Bc = bv[2];
+    const double Bp[2] = {BPID == P_GG_TT ? bv[3 % RealLayout<PID>::NBV] : 0.0,
+                          BPID == P_GG_TT ? bv[4 % RealLayout<PID>::NBV] : 0.0};
     const double xi = f.xi, z = 1.0 - xi, iz = 1.0 / z, is2 = 2.0 / s;
     const double th_s = xi < kp.xi_cut ? 1.0 : 0.0;
     // 1 / (xi^2 (1 - y_j) K) of both sectors from one reciprocal
     const double den0 = xi * xi * (1.0 - f.y[0]) * f.K, den1 = xi * xi * (1.0 - f.y[1]) * f.K;
     const double rden = 1.0 / (den0 * den1);
     const double iden[2] = {den1 * rden, den0 * rden};
+    // d xi P / d B_c, d xi P / d B_p, d xi P_0 / d B_s of the splitting kernels
+    const double kc = BPID == P_GG_TT ? 2.0 * CA_ * (z + xi * xi * z) : CF_ * (1.0 + z * z);
+    const double kp_ = BPID == P_GG_TT ? 2.0 * CA_ * 2.0 * (xi * xi * iz) : 0.0;
+    const double ks = BPID == P_GG_TT ? 2.0 * CA_ : 2.0 * CF_;
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
       const double Gs = (1.0 - f.y[j]) * f.S[j] * f.K0 * x2R;
-      double xiP, xiP0;
-      if constexpr (BPID == P_GG_TT) {
-        xiP = 2.0 * CA_ * ((z + xi * xi * z) * Bc + 2.0 * (xi * xi * iz) * Bp[j]);
-        xiP0 = 2.0 * CA_ * Bs;
-      } else {
-        xiP = CF_ * (1.0 + z * z) * Bc;
-        xiP0 = 2.0 * CF_ * Bs;
-      }
+      const double xiP = kc * Bc + kp_ * Bp[j];
+      const double xiP0 = ks * Bs;
       const double Gc = f.K * is2 * iz * 2.0 * g2 * xiP;
       const double Gsc = f.K0 * is2 * 2.0 * g2 * xiP0;
       const double th_c = f.y[j] > 1.0 - kp.delta ? 1.0 : 0.0;
@@ -682,6 +749,12 @@ __device__ __forceinline__ RealSubOut real_sub_event(const double* __restrict__ 
       // error scale: the real, the collinear term, and the soft pair (whose Borns are shared)
       mag += fabs(rsj) + fabs(th_c * Gc * iden[j]) + fabs(th_s * (Gs - th_c * Gsc) * iden[j]);
       near |= (th_s > 0.0 && xi < kp.xi_thr) || (th_c > 0.0 && 1.0 - f.y[j] < kp.y_thr);
+      a_R += f.S[j];
+      const double gcj = th_c * f.K * is2 * iz * 2.0 * g2 * iden[j];
+      ab[0] -= th_s * (1.0 - f.y[j]) * f.S[j] * f.K0 * (-(4.0 * g2 / s)) * iden[j];
+      ab[1] += th_s * th_c * f.K0 * is2 * 2.0 * g2 * ks * iden[j];
+      ab[2] -= gcj * kc;
+      if constexpr (BPID == P_GG_TT) ab[3 + j] = -gcj * kp_;
     }
   }
   // A point on the boundary of the FKS domain -- no emitted energy (xi = 0), all of it
@@ -693,38 +766,205 @@ __device__ __forceinline__ RealSubOut real_sub_event(const double* __restrict__ 
     mag = 0.0;
     near = false;
   }
+  if (items) {
+    // every block value to lane 0 (block b lives on lane b % LPE, slot b / LPE)
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      double x = 0.0;
+#pragma unroll
+      for (int i = 0; i < NBL; ++i)
+        if (i == b / LPE) x = blk[i];
+      if constexpr (LPE > 1) x = __shfl_sync(mask, x, b % LPE, LPE);
+      items->v[b] = x;
+      items->a[b] = a_R;
+    }
+#pragma unroll
+    for (int t = 0; t < RealLayout<PID>::NBV; ++t) {
+      items->v[NB + t] = bv[t];
+      items->a[NB + t] = ab[t];
+    }
+    items->born_scale = mag - fabs(R) * a_R;
+  }
   return RealSubOut{W, mag, {ysec[0], ysec[1]}, near};
 }
 
 // Stability test of a bulk-precision result: the error of W is ~ me_eps x (error
 // scale); the float32 amplitude error per unit scale grows towards the collinear limit,
 // as 1 + sqrt(rho_0 / rho) with rho = min_j (1 - y_j), rho_0 = 0.01.
-__device__ __forceinline__ bool unstable_point(const RealSubOut& r, const KParams& kp) {
+__device__ __forceinline__ double error_growth(const RealSubOut& r) {
   const float rho = fmaxf((float)fmin(1.0 - r.y[0], 1.0 - r.y[1]), 1e-30f);
-  const double grow = 1.0 + (double)sqrtf(0.01f / rho);
-  return r.near || !(r.mag * grow * kp.me_eps <= kp.tol * fabs(r.W));
+  return 1.0 + (double)sqrtf(0.01f / rho);
 }
+__device__ __forceinline__ bool unstable_point(const RealSubOut& r, const KParams& kp) {
+  return r.near || !(r.mag * error_growth(r) * kp.me_eps <= kp.tol * fabs(r.W));
+}
+
+// Items of a flagged point to re-evaluate in float64: bit b < NB for the real's block
+// b, bit NB for the Born values together.  Largest error scale first, until the scale
+// of the items left in float32, times the bulk-precision error per unit scale, is
+// within kp.item_budget x tol |W|.  Points inside the thresholds take every item.
+template <int PID>
+__device__ __forceinline__ unsigned rescue_mask(const RealSubOut& r, const RealItems& it, const KParams& kp) {
+  constexpr int NB = RealLayout<PID>::NB;
+  constexpr unsigned all = (1u << (NB + 1)) - 1u;
+  if (r.near) return all;
+  double e[NB + 1];
+  double rest = 0.0;
+#pragma unroll
+  for (int b = 0; b < NB; ++b) rest += (e[b] = fabs(it.a[b] * it.v[b]));
+  rest += (e[NB] = fabs(it.born_scale));
+  const double budget = kp.item_budget * kp.tol * fabs(r.W) / (error_growth(r) * kp.me_eps);
+  unsigned m = 0;
+#pragma unroll
+  for (int k = 0; k <= NB; ++k) {
+    if (!(rest > budget)) break;  // NaN or over budget: keep going
+    int pick = -1;
+    double best = -1.0;
+#pragma unroll
+    for (int b = 0; b <= NB; ++b)
+      if (!(m >> b & 1u) && e[b] > best) {
+        best = e[b];
+        pick = b;
+      }
+    if (pick < 0) break;
+    m |= 1u << pick;
+    rest -= best;
+  }
+  return m ? m : all;
+}
+
+// Buffers of the item rescue (structure of arrays, capacity `cap` points):
+// ev[slot], mask[slot], a[i * cap + slot], v[i * cap + slot]; the item lists hold
+// slot * 4 + b (real blocks) and slot (Born values); count[0] = flagged points,
+// count[2] = real-block items, count[3] = Born items (count[1] is the queued kernel's
+// tile counter).
+struct ItemBufs {
+  int* ev;
+  int* mask;
+  double* a;
+  double* v;
+  int* list_r;
+  int* list_b;
+  long cap;
+};
 
 // out[i] = wgt[i] * W(p_i).  In the bulk precision with kp.flag_unstable set, the
 // points failing the stability test are appended to resc_list; the float64 launch over
-// that list (idx, count) re-evaluates them.
+// that list (idx, count) re-evaluates them.  With kp.item_rescue set as well, each
+// flagged point gets a record (coefficients, bulk-precision values, item mask) and its
+// float64 items are appended to the item lists instead (warp-aggregated appends).
 template <int PID, typename T, int LPE>
 __global__ void __launch_bounds__(128, ME_MINB) k_real_sub(const double* __restrict__ p, const double* __restrict__ wgt,
                                                   long n, double* __restrict__ out, KParams kp,
                                                   const int* __restrict__ idx, const int* __restrict__ count,
-                                                  int* __restrict__ resc_list, int* __restrict__ resc_count) {
+                                                  int* __restrict__ resc_list, int* __restrict__ resc_count,
+                                                  ItemBufs ib) {
+  constexpr int NB = RealLayout<PID>::NB, NI = RealLayout<PID>::NI;
   const long gid = ((long)blockIdx.x * blockDim.x + threadIdx.x) / LPE;
   const int lane = threadIdx.x % LPE;
   const long nev = count ? (long)*count : n;
   if (gid >= nev) return;
   const long ev = idx ? (long)idx[gid] : gid;
-  const RealSubOut r = real_sub_event<PID, T, LPE>(p, n, ev, kp, lane, group_mask<LPE>());
+  RealItems it;
+  const bool want = kp.flag_unstable && kp.item_rescue;
+  const RealSubOut r = real_sub_event<PID, T, LPE>(p, n, ev, kp, lane, group_mask<LPE>(), want ? &it : nullptr);
   if (lane == 0) {
     out[ev] = (wgt ? wgt[ev] : 1.0) * r.W;
     if (kp.flag_unstable && unstable_point(r, kp)) {
-      const int slot = atomicAdd(resc_count, 1);
-      resc_list[slot] = (int)ev;
+      if (!kp.item_rescue) {
+        const int slot = atomicAdd(resc_count, 1);
+        resc_list[slot] = (int)ev;
+      } else {
+        const unsigned m = rescue_mask<PID>(r, it, kp);
+        // warp-aggregated appends over the flagged group leaders of this warp
+        const unsigned am = __activemask();
+        const int wl = threadIdx.x & 31, leader = __ffs(am) - 1;
+        const unsigned lt = (1u << wl) - 1u;
+        int base = 0;
+        if (wl == leader) base = atomicAdd(resc_count, __popc(am));
+        const int slot = __shfl_sync(am, base, leader) + __popc(am & lt);
+        ib.ev[slot] = (int)ev;
+        ib.mask[slot] = (int)m;
+#pragma unroll
+        for (int i = 0; i < NI; ++i) {
+          ib.a[i * ib.cap + slot] = it.a[i];
+          ib.v[i * ib.cap + slot] = it.v[i];
+        }
+        // real-block items, ordered by block then lane within the warp
+        unsigned bal[NB];
+        int tot = 0;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) tot += __popc(bal[b] = __ballot_sync(am, m >> b & 1u));
+        int rbase = 0;
+        if (wl == leader) rbase = atomicAdd(resc_count + 2, tot);
+        rbase = __shfl_sync(am, rbase, leader);
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+          if (m >> b & 1u) ib.list_r[rbase + __popc(bal[b] & lt)] = slot * 4 + b;
+          rbase += __popc(bal[b]);
+        }
+        const unsigned bb = __ballot_sync(am, m >> NB & 1u);
+        int bbase = 0;
+        if (wl == leader) bbase = atomicAdd(resc_count + 3, __popc(bb));
+        bbase = __shfl_sync(am, bbase, leader);
+        if (m >> NB & 1u) ib.list_b[bbase + __popc(bb & lt)] = slot;
+      }
     }
+  }
+}
+
+// Float64 evaluation of the rescue items (grid-stride over the item lists, counts read
+// on the device): blockIdx.y = 0 takes real blocks, 1 takes the Born values.  Every
+// item writes its value into its point's record.
+template <int PID>
+__global__ void __launch_bounds__(128, ME_MINB) k_rescue_items(const double* __restrict__ p, long n, KParams kp,
+                                                               const int* __restrict__ counts, ItemBufs ib) {
+  constexpr int NEXT = Proc<PID>::NEXT, NB = RealLayout<PID>::NB;
+  const long stride = (long)gridDim.x * blockDim.x;
+  if (blockIdx.y == 0) {
+    const long nit = counts[2];
+    for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < nit; t += stride) {
+      const int item = ib.list_r[t], slot = item >> 2, b = item & 3;
+      r4<double> k[NEXT];
+      load_event<NEXT>(p, n, ib.ev[slot], k);
+      const Kin<PID, double> K = prepare<PID, double>(k, kp.cp);
+      ib.v[b * ib.cap + slot] = real_block_value<PID, double>(K, b, kp);
+    }
+  } else {
+    const long nit = counts[3];
+    const unsigned self = 1u << (threadIdx.x & 31u);
+    for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < nit; t += stride) {
+      const int slot = ib.list_b[t];
+      r4<double> k[NEXT];
+      load_event<NEXT>(p, n, ib.ev[slot], k);
+      double bv[RealLayout<PID>::NBV];
+      if constexpr (PID == P_EE_UUG) {
+        FsrKin f;
+        fsr_map(k, f);
+        fsr_born_values<double, 1>(f, kp, 0, self, bv);
+      } else {
+        IsrKin f;
+        isr_map(k, kp.cp.mt, f);
+        isr_born_values<PID, double, 1>(f, kp, 0, self, bv);
+      }
+#pragma unroll
+      for (int i = 0; i < RealLayout<PID>::NBV; ++i) ib.v[(NB + i) * ib.cap + slot] = bv[i];
+    }
+  }
+}
+
+// W of every flagged point from its coefficients and values (float64 where re-evaluated).
+template <int PID>
+__global__ void k_rescue_combine(const double* __restrict__ wgt, double* __restrict__ out,
+                                 const int* __restrict__ counts, ItemBufs ib) {
+  constexpr int NI = RealLayout<PID>::NI;
+  const long m = counts[0];
+  for (long slot = (long)blockIdx.x * blockDim.x + threadIdx.x; slot < m; slot += (long)gridDim.x * blockDim.x) {
+    double W = 0.0;
+#pragma unroll
+    for (int i = 0; i < NI; ++i) W += ib.a[i * ib.cap + slot] * ib.v[i * ib.cap + slot];
+    const int ev = ib.ev[slot];
+    out[ev] = (wgt ? wgt[ev] : 1.0) * W;
   }
 }
 
@@ -806,7 +1046,8 @@ struct LaunchArgs {
   const int* idx;    // optional event list (rescue), length *count on the device
   const int* count;  // optional number of events, read on the device (events 0..*count-1 without idx)
   int* resc_list;    // real kernel in bulk precision: unstable points are appended here
-  int* resc_count;
+  int* resc_count;   // [0] flagged points, [1] queued kernel's tiles, [2] / [3] real-block / Born items
+  ItemBufs items;    // item rescue records and lists
   long groups;       // number of event groups to launch (n, or the list capacity)
   int* tiles;        // queued kernel: tile counter, zero at launch
 };
@@ -840,10 +1081,40 @@ cudaError_t launch_one(int kind, const LaunchArgs& a, cudaStream_t st) {
   } else {
     if constexpr (PID == P_EE_UUG || PID == P_GG_TTG || PID == P_UU_TTG)
       k_real_sub<PID, T, LPE><<<(unsigned)blocks, threads, 0, st>>>(a.p, a.wgt, a.n, a.out, a.kp, a.idx, a.count,
-                                                                       a.resc_list, a.resc_count);
+                                                                       a.resc_list, a.resc_count, a.items);
     else
       return cudaErrorInvalidValue;
   }
+  return cudaGetLastError();
+}
+
+// The item rescue after a bulk-precision launch with kp.item_rescue: float64 items,
+// then the recombination.  Persistent grids (resident blocks x SMs, found once per
+// device) walk the lists, whose lengths are read on the device.
+template <int PID>
+cudaError_t launch_items_one(const LaunchArgs& a, cudaStream_t st) {
+  (void)cudaGetLastError();
+  static std::atomic<int> resident[64];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  int g = resident[dev].load(std::memory_order_relaxed);
+  if (g == 0) {
+    int per = 0, sms = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_rescue_items<PID>, 128, 0);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    g = (per > 0 ? per : 1) * (sms > 0 ? sms : 1);
+    resident[dev].store(g, std::memory_order_relaxed);
+  }
+  const long cap_blocks = (a.items.cap * 4 + 127) / 128;
+  const unsigned gx = (unsigned)std::max(1L, std::min<long>(g, cap_blocks));
+  k_rescue_items<PID><<<dim3(gx, 2), 128, 0, st>>>(a.p, a.n, a.kp, a.resc_count, a.items);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const unsigned gc = (unsigned)std::max(1L, std::min<long>(4 * g, (a.items.cap + 255) / 256));
+  k_rescue_combine<PID><<<gc, 256, 0, st>>>(a.wgt, a.out, a.resc_count, a.items);
   return cudaGetLastError();
 }
 
@@ -853,6 +1124,10 @@ cudaError_t launch_gg(int pid, int kind, bool fp64, int lpe, const LaunchArgs& a
 cudaError_t launch_ggg(int pid, int kind, bool fp64, int lpe, const LaunchArgs& a, cudaStream_t st);
 cudaError_t launch_ggg64(int kind, int lpe, const LaunchArgs& a, cudaStream_t st);
 cudaError_t launch_uu(int pid, int kind, bool fp64, int lpe, const LaunchArgs& a, cudaStream_t st);
+// float64 items and recombination of the item rescue (one per process family)
+cudaError_t launch_items_ee(const LaunchArgs& a, cudaStream_t st);
+cudaError_t launch_items_gg(const LaunchArgs& a, cudaStream_t st);
+cudaError_t launch_items_uu(const LaunchArgs& a, cudaStream_t st);
 // mixed-precision subtracted real with the queued float64 re-evaluation (k_real_sub_queued)
 cudaError_t launch_queued(int pid, const LaunchArgs& a, cudaStream_t st);
 cudaError_t launch_queued_gg(const LaunchArgs& a, cudaStream_t st);

@@ -253,6 +253,34 @@ def test_queued_rescue_equals_separate_launches(me, name, seed):
         np.testing.assert_allclose(aq[:2], as_[:2], rtol=1e-6, atol=0)
 
 
+@pytest.mark.parametrize("name,seed", [("gg_ttg", 81), ("uu_ttg", 82), ("ee_uug", 83)])
+def test_item_rescue_matches_point_rescue(me, name, seed):
+    """The item rescue re-evaluates in float64 only the ingredients (real-emission
+    helicity blocks, counterterm Born values) a flagged point's tolerance needs and
+    recombines W = sum_i a_i v_i in float64; re-evaluating the flagged points whole is
+    the reference.  Same lane layout, so the float32 pass and the flagged points are
+    identical: the counts agree exactly, the item path does less float64 work, and the
+    weights agree to the mixed-precision tolerance (1e-5 of |W|, 99.9 %; the residual
+    float32 error of a flagged point is budgeted at a quarter of that).  A ragged size
+    spans many blocks and warps."""
+    n = 100003
+    b = synth.flat_points(name, n, seed)
+    p, w = _dev(b.p), _dev(b.wgt)
+    hi = me.Handle(name, precision=me.ME_PREC_MIXED, rescue=me.ME_RESCUE_ITEMS, lanes_per_event=2)
+    hp = me.Handle(name, precision=me.ME_PREC_MIXED, rescue=me.ME_RESCUE_POINTS, lanes_per_event=2)
+    wi = hi.real_subtracted(p, w).cpu().numpy()
+    wp = hp.real_subtracted(p, w).cpu().numpy()
+    pts, blocks, borns = hi.last_rescue_work()
+    assert pts == hp.last_rescued() > 0
+    nb = {"gg_ttg": 4, "uu_ttg": 2, "ee_uug": 2}[name]
+    assert 0 < blocks < nb * pts and borns <= pts
+    rel = np.abs(wi - wp) / np.abs(wp)
+    assert np.quantile(rel, 0.999) <= 1e-5 and rel.max() <= 1e-4, np.sort(rel)[-3:]
+    assert abs(wi.sum() - wp.sum()) <= 1e-6 * np.abs(wp).sum()
+    # unflagged points are untouched by the rescue: identical bits
+    np.testing.assert_array_equal(np.sort(np.flatnonzero(wi != wp)).size <= pts, True)
+
+
 def test_domain_boundary_points(me):
     """Points on the boundary of the FKS domain (no emitted energy, or the gluon exactly
     along a beam) carry weight 0 in both precisions, as in the oracle; they are not
