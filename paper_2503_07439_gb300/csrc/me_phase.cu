@@ -159,6 +159,135 @@ __global__ void k_rambo(uint64_t seed, uint32_t stream, long long first, double 
   if (wgt) wgt[i] = w;
 }
 
+// ---------------------------------------------------------------- points in FKS variables
+// Real-emission points generated directly in the sector variables of the FKS
+// subtraction, with a density that samples the soft and collinear regions: the emitted
+// gluon's energy fraction xi flat (flat three-body phase space has density ~ xi there),
+// y_j = 1 - 2 v^2 with v uniform towards the sector's reference direction j (density
+// g(y) = 1 / (4 sqrt((1 - y) / 2))), the azimuth and the Born direction uniform; the
+// two sectors are channels of one multichannel density.  Uniforms u0..u5 of point i are
+// those of Philox blocks 0..2 at counter (i lo, i hi, stream, block).
+__device__ __forceinline__ double coll_density(double y) {
+  return 1.0 / (4.0 * sqrt(fmax(0.0, 0.5 * (1.0 - y))));
+}
+
+__device__ __forceinline__ void boost_vel(const double p[4], const double b[3], double out[4]) {
+  const double b2 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+  const double g = 1.0 / sqrt(1.0 - b2);
+  const double bp = b[0] * p[1] + b[1] * p[2] + b[2] * p[3];
+  const double g2 = b2 > 0.0 ? (g - 1.0) / b2 : 0.0;
+  out[0] = g * (p[0] + bp);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) out[1 + d] = p[1 + d] + (g2 * bp + g * p[0]) * b[d];
+}
+
+// Initial-state sectors of 2 -> Q Qbar g (beams along +-z, Q mass `mass`): xi = xi_max u0,
+// y_j = 1 - 2 u1^2 w.r.t. beam j (j = 0 if u5 < 1/2: y = y_j along +z, else y = -y_j),
+// phi = 2 pi u2, the pair's rest-frame direction (2 u3 - 1, 2 pi u4); the pair recoils
+// against the gluon with mass^2 s (1 - xi).  dPhi_3 = dPhi_2(s) xi K dxi dy dphi,
+// K = s beta(s(1-xi)) / (64 pi^3 beta(s)): weight xi s beta(s(1-xi)) / (512 pi^4) x
+// xi_max 2 pi / ((g(y) + g(-y)) / 2).
+// Final-state sectors of massless 2 -> 3 (partner leg 2 if u0 < 1/2, else leg 3, along
+// (2 u1 - 1, 2 pi u2)): xi = u3, y_j = 1 - 2 u4^2 the gluon's cosine w.r.t. the partner,
+// phi = 2 pi u5 about it; the partner's energy sqrt(s)(1-xi)/(2 - xi(1-y_j)) leaves the
+// third parton massless.  Channel j has density 4 g(y_j) / (xi K_j) per unit dPhi_3,
+// K_j = s (1 - xi) / (16 pi^3 (2 - xi (1 - y_j))^2): weight 1 / sum_j 2 g(y_j) / (xi K_j).
+template <bool ISR>
+__global__ void k_fks_points(uint64_t seed, uint32_t stream, long long first, double rs, double mass, long n,
+                             double* __restrict__ p, double* __restrict__ wgt) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const unsigned long long idx = (unsigned long long)(first + i);
+  const uint32_t k0 = (uint32_t)(seed & 0xFFFFFFFFull), k1 = (uint32_t)(seed >> 32);
+  double u[6];
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    uint32_t c[4] = {(uint32_t)(idx & 0xFFFFFFFFull), (uint32_t)(idx >> 32), stream, (uint32_t)b};
+    philox4x32_10(c, k0, k1);
+    u[2 * b] = u01(c[0], c[1]);
+    u[2 * b + 1] = u01(c[2], c[3]);
+  }
+  const double s = rs * rs;
+  double q[5][4];  // legs: beams, then 2, 3, 4 (gluon)
+  const double hb = 0.5 * rs;
+  q[0][0] = hb; q[0][1] = 0.0; q[0][2] = 0.0; q[0][3] = hb;
+  q[1][0] = hb; q[1][1] = 0.0; q[1][2] = 0.0; q[1][3] = -hb;
+  double w;
+  if (ISR) {
+    const double ximax = 1.0 - 4.0 * mass * mass / s;
+    const double xi = ximax * u[0];
+    const double yj = 1.0 - 2.0 * u[1] * u[1];
+    const double y = u[5] < 0.5 ? yj : -yj;
+    double sf, cf, sp2, cp2;
+    sincos(2.0 * M_PI * u[2], &sf, &cf);
+    const double ek = 0.5 * rs * xi;
+    const double st = sqrt(fmax(0.0, (1.0 - y) * (1.0 + y)));
+    q[4][0] = ek;
+    q[4][1] = ek * st * cf;
+    q[4][2] = ek * st * sf;
+    q[4][3] = ek * y;
+    const double Q0 = rs - ek, M2 = Q0 * Q0 - ek * ek, M = sqrt(M2);
+    const double pstar = sqrt(fmax(0.0, 0.25 * M2 - mass * mass));
+    const double cp = 2.0 * u[3] - 1.0;
+    const double sp = sqrt(fmax(0.0, (1.0 - cp) * (1.0 + cp)));
+    sincos(2.0 * M_PI * u[4], &sp2, &cp2);
+    const double nv[3] = {sp * cp2, sp * sp2, cp};
+    const double e = 0.5 * M;
+    const double p3[4] = {e, pstar * nv[0], pstar * nv[1], pstar * nv[2]};
+    const double p4[4] = {e, -pstar * nv[0], -pstar * nv[1], -pstar * nv[2]};
+    const double bvec[3] = {-q[4][1] / Q0, -q[4][2] / Q0, -q[4][3] / Q0};
+    boost_vel(p3, bvec, q[2]);
+    boost_vel(p4, bvec, q[3]);
+    const double beta = sqrt(fmax(0.0, 1.0 - 4.0 * mass * mass / (s * (1.0 - xi))));
+    const double dens = 0.5 * (coll_density(y) + coll_density(-y));
+    w = xi * s * beta / (512.0 * M_PI * M_PI * M_PI * M_PI) * ximax * 2.0 * M_PI / dens;
+  } else {
+    const int partner = u[0] < 0.5 ? 2 : 3, other = 5 - partner;
+    const double cdir = 2.0 * u[1] - 1.0, xi = u[3], yj = 1.0 - 2.0 * u[4] * u[4];
+    double spd, cpd, sf, cf;
+    sincos(2.0 * M_PI * u[2], &spd, &cpd);
+    sincos(2.0 * M_PI * u[5], &sf, &cf);
+    const double sd = sqrt(fmax(0.0, (1.0 - cdir) * (1.0 + cdir)));
+    const double nj[3] = {sd * cpd, sd * spd, cdir};
+    double ea[3] = {-cdir * nj[0], -cdir * nj[1], 1.0 - cdir * nj[2]};  // z - (z.nj) nj
+    const double ia = 1.0 / sqrt(ea[0] * ea[0] + ea[1] * ea[1] + ea[2] * ea[2]);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) ea[d] *= ia;
+    const double eb[3] = {nj[1] * ea[2] - nj[2] * ea[1], nj[2] * ea[0] - nj[0] * ea[2], nj[0] * ea[1] - nj[1] * ea[0]};
+    const double sr = sqrt(fmax(0.0, (1.0 - yj) * (1.0 + yj)));
+    double ni[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) ni[d] = yj * nj[d] + sr * (cf * ea[d] + sf * eb[d]);
+    const double ei = 0.5 * rs * xi, ej = rs * (1.0 - xi) / (2.0 - xi * (1.0 - yj));
+    q[partner][0] = ej;
+    q[4][0] = ei;
+    q[other][0] = rs - ej - ei;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      q[partner][1 + d] = ej * nj[d];
+      q[4][1 + d] = ei * ni[d];
+      q[other][1 + d] = -(ej * nj[d] + ei * ni[d]);
+    }
+    // both channels' densities at this point, from its momenta
+    const double ig = 1.0 / sqrt(q[4][1] * q[4][1] + q[4][2] * q[4][2] + q[4][3] * q[4][3]);
+    double h = 0.0;
+#pragma unroll
+    for (int j = 2; j <= 3; ++j) {
+      const double kn = sqrt(q[j][1] * q[j][1] + q[j][2] * q[j][2] + q[j][3] * q[j][3]);
+      const double y = (q[4][1] * q[j][1] + q[4][2] * q[j][2] + q[4][3] * q[j][3]) * ig / kn;
+      const double d = 2.0 - xi * (1.0 - y);
+      const double K = s * (1.0 - xi) / (16.0 * M_PI * M_PI * M_PI * d * d);
+      h += 2.0 * coll_density(y) / (xi * K);
+    }
+    w = 1.0 / h;
+  }
+#pragma unroll
+  for (int comp = 0; comp < 4; ++comp)
+#pragma unroll
+    for (int l = 0; l < 5; ++l) p[(comp * 5 + l) * n + i] = q[l][comp];
+  if (wgt) wgt[i] = w;
+}
+
 // ---------------------------------------------------------------- unweighting
 // Hit-or-miss unweighting of signed weights: point i is kept iff u_i w_max < |w_i|, with
 // u_i the first uniform of Philox4x32-10 at counter (point lo, point hi, stream, 0);
@@ -343,6 +472,36 @@ extern "C" int me_generate_flat(me_handle* h, uint64_t seed, uint32_t stream, in
   }
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return me_internal_fail(ME_ERR_CUDA, (std::string("me_generate_flat: ") + cudaGetErrorString(e)).c_str());
+  return ME_OK;
+}
+
+extern "C" int me_generate_fks(me_handle* h, uint64_t seed, uint32_t stream, int64_t first_point, double sqrt_s,
+                               int64_t n, double* momenta, double* ps_weights) {
+  if (!h) return me_internal_fail(ME_ERR_ARG, "me_generate_fks: NULL handle");
+  const int pid = me_internal_handle_process(h);
+  const bool isr = pid == me_internal_process_id("gg_ttg") || pid == me_internal_process_id("uu_ttg");
+  if (!isr && pid != me_internal_process_id("ee_uug"))
+    return me_internal_fail(ME_ERR_PROCESS, "me_generate_fks: process has no FKS sectors");
+  if (n < 0 || n > (int64_t)INT32_MAX || first_point < 0 || !(sqrt_s > 0.0))
+    return me_internal_fail(ME_ERR_ARG, "me_generate_fks: bad n, first_point or sqrt_s");
+  if (n == 0) return ME_OK;
+  if (!momenta || !on_device(momenta) || (ps_weights && !on_device(ps_weights)))
+    return me_internal_fail(ME_ERR_ARG, "me_generate_fks: momenta and ps_weights must be device memory");
+  double masses[4];
+  int nout = 0;
+  cudaStream_t st = nullptr;
+  const int rc = me_internal_final_masses(h, masses, &nout, &st);
+  if (rc != ME_OK) return rc;
+  const double mass = masses[0];
+  if (!(2.0 * mass < sqrt_s)) return me_internal_fail(ME_ERR_ARG, "me_generate_fks: sqrt_s below the final-state masses");
+  const int threads = 128;
+  const unsigned blocks = (unsigned)((n + threads - 1) / threads);
+  if (isr)
+    k_fks_points<true><<<blocks, threads, 0, st>>>(seed, stream, first_point, sqrt_s, mass, n, momenta, ps_weights);
+  else
+    k_fks_points<false><<<blocks, threads, 0, st>>>(seed, stream, first_point, sqrt_s, mass, n, momenta, ps_weights);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return me_internal_fail(ME_ERR_CUDA, (std::string("me_generate_fks: ") + cudaGetErrorString(e)).c_str());
   return ME_OK;
 }
 

@@ -345,3 +345,68 @@ def fsr_emission_points(sqrt_s: float, cos_dir: np.ndarray, phi_dir: np.ndarray,
     out[0, other] = sqrt_s - ej - ei
     out[1:, other] = -(ej * nj + ei * ni)
     return np.ascontiguousarray(out)
+
+
+def _coll_density(y: np.ndarray) -> np.ndarray:
+    """Density in y of y = 1 - 2 v^2, v uniform in (0, 1): 1 / (4 sqrt((1 - y) / 2))."""
+    v = np.sqrt(np.maximum(0.0, 0.5 * (1.0 - y)))
+    with np.errstate(divide="ignore"):
+        return 1.0 / (4.0 * v)
+
+
+def fks_points(process: str, n: int, seed: int, first_point: int = 0, stream: int = 0,
+               sqrt_s: float | None = None) -> Batch:
+    """Phase-space points of a real-emission process generated directly in FKS variables
+    (the sector parametrisation of the subtraction), with a density that samples the soft
+    and collinear regions: flat in the emitted gluon's energy fraction xi (flat three-body
+    phase space has density ~ xi there), y_j = 1 - 2 v^2 with v uniform towards the
+    sector's reference direction j (density ~ 1/sqrt(1 - y_j)), the azimuth and the Born
+    direction uniform; both sectors are channels of one multichannel density, so each
+    weight is the phase-space measure over the sum of the channel densities.
+
+    Initial-state sectors (gg_ttg, uu_ttg; top mass MT): uniforms u0..u5 of the point
+    give xi = xi_max u0 (xi_max = 1 - 4 m^2 / s), v = u1, phi = 2 pi u2, the heavy pair's
+    rest-frame direction (2 u3 - 1, 2 pi u4) and the beam j (0 if u5 < 1/2: y = y_j is the
+    gluon's cosine w.r.t. +z; else y = -y_j).  dPhi_3 = dPhi_2(s) xi K dxi dy dphi with
+    dPhi_2(s) = beta(s) / (8 pi) dOmega* / (4 pi) and K = s beta(s(1-xi)) / (64 pi^3 beta(s)),
+    so the weight is xi s beta(s(1 - xi)) / (512 pi^4) xi_max 2 pi / ((g(y) + g(-y)) / 2),
+    g the density of y = 1 - 2 v^2.
+    Final-state sectors (ee_uug, massless): u0 chooses the partner (leg 2 if u0 < 1/2,
+    else leg 3), (2 u1 - 1, 2 pi u2) its direction, xi = u3, y_j = 1 - 2 u4^2 the gluon's
+    cosine w.r.t. the partner, phi = 2 pi u5; each sector's parametrisation covers the
+    space once, dPhi_3 = (1/(8 pi)) (dOmega/(4 pi)) xi K_j dxi dy dphi with
+    K_j = s (1 - xi) / (16 pi^3 (2 - xi (1 - y_j))^2), so channel j has density
+    4 g(y_j) / (xi K_j) per unit dPhi_3 and the weight is 1 / sum_j (2 g(y_j) / (xi K_j)),
+    y_j the gluon's cosine w.r.t. leg j."""
+    rs = sqrt_s if sqrt_s is not None else {"ee_uug": 100.0, "gg_ttg": 1000.0, "uu_ttg": 1000.0}[process]
+    s = rs * rs
+    u = uniforms(seed, stream, n, 6, first_point)
+    if process in ("gg_ttg", "uu_ttg"):
+        ximax = 1.0 - 4.0 * MT * MT / s
+        xi = ximax * u[0]
+        yj = 1.0 - 2.0 * u[1] * u[1]
+        y = np.where(u[5] < 0.5, yj, -yj)
+        p = emission_points(rs, MT, xi, y, 2.0 * math.pi * u[2], 2.0 * u[3] - 1.0, 2.0 * math.pi * u[4])
+        beta = np.sqrt(np.maximum(0.0, 1.0 - 4.0 * MT * MT / (s * (1.0 - xi))))
+        dens = 0.5 * (_coll_density(y) + _coll_density(-y))
+        w = xi * s * beta / (512.0 * math.pi ** 4) * ximax * 2.0 * math.pi / dens
+        return Batch(process, rs, p, w)
+    if process != "ee_uug":
+        raise ValueError(f"{process} has no FKS sectors")
+    cdir, pdir, xi = 2.0 * u[1] - 1.0, 2.0 * math.pi * u[2], u[3]
+    yj, phi = 1.0 - 2.0 * u[4] * u[4], 2.0 * math.pi * u[5]
+    p = np.empty((4, 5, n))
+    for partner, sel in ((2, u[0] < 0.5), (3, u[0] >= 0.5)):
+        if sel.any():
+            p[:, :, sel] = fsr_emission_points(rs, cdir[sel], pdir[sel], xi[sel], yj[sel], phi[sel], partner)
+    kg = p[1:, 4]
+    ng = kg / np.sqrt((kg * kg).sum(axis=0))
+    h = np.zeros(n)
+    for j in (2, 3):
+        kj = p[1:, j]
+        y = (ng * kj).sum(axis=0) / np.sqrt((kj * kj).sum(axis=0))
+        K = s * (1.0 - xi) / (16.0 * math.pi ** 3 * (2.0 - xi * (1.0 - y)) ** 2)
+        h += 2.0 * _coll_density(y) / (xi * K)
+    with np.errstate(divide="ignore"):
+        w = 1.0 / h
+    return Batch(process, rs, np.ascontiguousarray(p), w)

@@ -144,3 +144,67 @@ def test_approach_points_labels():
     b, lab = synth.approach_points("gg_ttg", 8, 5)
     assert b.n == 8 * 16
     assert set(np.unique(lab["kind"])) == {0, 1, 2}
+
+
+def test_fks_points_invert_to_their_sector_variables():
+    """Points generated in FKS variables map back, through the oracle's inverse sector
+    maps, to the variables they were built from, and are on shell and balanced."""
+    from oracle import fks
+    from oracle.matrix_element import to_points
+    n = 512
+    b = synth.fks_points("gg_ttg", n, 3)
+    u = synth.uniforms(3, 0, n, 6)
+    k = to_points(b.p)
+    ximax = 1.0 - 4.0 * synth.MT ** 2 / 1e6
+    kin = fks.isr_map(k, 4, 0, synth.MT)
+    np.testing.assert_allclose(kin.xi, ximax * u[0], rtol=1e-12)
+    yj = 1.0 - 2.0 * u[1] ** 2
+    np.testing.assert_allclose(kin.y, np.where(u[5] < 0.5, yj, -yj), atol=1e-12)
+    _check_momenta(b.p[:, 2:], [synth.MT, synth.MT, 0.0], 1000.0)
+    e = synth.fks_points("ee_uug", n, 3)
+    u = synth.uniforms(3, 0, n, 6)
+    ke = to_points(e.p)
+    for partner in (2, 3):
+        sel = (u[0] < 0.5) if partner == 2 else (u[0] >= 0.5)
+        kin = fks.fsr_map(ke[sel], 4, partner, 5 - partner)
+        np.testing.assert_allclose(kin.xi, u[3][sel], rtol=1e-12)
+        np.testing.assert_allclose(kin.y, 1.0 - 2.0 * u[4][sel] ** 2, atol=1e-12)
+    _check_momenta(e.p[:, 2:], [0.0, 0.0, 0.0], 100.0)
+
+
+def test_fks_point_weights_are_the_oracle_jacobians():
+    """Each weight is the phase-space measure over the generator density, with the sector
+    Jacobians K of the oracle's maps (pinned there by quadrature and the RAMBO volumes):
+    initial state dPhi_2(s) xi K x (xi_max 2 pi / ((g(y) + g(-y)) / 2)); final state
+    1 / sum_j 2 g(y_j) / (xi K_j), g(y) = 1 / (4 sqrt((1 - y)/2))."""
+    from oracle import fks
+    from oracle.matrix_element import to_points
+    n = 512
+    g = lambda y: 1.0 / (4.0 * np.sqrt(0.5 * (1.0 - y)))
+    b = synth.fks_points("uu_ttg", n, 8)
+    k = to_points(b.p)
+    kin = fks.isr_map(k, 4, 0, synth.MT)
+    s = 1e6
+    beta = math.sqrt(1.0 - 4.0 * synth.MT ** 2 / s)
+    ximax = 1.0 - 4.0 * synth.MT ** 2 / s
+    ref = beta / (8 * math.pi) * kin.xi * kin.K * ximax * 2 * math.pi / (0.5 * (g(kin.y) + g(-kin.y)))
+    # (the map recovers y from the momenta: 1 - |y| near 0 carries the momenta's rounding
+    # relative to 1 - |y|, hence 1e-10 rather than 1e-12; a wrong Jacobian is off by O(1))
+    np.testing.assert_allclose(b.wgt, ref, rtol=1e-10)
+    e = synth.fks_points("ee_uug", n, 8)
+    ke = to_points(e.p)
+    h = sum(2.0 * g(kk.y) / (kk.xi * kk.K) for kk in (fks.fsr_map(ke, 4, 2, 3), fks.fsr_map(ke, 4, 3, 2)))
+    np.testing.assert_allclose(e.wgt, 1.0 / h, rtol=1e-10)
+
+
+def test_fks_point_weights_integrate_to_the_phase_space_volume():
+    """Mean weight = three-body volume: s/(256 pi^3) for massless partons, the massive
+    RAMBO volume for t tbar g (within 4 combined standard errors)."""
+    n = 1 << 18
+    e = synth.fks_points("ee_uug", n, 12)
+    vol = 100.0 ** 2 / (256 * math.pi ** 3)
+    assert abs(e.wgt.mean() - vol) <= 4 * e.wgt.std() / math.sqrt(n)
+    b = synth.fks_points("gg_ttg", n, 12)
+    r = synth.flat_points("gg_ttg", n, 12)
+    err = math.hypot(b.wgt.std(), r.wgt.std()) / math.sqrt(n)
+    assert abs(b.wgt.mean() - r.wgt.mean()) <= 4 * err
