@@ -287,6 +287,13 @@ typedef struct me_server_params {
   int64_t mem_budget_bytes;  /* admission budget for in-flight request buffers */
   me_params params;          /* physics and precision, shared by all requests */
   int32_t use_graphs;        /* 1: replay each (process, kind) launch sequence from a captured CUDA graph */
+  int32_t persistent;        /* 1: the e+e-, g g and u ubar families (ee_uu/ee_uug, gg_tt/gg_ttg,
+                                uu_tt/uu_ttg) run on one persistent kernel per family that reads
+                                work descriptors from a ring in pinned host memory (no launch
+                                per request); gg_ttgg stays on the slots */
+  int32_t persistent_idle_us; /* a persistent kernel with no work for this long ends with
+                                 ME_ERR_TIMEOUT (counted by me_server_persistent_stats) and is
+                                 launched again by the next request of its family */
 } me_server_params;
 
 /* One batch: host buffers owned by the caller, kept alive until me_poll returns it. */
@@ -309,7 +316,8 @@ typedef struct me_result {
   double t_total_us;         /* submit -> completion seen by the slot thread */
 } me_result;
 
-/* Defaults: device 0, 4 slots, queue 4096, 8 GiB budget, mixed precision, graphs on. */
+/* Defaults: device 0, 4 slots, queue 4096, 8 GiB budget, mixed precision, graphs on,
+ * persistent kernels off (idle limit 2000 us when on). */
 void me_default_server_params(me_server_params* p);
 /* Start a server and its slot threads.  ME_ERR_ARG for bad parameters. */
 int me_server_create(const me_server_params* params, me_server** out);
@@ -323,6 +331,12 @@ int me_poll(me_server* s, me_ticket t, me_result* out, int64_t timeout_us);
 /* Requests run so far by replaying a captured CUDA graph (every request of a
  * (process, kind, weights) key after the first on a slot) and by ordinary launches. */
 int me_server_stats(me_server* s, int64_t* graph_runs, int64_t* plain_runs);
+/* Persistent kernels (server created with persistent = 1), summed over the families:
+ * kernel launches, launches that ended because their wait for work ran out
+ * (ME_ERR_TIMEOUT, the idle limit), and requests served by them.  The wait is a bounded
+ * device-side poll of the descriptor ring; every other wait in those kernels is bounded
+ * too, so a kernel always ends. */
+int me_server_persistent_stats(me_server* s, int64_t* launches, int64_t* idle_timeouts, int64_t* requests);
 /* Stop the slot threads, wait for in-flight work, free everything.  NULL is a no-op. */
 void me_server_destroy(me_server* s);
 

@@ -47,7 +47,8 @@ class MEParams(ctypes.Structure):
 class MEServerParams(ctypes.Structure):
     _fields_ = [("version", ctypes.c_uint32), ("device", ctypes.c_int32), ("n_slots", ctypes.c_int32),
                 ("max_queue", ctypes.c_int32), ("mem_budget_bytes", ctypes.c_int64), ("params", MEParams),
-                ("use_graphs", ctypes.c_int32)]
+                ("use_graphs", ctypes.c_int32), ("persistent", ctypes.c_int32),
+                ("persistent_idle_us", ctypes.c_int32)]
 
 
 class MERequest(ctypes.Structure):
@@ -97,6 +98,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "me_poll": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.POINTER(MEResult), i64]),
         "me_server_destroy": (None, [vp]),
         "me_server_stats": (ctypes.c_int, [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
+        "me_server_persistent_stats": (ctypes.c_int, [vp, ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                                      ctypes.POINTER(i64)]),
         "me_generate_flat": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.c_uint32, i64, ctypes.c_double, i64, vp, vp]),
         "me_generate_fks": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.c_uint32, i64, ctypes.c_double, i64, vp, vp]),
         "me_unweight": (ctypes.c_int, [vp, vp, i64, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint32, i64, vp, vp,
@@ -293,7 +296,8 @@ class Server:
     """Request loop (me_server_create / me_submit / me_poll / me_server_destroy)."""
 
     def __init__(self, device: int = 0, n_slots: int = 4, max_queue: int = 4096, mem_budget_bytes: int = 0,
-                 precision: int = ME_PREC_MIXED, use_graphs: bool = True, **params):
+                 precision: int = ME_PREC_MIXED, use_graphs: bool = True, persistent: bool = False,
+                 persistent_idle_us: int = 0, **params):
         self.lib = library()
         sp = MEServerParams()
         self.lib.me_default_server_params(ctypes.byref(sp))
@@ -301,6 +305,9 @@ class Server:
         sp.n_slots = n_slots
         sp.max_queue = max_queue
         sp.use_graphs = 1 if use_graphs else 0
+        sp.persistent = 1 if persistent else 0
+        if persistent_idle_us:
+            sp.persistent_idle_us = persistent_idle_us
         if mem_budget_bytes:
             sp.mem_budget_bytes = mem_budget_bytes
         sp.params = default_params(precision=precision, device=device, **params)
@@ -333,10 +340,14 @@ class Server:
                 "out": ko}
 
     def stats(self) -> dict:
-        """Requests run by replaying a captured CUDA graph and by ordinary launches."""
+        """Requests run by replaying a captured CUDA graph and by ordinary launches; with
+        persistent kernels also their launches, idle exits (ME_ERR_TIMEOUT) and requests."""
         g, p = ctypes.c_int64(), ctypes.c_int64()
         _check(self.lib.me_server_stats(self.s, ctypes.byref(g), ctypes.byref(p)))
-        return {"graph_runs": g.value, "plain_runs": p.value}
+        la, to, rq = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(self.lib.me_server_persistent_stats(self.s, ctypes.byref(la), ctypes.byref(to), ctypes.byref(rq)))
+        return {"graph_runs": g.value, "plain_runs": p.value, "persistent_launches": la.value,
+                "persistent_idle_timeouts": to.value, "persistent_requests": rq.value}
 
     def close(self):
         if getattr(self, "s", None):

@@ -1027,6 +1027,16 @@ int me_internal_kparams(const char* process, const me_params* params, me::KParam
 
 int me_internal_handle_process(const me_handle* h) { return h ? h->proc->pid : -1; }
 
+int me_internal_device_kparams(const char* process, const me_params* params, me::KParams* kp, int* pid) {
+  int rc = me_internal_kparams(process, params, kp, pid);
+  if (rc != ME_OK) return rc;
+  ColourTables* d_tab = nullptr;
+  if ((rc = device_setup(params->device, &d_tab)) != ME_OK) return rc;
+  kp->tab = d_tab;
+  kp->item_budget = kItemBudget;
+  return ME_OK;
+}
+
 int me_internal_process_id(const char* name) {
   if (!name) return -1;
   for (const auto& d : kProcs)

@@ -34,6 +34,8 @@ struct KParams;
 int me_internal_build_tables(me::ColourTables* tab);
 // Validate parameters and fill kernel parameters for a process (tables pointer unset).
 int me_internal_kparams(const char* process, const me_params* params, me::KParams* kp, int* pid);
+// The same with the device-resident tables of params->device set up and filled in.
+int me_internal_device_kparams(const char* process, const me_params* params, me::KParams* kp, int* pid);
 // Whether a buffer of CUDA memory type `mem_type` on device `mem_device` can be handed to
 // a kernel on `want_device` without peer access (1) or not (0); exported with C linkage.
 extern "C" int me_internal_buffer_usable(int mem_type, int mem_device, int want_device);

@@ -11,6 +11,10 @@
 // key's launch sequence -- main kernel, float64 rescue, reduction, with the batch size
 // read on the device -- in a CUDA graph once, and replays it for every later request of
 // the key (momenta copied with the slot's fixed stride).
+// With persistent = 1 the e+e-, g g and u ubar families instead run on one persistent
+// kernel each (me_persist.cuh): a family thread stages each request in pinned host
+// memory, publishes a work descriptor to the family's ring, launches the kernel when none
+// is running, and retires requests as their completion records appear.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -30,6 +34,7 @@
 
 #include "../../include/me.h"
 #include "me_internal.h"
+#include "me_persist.cuh"
 
 namespace {
 
@@ -73,6 +78,39 @@ struct Slot {
   Req* cur = nullptr;
 };
 
+// One persistent process family: its ring, control words, staging and kernel state.
+struct Family {
+  int id = -1;
+  int pid_born = -1, pid_real = -1;
+  cudaStream_t st = nullptr;
+  cudaEvent_t kdone = nullptr;
+  me::PDesc* descs = nullptr;  // pinned, mapped (host view)
+  me::PDone* dones = nullptr;
+  me::PCtl* ctl = nullptr;
+  me::PDesc* d_descs = nullptr;  // device views of the same
+  me::PDone* d_dones = nullptr;
+  me::PCtl* d_ctl = nullptr;
+  me::PDev* dev = nullptr;  // device memory
+  me::KParams kpB{}, kpR{};
+  double* h_buf[me::P_RING] = {};  // staging per ring slot: momenta, weights, output
+  double* d_buf[me::P_RING] = {};
+  size_t cap[me::P_RING] = {};     // doubles
+  Req* inflight[me::P_RING] = {};
+  clk::time_point t_pub[me::P_RING];
+  unsigned next = 0, oldest = 0, kpos0 = 0;
+  bool running = false;
+  std::deque<Req*> queue;
+  std::thread worker;
+  std::atomic<int64_t> launches{0}, timeouts{0}, served{0};
+};
+
+int family_of(int pid) {
+  if (pid == me::P_EE_UU || pid == me::P_EE_UUG) return 0;
+  if (pid == me::P_GG_TT || pid == me::P_GG_TTG) return 1;
+  if (pid == me::P_UU_TT || pid == me::P_UU_TTG) return 2;
+  return -1;
+}
+
 void drop_graphs(Slot& s) {
   for (auto& kv : s.progs) {
     if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
@@ -91,6 +129,7 @@ struct me_server {
   std::unordered_map<uint64_t, Req*> reqs;
   std::vector<Slot> slots;
   std::vector<std::thread> workers;  // one per slot
+  Family fam[3];                     // persistent families (persistent = 1)
   bool stop = false;
   int64_t mem_in_use = 0;
   uint64_t next_ticket = 1;
@@ -296,6 +335,221 @@ static void slot_loop(me_server* sv, int si) {
   }
 }
 
+// ---------------------------------------------------------------- persistent families
+static const char* kFamBorn[3] = {"ee_uu", "gg_tt", "uu_tt"};
+static const char* kFamReal[3] = {"ee_uug", "gg_ttg", "uu_ttg"};
+
+static int family_init(me_server* sv, Family& f, int id) {
+  f.id = id;
+  me_params prm = sv->prm.params;
+  prm.device = sv->prm.device;
+  int rc = me_internal_device_kparams(kFamBorn[id], &prm, &f.kpB, &f.pid_born);
+  if (rc == ME_OK) rc = me_internal_device_kparams(kFamReal[id], &prm, &f.kpR, &f.pid_real);
+  if (rc != ME_OK) return rc;
+  if (cudaStreamCreateWithFlags(&f.st, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&f.kdone, cudaEventDisableTiming) != cudaSuccess ||
+      cudaHostAlloc(&f.descs, me::P_RING * sizeof(me::PDesc), cudaHostAllocMapped) != cudaSuccess ||
+      cudaHostAlloc(&f.dones, me::P_RING * sizeof(me::PDone), cudaHostAllocMapped) != cudaSuccess ||
+      cudaHostAlloc(&f.ctl, sizeof(me::PCtl), cudaHostAllocMapped) != cudaSuccess ||
+      cudaMalloc(&f.dev, sizeof(me::PDev)) != cudaSuccess)
+    return sfail(ME_ERR_CUDA, "me_server_create: persistent family allocation failed");
+  std::memset(f.descs, 0, me::P_RING * sizeof(me::PDesc));
+  std::memset(f.dones, 0, me::P_RING * sizeof(me::PDone));
+  std::memset(f.ctl, 0, sizeof(me::PCtl));
+  if (cudaHostGetDevicePointer((void**)&f.d_descs, f.descs, 0) != cudaSuccess ||
+      cudaHostGetDevicePointer((void**)&f.d_dones, f.dones, 0) != cudaSuccess ||
+      cudaHostGetDevicePointer((void**)&f.d_ctl, f.ctl, 0) != cudaSuccess)
+    return sfail(ME_ERR_CUDA, "me_server_create: mapped pointers");
+  return ME_OK;
+}
+
+static void family_free(Family& f) {
+  for (int i = 0; i < me::P_RING; ++i) cudaFreeHost(f.h_buf[i]);
+  cudaFreeHost(f.descs);
+  cudaFreeHost(f.dones);
+  cudaFreeHost(f.ctl);
+  cudaFree(f.dev);
+  if (f.kdone) cudaEventDestroy(f.kdone);
+  if (f.st) cudaStreamDestroy(f.st);
+}
+
+// Retire request r of ring slot `slot` with `status` (family thread).
+static void family_finish(me_server* sv, Family& f, int slot, int status) {
+  Req* r = f.inflight[slot];
+  f.inflight[slot] = nullptr;
+  r->res.status = status;
+  r->res.n = r->n;
+  double a = 0, b = 0;
+  if (status == ME_OK) {
+    const double* o = f.h_buf[slot] + (size_t)r->n * (4 * r->n_ext + 1);
+    std::memcpy(r->out, o, (size_t)r->n * 8);
+    for (int64_t i = 0; i < r->n; ++i) {
+      a += r->out[i];
+      b += r->out[i] * r->out[i];
+    }
+    r->res.n_rescued = f.dones[slot].n_rescued;
+  }
+  r->res.sum_w = a;
+  r->res.sum_w2 = b;
+  const auto now = clk::now();
+  r->res.t_queue_us = std::chrono::duration<double, std::micro>(r->t_admit - r->t_submit).count();
+  r->res.t_device_us = std::chrono::duration<double, std::micro>(now - f.t_pub[slot]).count();
+  r->res.t_total_us = std::chrono::duration<double, std::micro>(now - r->t_submit).count();
+  std::lock_guard<std::mutex> lk(sv->mu);
+  sv->mem_in_use -= (int64_t)r->bytes;
+  r->done = true;
+  ++f.served;
+  sv->cv_done.notify_all();
+  sv->cv_work.notify_all();
+}
+
+// Stage request r in ring slot `slot` and publish its descriptor (family thread).
+static int family_publish(me_server* sv, Family& f, Req* r) {
+  const int slot = (int)(f.next % me::P_RING);
+  const size_t need = (size_t)r->n * (4 * r->n_ext + 2);  // momenta, weights, output
+  if (need > f.cap[slot]) {
+    std::shared_lock<std::shared_mutex> cs(sv->cuda_mu);
+    cudaFreeHost(f.h_buf[slot]);
+    f.h_buf[slot] = f.d_buf[slot] = nullptr;
+    f.cap[slot] = 0;
+    const size_t c = std::max<size_t>(need, 4096 * 28);
+    if (cudaHostAlloc(&f.h_buf[slot], c * 8, cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer((void**)&f.d_buf[slot], f.h_buf[slot], 0) != cudaSuccess)
+      return sfail(ME_ERR_OOM, "persistent staging allocation failed");
+    f.cap[slot] = c;
+  }
+  const size_t pn = (size_t)r->n * 4 * r->n_ext;
+  std::memcpy(f.h_buf[slot], r->p, pn * 8);
+  if (r->w) std::memcpy(f.h_buf[slot] + pn, r->w, (size_t)r->n * 8);
+  me::PDesc& d = f.descs[slot];
+  d.p = f.d_buf[slot];
+  d.w = r->w ? f.d_buf[slot] + pn : nullptr;
+  d.out = f.d_buf[slot] + pn + r->n;
+  d.n = r->n;
+  d.pid = r->pid;
+  d.kind = r->kind == ME_KIND_REAL_SUBTRACTED ? me::K_REAL : me::K_TREE;
+  d.nlo = 1.0;
+  if (r->kind == ME_KIND_NBODY_NLO) {  // the n-body NLO factor of e+e- -> u ubar
+    const me_params& pp = sv->prm.params;
+    const double a_s = pp.alpha_s * (4.0 / 3.0) / (2.0 * M_PI);
+    d.nlo = 1.0 + a_s * (5.0 - 2.0 * M_PI * M_PI / 3.0 - (3.0 + 4.0 * std::log(pp.xi_cut)) * std::log(0.5 * pp.delta));
+  }
+  f.inflight[slot] = r;
+  f.t_pub[slot] = clk::now();
+  __atomic_store_n(&d.seq, f.next + 1, __ATOMIC_RELEASE);  // last: the descriptor is complete
+  ++f.next;
+  return ME_OK;
+}
+
+// Launch the family's kernel at the first unprocessed position (family thread).
+static int family_launch(me_server* sv, Family& f) {
+  std::shared_lock<std::shared_mutex> cs(sv->cuda_mu);
+  cudaSetDevice(sv->prm.device);
+  f.ctl->exit_status = 0;
+  f.ctl->error = 0;
+  f.ctl->stop = 0;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, sv->prm.device);
+  // one block on half of the SMs per family (255 registers x 128 threads: two blocks fit
+  // an SM), so the three families and the slots' kernels are resident together
+  const unsigned blocks = (unsigned)std::max(1, sms / 2);
+  cudaError_t e = cudaMemsetAsync(f.dev, 0, sizeof(me::PDev), f.st);
+  if (e == cudaSuccess)
+    e = me::launch_serve(f.id, sv->prm.params.precision == ME_PREC_MIXED, blocks, f.d_descs, f.d_dones, f.d_ctl,
+                         f.dev, f.kpB, f.kpR, f.kpos0, (unsigned long long)sv->prm.persistent_idle_us * 1000ull, f.st);
+  if (e == cudaSuccess) e = cudaEventRecord(f.kdone, f.st);
+  if (e != cudaSuccess) return sfail(ME_ERR_CUDA, std::string("persistent launch: ") + cudaGetErrorString(e));
+  f.running = true;
+  ++f.launches;
+  return ME_OK;
+}
+
+static void family_loop(me_server* sv, int id) {
+  Family& f = sv->fam[id];
+  cudaSetDevice(sv->prm.device);
+  for (;;) {
+    bool stopping;
+    // admit the oldest queued requests while the ring has room and memory allows
+    std::vector<Req*> admit;
+    {
+      std::unique_lock<std::mutex> lk(sv->mu);
+      stopping = sv->stop;
+      while (!f.queue.empty() && f.next + (unsigned)admit.size() - f.oldest < (unsigned)me::P_RING) {
+        Req* head = f.queue.front();
+        if (sv->mem_in_use + (int64_t)head->bytes > sv->prm.mem_budget_bytes && sv->mem_in_use != 0) break;
+        f.queue.pop_front();
+        sv->mem_in_use += (int64_t)head->bytes;
+        head->t_admit = clk::now();
+        admit.push_back(head);
+      }
+      if (admit.empty() && f.oldest == f.next && !f.running) {
+        if (stopping) break;
+        sv->cv_work.wait_for(lk, std::chrono::milliseconds(5));
+        continue;
+      }
+    }
+    for (Req* r : admit) {
+      const int rc = family_publish(sv, f, r);
+      if (rc != ME_OK) {  // not published: retire it with the error
+        const int slot = (int)(f.next % me::P_RING);
+        f.inflight[slot] = r;
+        f.t_pub[slot] = clk::now();
+        family_finish(sv, f, slot, rc);
+      }
+    }
+    if (f.oldest != f.next && !f.running && family_launch(sv, f) != ME_OK) {
+      while (f.oldest != f.next) family_finish(sv, f, (int)(f.oldest++ % me::P_RING), ME_ERR_CUDA);
+    }
+    if (stopping && f.running) f.ctl->stop = 1;
+    // completions, in ring order
+    bool progress = !admit.empty();
+    while (f.oldest != f.next) {
+      const int slot = (int)(f.oldest % me::P_RING);
+      const unsigned seq = __atomic_load_n(&f.dones[slot].seq, __ATOMIC_ACQUIRE);
+      if (seq != f.oldest + 1) break;
+      family_finish(sv, f, slot, f.dones[slot].status);
+      ++f.oldest;
+      progress = true;
+    }
+    if (f.running) {
+      cudaError_t q;
+      {
+        std::shared_lock<std::shared_mutex> cs(sv->cuda_mu);
+        q = cudaEventQuery(f.kdone);
+      }
+      if (q != cudaErrorNotReady) {
+        f.running = false;
+        progress = true;
+        // completions published just before the kernel ended
+        while (f.oldest != f.next) {
+          const int slot = (int)(f.oldest % me::P_RING);
+          if (__atomic_load_n(&f.dones[slot].seq, __ATOMIC_ACQUIRE) != f.oldest + 1)
+            break;
+          family_finish(sv, f, slot, f.dones[slot].status);
+          ++f.oldest;
+        }
+        if (f.ctl->exit_status == ME_ERR_TIMEOUT) ++f.timeouts;
+        f.kpos0 = f.ctl->exit_pos;
+        if (q != cudaSuccess || f.ctl->error || f.kpos0 != f.oldest) {
+          std::fprintf(stderr, "me_server: persistent kernel of family %d ended abnormally (%s)\n", id,
+                       q != cudaSuccess ? cudaGetErrorString(q) : "wait limit");
+          cudaGetLastError();
+          // requests it did not finish fail; the next launch starts after them
+          while (f.oldest != f.next) family_finish(sv, f, (int)(f.oldest++ % me::P_RING), ME_ERR_TIMEOUT);
+          f.kpos0 = f.next;
+        }
+      }
+    }
+    if (!progress) std::this_thread::sleep_for(std::chrono::microseconds(f.oldest != f.next ? 5 : 50));
+  }
+  // stopped: the kernel (if any) has been told to stop and has ended
+  if (f.running) {
+    f.ctl->stop = 1;
+    cudaEventSynchronize(f.kdone);
+    f.running = false;
+  }
+}
+
 extern "C" {
 
 void me_default_server_params(me_server_params* p) {
@@ -307,6 +561,8 @@ void me_default_server_params(me_server_params* p) {
   p->max_queue = 4096;
   p->mem_budget_bytes = (int64_t)8 << 30;
   p->use_graphs = 1;
+  p->persistent = 0;
+  p->persistent_idle_us = 2000;
   me_default_params(&p->params);
   p->params.precision = ME_PREC_MIXED;
 }
@@ -315,7 +571,7 @@ int me_server_create(const me_server_params* prm, me_server** out) {
   if (!prm || !out) return sfail(ME_ERR_ARG, "me_server_create: NULL argument");
   *out = nullptr;
   if (prm->version != ME_PARAMS_VERSION || prm->n_slots < 1 || prm->n_slots > 64 || prm->max_queue < 1 ||
-      prm->mem_budget_bytes <= 0)
+      prm->mem_budget_bytes <= 0 || (prm->persistent && (prm->persistent_idle_us < 100 || prm->persistent_idle_us > 10000000)))
     return sfail(ME_ERR_ARG, "me_server_create: bad parameters");
   if (cudaSetDevice(prm->device) != cudaSuccess) return sfail(ME_ERR_CUDA, "me_server_create: bad device");
   me_server* sv = new me_server();
@@ -330,6 +586,16 @@ int me_server_create(const me_server_params* prm, me_server** out) {
       return sfail(ME_ERR_CUDA, "me_server_create: stream/event allocation failed");
     }
     *s.h_resc = 0;
+  }
+  if (prm->persistent) {
+    for (int id = 0; id < 3; ++id) {
+      const int rc = family_init(sv, sv->fam[id], id);
+      if (rc != ME_OK) {
+        me_server_destroy(sv);
+        return rc;
+      }
+    }
+    for (int id = 0; id < 3; ++id) sv->fam[id].worker = std::thread(family_loop, sv, id);
   }
   for (int i = 0; i < prm->n_slots; ++i) sv->workers.emplace_back(slot_loop, sv, i);
   *out = sv;
@@ -366,7 +632,17 @@ int me_submit(me_server* sv, const me_request* rq, me_ticket* out) {
   }
   r->ticket = sv->next_ticket++;
   sv->reqs[r->ticket] = r;
-  sv->pending.push_back(r);
+  // a family's kernel evaluates its Born process (Born, and the n-body NLO weight for
+  // e+e- -> u ubar) and the subtracted real of its real process; anything else (gg_ttgg,
+  // or a kind a process does not have, which then fails there) goes to the slots
+  const int fam = sv->prm.persistent ? family_of(pid) : -1;
+  const bool fam_born = fam >= 0 && pid == sv->fam[fam].pid_born &&
+                        (r->kind == ME_KIND_BORN || (r->kind == ME_KIND_NBODY_NLO && pid == me::P_EE_UU));
+  const bool fam_real = fam >= 0 && pid == sv->fam[fam].pid_real && r->kind == ME_KIND_REAL_SUBTRACTED;
+  if (fam_born || fam_real)
+    sv->fam[fam].queue.push_back(r);
+  else
+    sv->pending.push_back(r);
   *out = r->ticket;
   sv->cv_work.notify_all();
   return ME_OK;
@@ -388,6 +664,18 @@ int me_poll(me_server* sv, me_ticket t, me_result* out, int64_t timeout_us) {
   return ME_OK;
 }
 
+int me_server_persistent_stats(me_server* sv, int64_t* launches, int64_t* idle_timeouts, int64_t* requests) {
+  if (!sv || !launches || !idle_timeouts || !requests) return sfail(ME_ERR_ARG, "me_server_persistent_stats: NULL argument");
+  std::lock_guard<std::mutex> lk(sv->mu);
+  *launches = *idle_timeouts = *requests = 0;
+  for (auto& f : sv->fam) {
+    *launches += f.launches.load();
+    *idle_timeouts += f.timeouts.load();
+    *requests += f.served.load();
+  }
+  return ME_OK;
+}
+
 int me_server_stats(me_server* sv, int64_t* graph_runs, int64_t* plain_runs) {
   if (!sv || !graph_runs || !plain_runs) return sfail(ME_ERR_ARG, "me_server_stats: NULL argument");
   *graph_runs = sv->graph_runs.load();
@@ -404,7 +692,10 @@ void me_server_destroy(me_server* sv) {
   sv->cv_work.notify_all();
   for (auto& t : sv->workers)
     if (t.joinable()) t.join();
+  for (auto& f : sv->fam)
+    if (f.worker.joinable()) f.worker.join();
   cudaSetDevice(sv->prm.device);
+  for (auto& f : sv->fam) family_free(f);
   for (auto& s : sv->slots) {
     if (s.st) cudaStreamSynchronize(s.st);
     drop_graphs(s);
