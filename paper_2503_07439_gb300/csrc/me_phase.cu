@@ -56,23 +56,10 @@ struct Masses {
   double m[4];
 };
 
+// RAMBO point from 4 NOUT uniforms: final momenta k[j][0..3] and the weight.
 template <int NOUT>
-__global__ void k_rambo(uint64_t seed, uint32_t stream, long long first, double rs, Masses ms, double w_massless, long n,
-                        double* __restrict__ p, double* __restrict__ wgt) {
-  const double* masses = ms.m;
-  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  constexpr int NEXT = NOUT + 2;
-  const unsigned long long idx = (unsigned long long)(first + i);
-  const uint32_t k0 = (uint32_t)(seed & 0xFFFFFFFFull), k1 = (uint32_t)(seed >> 32);
-  double u[4 * NOUT];
-#pragma unroll
-  for (int b = 0; b < 2 * NOUT; ++b) {
-    uint32_t c[4] = {(uint32_t)(idx & 0xFFFFFFFFull), (uint32_t)(idx >> 32), stream, (uint32_t)b};
-    philox4x32_10(c, k0, k1);
-    u[2 * b] = u01(c[0], c[1]);
-    u[2 * b + 1] = u01(c[2], c[3]);
-  }
+__device__ __forceinline__ void rambo_point(const double* u, double rs, const double* masses, double w_massless,
+                                            double k[][4], double& w_out) {
   // massless momenta
   double q[NOUT][4], Q[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
@@ -93,7 +80,6 @@ __global__ void k_rambo(uint64_t seed, uint32_t stream, long long first, double 
   const double M = sqrt(Q[0] * Q[0] - Q[1] * Q[1] - Q[2] * Q[2] - Q[3] * Q[3]);
   const double b[3] = {-Q[1] / M, -Q[2] / M, -Q[3] / M};
   const double x = rs / M, g = Q[0] / M, a = 1.0 / (1.0 + g);
-  double k[NOUT][4];
 #pragma unroll
   for (int j = 0; j < NOUT; ++j) {
     const double bq = b[0] * q[j][1] + b[1] * q[j][2] + b[2] * q[j][3];
@@ -146,6 +132,27 @@ __global__ void k_rambo(uint64_t seed, uint32_t stream, long long first, double 
     for (int e = 0; e < 2 * NOUT - 3; ++e) pw *= sk / rs;
     w *= pw * prod * rs / sk2e;
   }
+  w_out = w;
+}
+
+template <int NOUT>
+__global__ void k_rambo(uint64_t seed, uint32_t stream, long long first, double rs, Masses ms, double w_massless, long n,
+                        double* __restrict__ p, double* __restrict__ wgt) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  constexpr int NEXT = NOUT + 2;
+  const unsigned long long idx = (unsigned long long)(first + i);
+  const uint32_t k0 = (uint32_t)(seed & 0xFFFFFFFFull), k1 = (uint32_t)(seed >> 32);
+  double u[4 * NOUT];
+#pragma unroll
+  for (int b = 0; b < 2 * NOUT; ++b) {
+    uint32_t c[4] = {(uint32_t)(idx & 0xFFFFFFFFull), (uint32_t)(idx >> 32), stream, (uint32_t)b};
+    philox4x32_10(c, k0, k1);
+    u[2 * b] = u01(c[0], c[1]);
+    u[2 * b + 1] = u01(c[2], c[3]);
+  }
+  double k[NOUT][4], w;
+  rambo_point<NOUT>(u, rs, ms.m, w_massless, k, w);
   // beams, then the outgoing momenta: p[comp][leg][n]
   const double hb = 0.5 * rs;
   const double beams[2][4] = {{hb, 0.0, 0.0, hb}, {hb, 0.0, 0.0, -hb}};
@@ -160,15 +167,26 @@ __global__ void k_rambo(uint64_t seed, uint32_t stream, long long first, double 
 }
 
 // ---------------------------------------------------------------- points in FKS variables
-// Real-emission points generated directly in the sector variables of the FKS
-// subtraction, with a density that samples the soft and collinear regions: the emitted
-// gluon's energy fraction xi flat (flat three-body phase space has density ~ xi there),
-// y_j = 1 - 2 v^2 with v uniform towards the sector's reference direction j (density
-// g(y) = 1 / (4 sqrt((1 - y) / 2))), the azimuth and the Born direction uniform; the
-// two sectors are channels of one multichannel density.  Uniforms u0..u5 of point i are
-// those of Philox blocks 0..2 at counter (i lo, i hi, stream, block).
+// Real-emission points from a multichannel density whose channels are the variables of the
+// two FKS sectors plus flat phase space (RAMBO).  u0 picks the channel: flat with share
+// kAlphaFlat, else one sector (equal shares).  A sector channel is flat in the emitted
+// gluon's energy fraction xi (flat three-body phase space has density ~ xi there) and
+// samples its cosine to the sector's reference direction as y_j = 1 - 2 v^2, v uniform in
+// (v_min, 1), 2 v_min^2 = kYCut (density g(y) = 1 / (4 v (1 - v_min)) ~ 1/sqrt(1 - y)),
+// azimuth and Born direction uniform.  The weight is the phase-space measure over the sum
+// of all channel densities at the point, 1 / (a_flat / w_RAMBO + sum_j a_j h_j): bounded
+// by w_RAMBO / a_flat where the sector channels are thin, and no sector channel comes
+// closer than kYCut to a collinear limit (the flat channel covers that region).
+// Uniforms: u0..u17 of point i from Philox blocks 0..8 at counter (i lo, i hi, stream,
+// block); the flat channel's RAMBO takes u6..u17.
+constexpr double kAlphaFlat = 0.25;
+constexpr double kYCut = 1e-6;
+
 __device__ __forceinline__ double coll_density(double y) {
-  return 1.0 / (4.0 * sqrt(fmax(0.0, 0.5 * (1.0 - y))));
+  const double vmin = sqrt(0.5 * kYCut);
+  const double omy = 1.0 - y;
+  if (!(omy >= kYCut)) return 0.0;
+  return 1.0 / (4.0 * sqrt(0.5 * omy) * (1.0 - vmin));
 }
 
 __device__ __forceinline__ void boost_vel(const double p[4], const double b[3], double out[4]) {
@@ -181,45 +199,55 @@ __device__ __forceinline__ void boost_vel(const double p[4], const double b[3], 
   for (int d = 0; d < 3; ++d) out[1 + d] = p[1 + d] + (g2 * bp + g * p[0]) * b[d];
 }
 
-// Initial-state sectors of 2 -> Q Qbar g (beams along +-z, Q mass `mass`): xi = xi_max u0,
-// y_j = 1 - 2 u1^2 w.r.t. beam j (j = 0 if u5 < 1/2: y = y_j along +z, else y = -y_j),
-// phi = 2 pi u2, the pair's rest-frame direction (2 u3 - 1, 2 pi u4); the pair recoils
-// against the gluon with mass^2 s (1 - xi).  dPhi_3 = dPhi_2(s) xi K dxi dy dphi,
-// K = s beta(s(1-xi)) / (64 pi^3 beta(s)): weight xi s beta(s(1-xi)) / (512 pi^4) x
-// xi_max 2 pi / ((g(y) + g(-y)) / 2).
-// Final-state sectors of massless 2 -> 3 (partner leg 2 if u0 < 1/2, else leg 3, along
-// (2 u1 - 1, 2 pi u2)): xi = u3, y_j = 1 - 2 u4^2 the gluon's cosine w.r.t. the partner,
-// phi = 2 pi u5 about it; the partner's energy sqrt(s)(1-xi)/(2 - xi(1-y_j)) leaves the
-// third parton massless.  Channel j has density 4 g(y_j) / (xi K_j) per unit dPhi_3,
-// K_j = s (1 - xi) / (16 pi^3 (2 - xi (1 - y_j))^2): weight 1 / sum_j 2 g(y_j) / (xi K_j).
+// Initial-state sectors of 2 -> Q Qbar g (beams j = 0 along +z, 1 along -z, Q mass
+// `mass`): xi = xi_max u1, v from u2, phi = 2 pi u3, the pair's rest-frame direction
+// (2 u4 - 1, 2 pi u5); the pair recoils against the gluon with mass^2 s (1 - xi).
+// dPhi_3 = dPhi_2(s) xi K dxi dy dphi, K = s beta(s(1-xi)) / (64 pi^3 beta(s)):
+// channel density h_j = 4 g(y_j) / (xi_max beta(s) xi K).
+// Final-state sectors of massless 2 -> 3 (partner leg 2 or 3, along (2 u1 - 1, 2 pi u2)):
+// xi = u3, v from u4, phi = 2 pi u5 about the partner; the partner's energy
+// sqrt(s)(1-xi)/(2 - xi(1-y_j)) leaves the third parton massless; channel density
+// h_j = 4 g(y_j) / (xi K_j), K_j = s (1 - xi) / (16 pi^3 (2 - xi (1 - y_j))^2).
 template <bool ISR>
-__global__ void k_fks_points(uint64_t seed, uint32_t stream, long long first, double rs, double mass, long n,
-                             double* __restrict__ p, double* __restrict__ wgt) {
+__global__ void k_fks_points(uint64_t seed, uint32_t stream, long long first, double rs, double mass, double w3_massless,
+                             long n, double* __restrict__ p, double* __restrict__ wgt) {
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const unsigned long long idx = (unsigned long long)(first + i);
   const uint32_t k0 = (uint32_t)(seed & 0xFFFFFFFFull), k1 = (uint32_t)(seed >> 32);
-  double u[6];
+  double u[18];
 #pragma unroll
-  for (int b = 0; b < 3; ++b) {
+  for (int b = 0; b < 9; ++b) {
     uint32_t c[4] = {(uint32_t)(idx & 0xFFFFFFFFull), (uint32_t)(idx >> 32), stream, (uint32_t)b};
     philox4x32_10(c, k0, k1);
     u[2 * b] = u01(c[0], c[1]);
     u[2 * b + 1] = u01(c[2], c[3]);
   }
   const double s = rs * rs;
+  const double a_f = kAlphaFlat, a_s = 0.5 * (1.0 - kAlphaFlat);
+  const bool flat = u[0] < a_f;
+  const int sec = u[0] < a_f + a_s ? 0 : 1;
+  const double vmin = sqrt(0.5 * kYCut);
+  const double masses[3] = {ISR ? mass : 0.0, ISR ? mass : 0.0, 0.0};
   double q[5][4];  // legs: beams, then 2, 3, 4 (gluon)
   const double hb = 0.5 * rs;
   q[0][0] = hb; q[0][1] = 0.0; q[0][2] = 0.0; q[0][3] = hb;
   q[1][0] = hb; q[1][1] = 0.0; q[1][2] = 0.0; q[1][3] = -hb;
-  double w;
-  if (ISR) {
+  if (flat) {
+    double k[3][4], wr;
+    rambo_point<3>(u + 6, rs, masses, w3_massless, k, wr);
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) q[2 + j][c] = k[j][c];
+  } else if (ISR) {
     const double ximax = 1.0 - 4.0 * mass * mass / s;
-    const double xi = ximax * u[0];
-    const double yj = 1.0 - 2.0 * u[1] * u[1];
-    const double y = u[5] < 0.5 ? yj : -yj;
+    const double xi = ximax * u[1];
+    const double v = vmin + (1.0 - vmin) * u[2];
+    const double yj = 1.0 - 2.0 * v * v;
+    const double y = sec == 0 ? yj : -yj;
     double sf, cf, sp2, cp2;
-    sincos(2.0 * M_PI * u[2], &sf, &cf);
+    sincos(2.0 * M_PI * u[3], &sf, &cf);
     const double ek = 0.5 * rs * xi;
     const double st = sqrt(fmax(0.0, (1.0 - y) * (1.0 + y)));
     q[4][0] = ek;
@@ -228,9 +256,9 @@ __global__ void k_fks_points(uint64_t seed, uint32_t stream, long long first, do
     q[4][3] = ek * y;
     const double Q0 = rs - ek, M2 = Q0 * Q0 - ek * ek, M = sqrt(M2);
     const double pstar = sqrt(fmax(0.0, 0.25 * M2 - mass * mass));
-    const double cp = 2.0 * u[3] - 1.0;
+    const double cp = 2.0 * u[4] - 1.0;
     const double sp = sqrt(fmax(0.0, (1.0 - cp) * (1.0 + cp)));
-    sincos(2.0 * M_PI * u[4], &sp2, &cp2);
+    sincos(2.0 * M_PI * u[5], &sp2, &cp2);
     const double nv[3] = {sp * cp2, sp * sp2, cp};
     const double e = 0.5 * M;
     const double p3[4] = {e, pstar * nv[0], pstar * nv[1], pstar * nv[2]};
@@ -238,12 +266,11 @@ __global__ void k_fks_points(uint64_t seed, uint32_t stream, long long first, do
     const double bvec[3] = {-q[4][1] / Q0, -q[4][2] / Q0, -q[4][3] / Q0};
     boost_vel(p3, bvec, q[2]);
     boost_vel(p4, bvec, q[3]);
-    const double beta = sqrt(fmax(0.0, 1.0 - 4.0 * mass * mass / (s * (1.0 - xi))));
-    const double dens = 0.5 * (coll_density(y) + coll_density(-y));
-    w = xi * s * beta / (512.0 * M_PI * M_PI * M_PI * M_PI) * ximax * 2.0 * M_PI / dens;
   } else {
-    const int partner = u[0] < 0.5 ? 2 : 3, other = 5 - partner;
-    const double cdir = 2.0 * u[1] - 1.0, xi = u[3], yj = 1.0 - 2.0 * u[4] * u[4];
+    const int partner = 2 + sec, other = 5 - partner;
+    const double cdir = 2.0 * u[1] - 1.0, xi = u[3];
+    const double v = vmin + (1.0 - vmin) * u[4];
+    const double yj = 1.0 - 2.0 * v * v;
     double spd, cpd, sf, cf;
     sincos(2.0 * M_PI * u[2], &spd, &cpd);
     sincos(2.0 * M_PI * u[5], &sf, &cf);
@@ -268,24 +295,43 @@ __global__ void k_fks_points(uint64_t seed, uint32_t stream, long long first, do
       q[4][1 + d] = ei * ni[d];
       q[other][1 + d] = -(ej * nj[d] + ei * ni[d]);
     }
-    // both channels' densities at this point, from its momenta
-    const double ig = 1.0 / sqrt(q[4][1] * q[4][1] + q[4][2] * q[4][2] + q[4][3] * q[4][3]);
-    double h = 0.0;
+  }
+  // every channel's density at this point, from its momenta
+  double h;
+  {
+    double kabs[3], sk = 0.0, prod = 1.0, sk2e = 0.0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      kabs[j] = sqrt(q[2 + j][1] * q[2 + j][1] + q[2 + j][2] * q[2 + j][2] + q[2 + j][3] * q[2 + j][3]);
+      sk += kabs[j];
+      prod *= kabs[j] / q[2 + j][0];
+      sk2e += kabs[j] * kabs[j] / q[2 + j][0];
+    }
+    const double wr = ISR ? w3_massless * (sk / rs) * (sk / rs) * (sk / rs) * prod * rs / sk2e : w3_massless;
+    h = a_f / wr;
+  }
+  const double ig = 1.0 / sqrt(q[4][1] * q[4][1] + q[4][2] * q[4][2] + q[4][3] * q[4][3]);
+  const double xi_pt = 2.0 * q[4][0] / rs;
+  if (ISR) {
+    const double ximax = 1.0 - 4.0 * mass * mass / s, beta = sqrt(1.0 - 4.0 * mass * mass / s);
+    const double K = s * sqrt(fmax(0.0, 1.0 - 4.0 * mass * mass / (s * (1.0 - xi_pt)))) / (64.0 * M_PI * M_PI * M_PI * beta);
+    const double cz = q[4][3] * ig;
+    h += a_s * 4.0 * (coll_density(cz) + coll_density(-cz)) / (ximax * beta * xi_pt * K);
+  } else {
 #pragma unroll
     for (int j = 2; j <= 3; ++j) {
       const double kn = sqrt(q[j][1] * q[j][1] + q[j][2] * q[j][2] + q[j][3] * q[j][3]);
       const double y = (q[4][1] * q[j][1] + q[4][2] * q[j][2] + q[4][3] * q[j][3]) * ig / kn;
-      const double d = 2.0 - xi * (1.0 - y);
-      const double K = s * (1.0 - xi) / (16.0 * M_PI * M_PI * M_PI * d * d);
-      h += 2.0 * coll_density(y) / (xi * K);
+      const double d = 2.0 - xi_pt * (1.0 - y);
+      const double K = s * (1.0 - xi_pt) / (16.0 * M_PI * M_PI * M_PI * d * d);
+      h += a_s * 4.0 * coll_density(y) / (xi_pt * K);
     }
-    w = 1.0 / h;
   }
 #pragma unroll
   for (int comp = 0; comp < 4; ++comp)
 #pragma unroll
     for (int l = 0; l < 5; ++l) p[(comp * 5 + l) * n + i] = q[l][comp];
-  if (wgt) wgt[i] = w;
+  if (wgt) wgt[i] = 1.0 / h;
 }
 
 // ---------------------------------------------------------------- unweighting
@@ -496,10 +542,12 @@ extern "C" int me_generate_fks(me_handle* h, uint64_t seed, uint32_t stream, int
   if (!(2.0 * mass < sqrt_s)) return me_internal_fail(ME_ERR_ARG, "me_generate_fks: sqrt_s below the final-state masses");
   const int threads = 128;
   const unsigned blocks = (unsigned)((n + threads - 1) / threads);
+  // massless three-body volume (2 pi)^(4-3n) (pi/2)^(n-1) s^(n-2) / ((n-1)! (n-2)!) = s / (256 pi^3)
+  const double w3 = sqrt_s * sqrt_s / (256.0 * M_PI * M_PI * M_PI);
   if (isr)
-    k_fks_points<true><<<blocks, threads, 0, st>>>(seed, stream, first_point, sqrt_s, mass, n, momenta, ps_weights);
+    k_fks_points<true><<<blocks, threads, 0, st>>>(seed, stream, first_point, sqrt_s, mass, w3, n, momenta, ps_weights);
   else
-    k_fks_points<false><<<blocks, threads, 0, st>>>(seed, stream, first_point, sqrt_s, mass, n, momenta, ps_weights);
+    k_fks_points<false><<<blocks, threads, 0, st>>>(seed, stream, first_point, sqrt_s, mass, w3, n, momenta, ps_weights);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return me_internal_fail(ME_ERR_CUDA, (std::string("me_generate_fks: ") + cudaGetErrorString(e)).c_str());
   return ME_OK;

@@ -347,66 +347,105 @@ def fsr_emission_points(sqrt_s: float, cos_dir: np.ndarray, phi_dir: np.ndarray,
     return np.ascontiguousarray(out)
 
 
+FKS_ALPHA_FLAT = 0.25  # share of the flat (RAMBO) channel in fks_points
+FKS_Y_CUT = 1e-6       # the FKS channels sample 1 - y_j >= FKS_Y_CUT (the flat channel covers all)
+
+
 def _coll_density(y: np.ndarray) -> np.ndarray:
-    """Density in y of y = 1 - 2 v^2, v uniform in (0, 1): 1 / (4 sqrt((1 - y) / 2))."""
-    v = np.sqrt(np.maximum(0.0, 0.5 * (1.0 - y)))
-    with np.errstate(divide="ignore"):
-        return 1.0 / (4.0 * v)
+    """Density in y of y = 1 - 2 v^2 with v uniform in (v_min, 1), 2 v_min^2 = FKS_Y_CUT:
+    1 / (4 v (1 - v_min)) for 1 - y >= FKS_Y_CUT, else 0."""
+    vmin = math.sqrt(0.5 * FKS_Y_CUT)
+    omy = 1.0 - y
+    v = np.sqrt(np.maximum(0.0, 0.5 * omy))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        g = 1.0 / (4.0 * v * (1.0 - vmin))
+    return np.where(omy >= FKS_Y_CUT, g, 0.0)
+
+
+def rambo_weight(sqrt_s: float, masses, p_out: np.ndarray) -> np.ndarray:
+    """The (massive) RAMBO weight of final momenta p_out[4][n][N] (rambo_massive's weight
+    as a function of the point): 1 / the density RAMBO generates it with."""
+    n = len(masses)
+    s = sqrt_s * sqrt_s
+    w0 = (2 * math.pi) ** (4 - 3 * n) * (0.5 * math.pi) ** (n - 1) * s ** (n - 2) / (
+        math.factorial(n - 1) * math.factorial(n - 2))
+    if not np.any(np.asarray(masses)):
+        return np.full(p_out.shape[2], w0)
+    kabs = np.sqrt((p_out[1:] ** 2).sum(axis=0))
+    e = p_out[0]
+    return w0 * (kabs.sum(axis=0) / sqrt_s) ** (2 * n - 3) * np.prod(kabs / e, axis=0) \
+        * sqrt_s / (kabs * kabs / e).sum(axis=0)
 
 
 def fks_points(process: str, n: int, seed: int, first_point: int = 0, stream: int = 0,
                sqrt_s: float | None = None) -> Batch:
-    """Phase-space points of a real-emission process generated directly in FKS variables
-    (the sector parametrisation of the subtraction), with a density that samples the soft
-    and collinear regions: flat in the emitted gluon's energy fraction xi (flat three-body
-    phase space has density ~ xi there), y_j = 1 - 2 v^2 with v uniform towards the
-    sector's reference direction j (density ~ 1/sqrt(1 - y_j)), the azimuth and the Born
-    direction uniform; both sectors are channels of one multichannel density, so each
-    weight is the phase-space measure over the sum of the channel densities.
+    """Phase-space points of a real-emission process sampled with a multichannel density
+    whose channels are the variables of its FKS sectors plus flat phase space.
 
-    Initial-state sectors (gg_ttg, uu_ttg; top mass MT): uniforms u0..u5 of the point
-    give xi = xi_max u0 (xi_max = 1 - 4 m^2 / s), v = u1, phi = 2 pi u2, the heavy pair's
-    rest-frame direction (2 u3 - 1, 2 pi u4) and the beam j (0 if u5 < 1/2: y = y_j is the
-    gluon's cosine w.r.t. +z; else y = -y_j).  dPhi_3 = dPhi_2(s) xi K dxi dy dphi with
-    dPhi_2(s) = beta(s) / (8 pi) dOmega* / (4 pi) and K = s beta(s(1-xi)) / (64 pi^3 beta(s)),
-    so the weight is xi s beta(s(1 - xi)) / (512 pi^4) xi_max 2 pi / ((g(y) + g(-y)) / 2),
-    g the density of y = 1 - 2 v^2.
-    Final-state sectors (ee_uug, massless): u0 chooses the partner (leg 2 if u0 < 1/2,
-    else leg 3), (2 u1 - 1, 2 pi u2) its direction, xi = u3, y_j = 1 - 2 u4^2 the gluon's
-    cosine w.r.t. the partner, phi = 2 pi u5; each sector's parametrisation covers the
-    space once, dPhi_3 = (1/(8 pi)) (dOmega/(4 pi)) xi K_j dxi dy dphi with
-    K_j = s (1 - xi) / (16 pi^3 (2 - xi (1 - y_j))^2), so channel j has density
-    4 g(y_j) / (xi K_j) per unit dPhi_3 and the weight is 1 / sum_j (2 g(y_j) / (xi K_j)),
-    y_j the gluon's cosine w.r.t. leg j."""
+    Channels (u0 picks one): flat RAMBO with share FKS_ALPHA_FLAT; otherwise one of the two
+    sectors, equal shares.  A sector channel is flat in the emitted gluon's energy fraction
+    xi (flat three-body phase space has density ~ xi there) and samples its cosine to the
+    sector's reference direction as y_j = 1 - 2 v^2, v uniform in (v_min, 1) with
+    2 v_min^2 = FKS_Y_CUT (density ~ 1/sqrt(1 - y_j)), azimuth and Born direction uniform.
+    The weight of a point is the phase-space measure over the summed channel densities at
+    that point: 1 / (a_flat / w_RAMBO + sum_j a_j h_j), so it stays bounded by
+    w_RAMBO / a_flat wherever the sector channels are thin (a hard gluon back to back
+    with collinear partons), and no point closer than FKS_Y_CUT to a collinear limit
+    comes from a sector channel (the flat channel still covers that region).
+
+    Initial-state sectors (gg_ttg, uu_ttg; beams j = 0 along +z, 1 along -z; top mass
+    MT): xi = xi_max u1 (xi_max = 1 - 4 m^2 / s), v from u2, phi = 2 pi u3, the heavy
+    pair's rest-frame direction (2 u4 - 1, 2 pi u5); dPhi_3 = dPhi_2(s) xi K dxi dy dphi
+    with dPhi_2(s) = beta(s)/(8 pi) dOmega*/(4 pi), K = s beta(s(1-xi)) / (64 pi^3 beta(s)),
+    so h_j = 4 g(y_j) / (xi_max beta(s) xi K).
+    Final-state sectors (ee_uug, massless): partner leg 2 or 3, its direction
+    (2 u1 - 1, 2 pi u2), xi = u3, v from u4, phi = 2 pi u5 about it; each sector's
+    parametrisation covers the space once, dPhi_3 = (1/(8 pi)) (dOmega/(4 pi)) xi K_j dxi dy
+    dphi with K_j = s (1 - xi) / (16 pi^3 (2 - xi (1 - y_j))^2), so h_j = 4 g(y_j)/(xi K_j).
+    The flat channel is RAMBO (rambo_massive) on uniforms u6..u17."""
     rs = sqrt_s if sqrt_s is not None else {"ee_uug": 100.0, "gg_ttg": 1000.0, "uu_ttg": 1000.0}[process]
     s = rs * rs
-    u = uniforms(seed, stream, n, 6, first_point)
-    if process in ("gg_ttg", "uu_ttg"):
-        ximax = 1.0 - 4.0 * MT * MT / s
-        xi = ximax * u[0]
-        yj = 1.0 - 2.0 * u[1] * u[1]
-        y = np.where(u[5] < 0.5, yj, -yj)
-        p = emission_points(rs, MT, xi, y, 2.0 * math.pi * u[2], 2.0 * u[3] - 1.0, 2.0 * math.pi * u[4])
-        beta = np.sqrt(np.maximum(0.0, 1.0 - 4.0 * MT * MT / (s * (1.0 - xi))))
-        dens = 0.5 * (_coll_density(y) + _coll_density(-y))
-        w = xi * s * beta / (512.0 * math.pi ** 4) * ximax * 2.0 * math.pi / dens
-        return Batch(process, rs, p, w)
-    if process != "ee_uug":
+    isr = process in ("gg_ttg", "uu_ttg")
+    if not isr and process != "ee_uug":
         raise ValueError(f"{process} has no FKS sectors")
-    cdir, pdir, xi = 2.0 * u[1] - 1.0, 2.0 * math.pi * u[2], u[3]
-    yj, phi = 1.0 - 2.0 * u[4] * u[4], 2.0 * math.pi * u[5]
+    masses = [MT, MT, 0.0] if isr else [0.0, 0.0, 0.0]
+    u = uniforms(seed, stream, n, 18, first_point)
+    vmin = math.sqrt(0.5 * FKS_Y_CUT)
+    a_f = FKS_ALPHA_FLAT
+    a_s = 0.5 * (1.0 - a_f)
+    flat = u[0] < a_f
+    sec = np.where(u[0] < a_f + a_s, 0, 1)
+    v = vmin + (1.0 - vmin) * u[2] if isr else vmin + (1.0 - vmin) * u[4]
+    yj = 1.0 - 2.0 * v * v
     p = np.empty((4, 5, n))
-    for partner, sel in ((2, u[0] < 0.5), (3, u[0] >= 0.5)):
-        if sel.any():
-            p[:, :, sel] = fsr_emission_points(rs, cdir[sel], pdir[sel], xi[sel], yj[sel], phi[sel], partner)
+    if isr:
+        ximax = 1.0 - 4.0 * MT * MT / s
+        xi = ximax * u[1]
+        y = np.where(sec == 0, yj, -yj)
+        p[:] = emission_points(rs, MT, xi, y, 2.0 * math.pi * u[3], 2.0 * u[4] - 1.0, 2.0 * math.pi * u[5])
+    else:
+        cdir, pdir, xi, phi = 2.0 * u[1] - 1.0, 2.0 * math.pi * u[2], u[3], 2.0 * math.pi * u[5]
+        for partner, sel in ((2, sec == 0), (3, sec == 1)):
+            if sel.any():
+                p[:, :, sel] = fsr_emission_points(rs, cdir[sel], pdir[sel], xi[sel], yj[sel], phi[sel], partner)
+    if flat.any():
+        pf, _ = rambo_massive(rs, masses, u[6:18][:, flat])
+        p[:, :, flat] = with_beams(rs, pf)
+    # every channel's density at every point, from its momenta
     kg = p[1:, 4]
     ng = kg / np.sqrt((kg * kg).sum(axis=0))
-    h = np.zeros(n)
-    for j in (2, 3):
-        kj = p[1:, j]
-        y = (ng * kj).sum(axis=0) / np.sqrt((kj * kj).sum(axis=0))
-        K = s * (1.0 - xi) / (16.0 * math.pi ** 3 * (2.0 - xi * (1.0 - y)) ** 2)
-        h += 2.0 * _coll_density(y) / (xi * K)
-    with np.errstate(divide="ignore"):
-        w = 1.0 / h
-    return Batch(process, rs, np.ascontiguousarray(p), w)
+    xi_pt = 2.0 * p[0, 4] / rs
+    h = a_f / rambo_weight(rs, masses, p[:, 2:])
+    if isr:
+        ximax = 1.0 - 4.0 * MT * MT / s
+        beta = math.sqrt(1.0 - 4.0 * MT * MT / s)
+        K = s * np.sqrt(np.maximum(0.0, 1.0 - 4.0 * MT * MT / (s * (1.0 - xi_pt)))) / (64.0 * math.pi ** 3 * beta)
+        for sign in (1.0, -1.0):
+            h = h + a_s * 4.0 * _coll_density(sign * ng[2]) / (ximax * beta * xi_pt * K)
+    else:
+        for j in (2, 3):
+            kj = p[1:, j]
+            y = (ng * kj).sum(axis=0) / np.sqrt((kj * kj).sum(axis=0))
+            K = s * (1.0 - xi_pt) / (16.0 * math.pi ** 3 * (2.0 - xi_pt * (1.0 - y)) ** 2)
+            h = h + a_s * 4.0 * _coll_density(y) / (xi_pt * K)
+    return Batch(process, rs, np.ascontiguousarray(p), 1.0 / h)

@@ -147,53 +147,63 @@ def test_approach_points_labels():
 
 
 def test_fks_points_invert_to_their_sector_variables():
-    """Points generated in FKS variables map back, through the oracle's inverse sector
-    maps, to the variables they were built from, and are on shell and balanced."""
+    """Points from a sector channel map back, through the oracle's inverse sector maps, to
+    the variables they were built from; every point is on shell and balanced."""
     from oracle import fks
     from oracle.matrix_element import to_points
-    n = 512
+    n = 2048
+    a_f, a_s = synth.FKS_ALPHA_FLAT, 0.5 * (1.0 - synth.FKS_ALPHA_FLAT)
+    vmin = math.sqrt(0.5 * synth.FKS_Y_CUT)
     b = synth.fks_points("gg_ttg", n, 3)
-    u = synth.uniforms(3, 0, n, 6)
+    u = synth.uniforms(3, 0, n, 18)
     k = to_points(b.p)
     ximax = 1.0 - 4.0 * synth.MT ** 2 / 1e6
-    kin = fks.isr_map(k, 4, 0, synth.MT)
-    np.testing.assert_allclose(kin.xi, ximax * u[0], rtol=1e-12)
-    yj = 1.0 - 2.0 * u[1] ** 2
-    np.testing.assert_allclose(kin.y, np.where(u[5] < 0.5, yj, -yj), atol=1e-12)
+    for beam, sel in ((0, (u[0] >= a_f) & (u[0] < a_f + a_s)), (1, u[0] >= a_f + a_s)):
+        kin = fks.isr_map(k[sel], 4, beam, synth.MT)
+        np.testing.assert_allclose(kin.xi, ximax * u[1][sel], rtol=1e-12)
+        v = vmin + (1.0 - vmin) * u[2][sel]
+        np.testing.assert_allclose(kin.y, 1.0 - 2.0 * v * v, atol=1e-12)
     _check_momenta(b.p[:, 2:], [synth.MT, synth.MT, 0.0], 1000.0)
     e = synth.fks_points("ee_uug", n, 3)
-    u = synth.uniforms(3, 0, n, 6)
     ke = to_points(e.p)
-    for partner in (2, 3):
-        sel = (u[0] < 0.5) if partner == 2 else (u[0] >= 0.5)
+    for partner, sel in ((2, (u[0] >= a_f) & (u[0] < a_f + a_s)), (3, u[0] >= a_f + a_s)):
         kin = fks.fsr_map(ke[sel], 4, partner, 5 - partner)
         np.testing.assert_allclose(kin.xi, u[3][sel], rtol=1e-12)
-        np.testing.assert_allclose(kin.y, 1.0 - 2.0 * u[4][sel] ** 2, atol=1e-12)
+        v = vmin + (1.0 - vmin) * u[4][sel]
+        np.testing.assert_allclose(kin.y, 1.0 - 2.0 * v * v, atol=1e-12)
     _check_momenta(e.p[:, 2:], [0.0, 0.0, 0.0], 100.0)
 
 
 def test_fks_point_weights_are_the_oracle_jacobians():
-    """Each weight is the phase-space measure over the generator density, with the sector
-    Jacobians K of the oracle's maps (pinned there by quadrature and the RAMBO volumes):
-    initial state dPhi_2(s) xi K x (xi_max 2 pi / ((g(y) + g(-y)) / 2)); final state
-    1 / sum_j 2 g(y_j) / (xi K_j), g(y) = 1 / (4 sqrt((1 - y)/2))."""
+    """Each weight is the phase-space measure over the summed channel densities, with the
+    sector Jacobians K of the oracle's maps (pinned there by quadrature and the RAMBO
+    volumes) and the RAMBO weight of the point: 1 / (a_flat / w_RAMBO + sum_j a_j h_j),
+    h_j = 4 g(y_j) / (xi_max beta(s) xi K) (initial state, dPhi_2(s) = beta(s)/(8 pi) x
+    dOmega*/(4 pi)) or 4 g(y_j) / (xi K_j) (final state), g(y) = 1 / (4 v (1 - v_min)),
+    v = sqrt((1 - y)/2), for 1 - y >= the cut."""
     from oracle import fks
     from oracle.matrix_element import to_points
-    n = 512
-    g = lambda y: 1.0 / (4.0 * np.sqrt(0.5 * (1.0 - y)))
-    b = synth.fks_points("uu_ttg", n, 8)
-    k = to_points(b.p)
-    kin = fks.isr_map(k, 4, 0, synth.MT)
+    n = 1024
+    a_f, a_s = synth.FKS_ALPHA_FLAT, 0.5 * (1.0 - synth.FKS_ALPHA_FLAT)
+    vmin = math.sqrt(0.5 * synth.FKS_Y_CUT)
+    g = lambda y: np.where(1 - y >= synth.FKS_Y_CUT, 1.0 / (4.0 * np.sqrt(0.5 * (1.0 - y)) * (1.0 - vmin)), 0.0)
     s = 1e6
     beta = math.sqrt(1.0 - 4.0 * synth.MT ** 2 / s)
     ximax = 1.0 - 4.0 * synth.MT ** 2 / s
-    ref = beta / (8 * math.pi) * kin.xi * kin.K * ximax * 2 * math.pi / (0.5 * (g(kin.y) + g(-kin.y)))
+    b = synth.fks_points("uu_ttg", n, 8)
+    k = to_points(b.p)
+    h = a_f / synth.rambo_weight(1000.0, [synth.MT, synth.MT, 0.0], b.p[:, 2:])
+    for beam in (0, 1):
+        kin = fks.isr_map(k, 4, beam, synth.MT)
+        h = h + a_s * 4.0 * g(kin.y) / (ximax * beta * kin.xi * kin.K)
     # (the map recovers y from the momenta: 1 - |y| near 0 carries the momenta's rounding
     # relative to 1 - |y|, hence 1e-10 rather than 1e-12; a wrong Jacobian is off by O(1))
-    np.testing.assert_allclose(b.wgt, ref, rtol=1e-10)
+    np.testing.assert_allclose(b.wgt, 1.0 / h, rtol=1e-10)
     e = synth.fks_points("ee_uug", n, 8)
     ke = to_points(e.p)
-    h = sum(2.0 * g(kk.y) / (kk.xi * kk.K) for kk in (fks.fsr_map(ke, 4, 2, 3), fks.fsr_map(ke, 4, 3, 2)))
+    h = a_f / (100.0 ** 2 / (256 * math.pi ** 3))
+    for kk in (fks.fsr_map(ke, 4, 2, 3), fks.fsr_map(ke, 4, 3, 2)):
+        h = h + a_s * 4.0 * g(kk.y) / (kk.xi * kk.K)
     np.testing.assert_allclose(e.wgt, 1.0 / h, rtol=1e-10)
 
 
