@@ -38,8 +38,10 @@ N_POINTS = 1 << 20
 METRIC = "NLO real-minus-counterterm events/s (gg->ttg, FKS, 1 GB300)"
 UNIT = "events/s"
 WORKLOAD = ("gg->ttg real-emission minus FKS soft/collinear counterterms, sqrt(s)=1 TeV, m_t=173, "
-            "2^20 flat massive-RAMBO points, mixed precision (fp32 amplitudes + fp64 rescue)")
+            "2^20 flat massive-RAMBO points, mixed precision (fp32 amplitudes; fp64 re-evaluation of the "
+            "flagged points' real-emission blocks and counterterm Borns that their tolerance needs)")
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+NB_REAL = {"gg_ttg": 4, "uu_ttg": 2, "ee_uug": 2}  # live helicity blocks of the real emission
 FP64_PER_SM_CLK = 2  # DFMA thread-ops per SM per clock (ncu: ..._op_dfma_pred_on.avg.peak_sustained)
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu --set full
 # capture of each kernel (summaries in profiles/), with the hash of the kernel sources they
@@ -76,21 +78,23 @@ def traffic_per_launch(workload: str, stage: str, points: int):
     return t["bytes"] * points / t["points"]  # scales with the points of the launch
 WORKLOADS = {
     "c2": {"calls": [("gg_ttg", "real_subtracted", SEED)], "n": N_POINTS, "metric": METRIC, "workload": WORKLOAD,
-           "kernel": "k_real_sub<gg_ttg, float>", "l2": "inputs 168 MB per batch > 129 MB L2 (no flush)"},
+           "kernels": {"gg_ttg": "k_real_sub<gg_ttg, float>"},
+           "l2": "inputs 168 MB per batch > 129 MB L2 (no flush)"},
     "c0": {"calls": [("ee_uu", "nbody_nlo", 1), ("ee_uug", "real_subtracted", 2)], "n": 65536,
            "metric": "e+e- -> u ubar NLO events/s (n-body + real-minus-counterterm, 1 GB300)",
            "workload": "e+e- -> u ubar (g) at sqrt(s)=100 GeV: 65536 Born points (n-body NLO weight) + 65536 "
                        "real points (FKS final-state sectors), mixed precision",
-           "kernel": "k_tree<ee_uu, float>", "l2": "inputs 15 MB (< L2; compute-bound kernels)"},
+           "kernels": {"ee_uu": "k_tree<ee_uu, float>", "ee_uug": "k_real_sub<ee_uug, float>"},
+           "l2": "inputs 15 MB (< L2; compute-bound kernels)"},
     "c1": {"calls": [("gg_tt", "born", 3)], "n": N_POINTS,
            "metric": "gg -> t tbar LO events/s (1 GB300)",
            "workload": "gg -> t tbar LO, sqrt(s_hat) ~ U[400,2000] GeV, 2^20 points, float32 amplitudes",
-           "kernel": "k_tree<gg_tt, float>", "l2": "inputs 134 MB per batch > 129 MB L2 (no flush)"},
+           "kernels": {"gg_tt": "k_tree<gg_tt, float>"}, "l2": "inputs 134 MB per batch > 129 MB L2 (no flush)"},
     "c3": {"calls": [("gg_ttgg", "born", 6)], "n": 1 << 18,
            "metric": "gg -> t tbar g g tree events/s (tensor-core colour sum, 1 GB300)",
            "workload": "gg -> t tbar g g tree at sqrt(s)=2 TeV, 2^18 flat massive-RAMBO points, float32 "
                        "amplitudes, 24-flow colour sum on tensor cores (bf16 x3 split, f32 accumulate)",
-           "kernel": "k_tree_tc4 (gg_ttgg, float; four lanes per event, mma.sync bf16 colour sum)",
+           "kernels": {"gg_ttgg": "k_tree_tc4 (gg_ttgg, float; four lanes per event, mma.sync bf16 colour sum)"},
            "l2": "inputs 50 MB (< L2; compute-bound kernel)"},
 }
 
@@ -189,13 +193,35 @@ def _oracle_chunk(args):
     return n, time.perf_counter() - t0
 
 
-def cpu_baseline(points_per_worker: int = 8192, max_workers: int = 8):
-    workers = max(1, min(max_workers, os.cpu_count() or 1))
+def _one_thread_per_worker():
+    """numpy in every spawned worker runs single-threaded (one core each): the
+    environment is set before the pool starts, since a spawned child imports numpy
+    before any initializer runs."""
+    keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    old = {k: os.environ.get(k) for k in keys}
+    for k in keys:
+        os.environ[k] = "1"
+    return old
+
+
+def _restore_env(old):
+    for k, v in old.items():
+        if v is None:
+            os.environ.pop(k, None)
+        else:
+            os.environ[k] = v
+
+
+def cpu_baseline(points_per_worker: int = 8192):
+    """The float64 oracle on every host core (one spawned process per core)."""
+    workers = max(1, os.cpu_count() or 1)
     ctx = mp.get_context("spawn")
+    old = _one_thread_per_worker()
     t0 = time.perf_counter()
     with ctx.Pool(workers) as pool:
         res = pool.map(_oracle_chunk, [(i * points_per_worker, points_per_worker) for i in range(workers)])
     wall = time.perf_counter() - t0
+    _restore_env(old)
     n = sum(r[0] for r in res)
     busy = max(r[1] for r in res)
     return {"value": n / busy, "unit": UNIT, "cores": workers, "kind": "oracle",
@@ -220,22 +246,61 @@ SERVE_KIND = {"ee_uu": "born", "ee_uug": "real_subtracted", "gg_tt": "born", "gg
               "gg_ttgg": "born", "uu_ttg": "real_subtracted"}
 
 
+def _warm_server(me, srv, n_slots):
+    """The handles of every slot, and the lane layouts of every process and batch-size class
+    the stream holds (256 .. 65536 points), tuned one request at a time."""
+    import synth
+    for proc in SERVE_KIND:
+        for size in (256, 512, 1024, 2048, 4096, 8192, 16384, 32768, 65536):
+            srv.poll(srv.submit(proc, SERVE_KIND[proc], synth.flat_points(proc, size, 99).p))
+        b = synth.flat_points(proc, 4096, 99)
+        ts = [srv.submit(proc, SERVE_KIND[proc], b.p) for _ in range(2 * n_slots)]
+        for t in ts:
+            srv.poll(t)
+
+
+def _run_load(srv, reqs, data, total, capacity, load):
+    """Live arrivals at `load` x capacity (events/s); latency submit -> completion."""
+    n_requests = len(reqs)
+    rate = load * capacity / (total / n_requests)  # requests per second
+    arrivals = [r["arrival"] / rate for r in reqs]
+    lat = [0.0] * n_requests
+    tickets = [None] * n_requests
+    done = threading.Event()
+
+    def poller():
+        for i in range(n_requests):
+            while tickets[i] is None:
+                time.sleep(1e-4)
+            lat[i] = srv.poll(tickets[i])["t_total_us"] * 1e-3
+        done.set()
+
+    th = threading.Thread(target=poller)
+    th.start()
+    start = time.perf_counter()
+    for i, (r, d) in enumerate(zip(reqs, data)):
+        while time.perf_counter() - start < arrivals[i]:
+            time.sleep(5e-5)
+        tickets[i] = srv.submit(r["process"], SERVE_KIND[r["process"]], d.p, d.wgt)
+    done.wait()
+    th.join()
+    return arrivals, {"offered_load": load, "events_per_s": total / (time.perf_counter() - start),
+                      "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))}
+
+
 def serving_metrics(me, n_requests: int = 400, loads=(0.5, 0.9, 1.2), seed: int = 7, device: int = 0,
                     n_slots: int = 8):
     """Served mixed stream: Poisson arrivals scaled to each offered load x the measured
     capacity, sizes log-uniform in [256, 65536], processes uniform; latency submit ->
-    completion.  Compared with the plain FP64 path run one batch at a time on the same
-    arrivals (its service times are measured once, the queue is replayed per load)."""
+    completion.  The slots with replayed CUDA graphs (default server) and the persistent
+    family kernels run the same arrivals; the plain FP64 path runs them live, one batch at
+    a time."""
     import synth
     reqs = synth.mixed_stream(n_requests, seed)
     data = [synth.flat_points(r["process"], r["n"], r["seed"]) for r in reqs]
     total = sum(r["n"] for r in reqs)
     srv = me.Server(device=device, n_slots=n_slots, precision=me.ME_PREC_MIXED)
-    for proc in SERVE_KIND:  # warm-up: handles of every slot and lane-layout tuning
-        b = synth.flat_points(proc, 4096, 99)
-        ts = [srv.submit(proc, SERVE_KIND[proc], b.p) for _ in range(2 * n_slots)]
-        for t in ts:
-            srv.poll(t)
+    _warm_server(me, srv, n_slots)
     t0 = time.perf_counter()
     ts = [srv.submit(r["process"], SERVE_KIND[r["process"]], d.p, d.wgt) for r, d in zip(reqs, data)]
     for t in ts:
@@ -243,60 +308,60 @@ def serving_metrics(me, n_requests: int = 400, loads=(0.5, 0.9, 1.2), seed: int 
     capacity = total / (time.perf_counter() - t0)
 
     def run_load(load):
-        rate = load * capacity / (total / n_requests)  # requests per second
-        arrivals = [r["arrival"] / rate for r in reqs]
-        lat = [0.0] * n_requests
-        tickets = [None] * n_requests
-        done = threading.Event()
-
-        def poller():
-            for i in range(n_requests):
-                while tickets[i] is None:
-                    time.sleep(1e-4)
-                lat[i] = srv.poll(tickets[i])["t_total_us"] * 1e-3
-            done.set()
-
-        th = threading.Thread(target=poller)
-        th.start()
-        start = time.perf_counter()
-        for i, (r, d) in enumerate(zip(reqs, data)):
-            while time.perf_counter() - start < arrivals[i]:
-                time.sleep(5e-5)
-            tickets[i] = srv.submit(r["process"], SERVE_KIND[r["process"]], d.p, d.wgt)
-        done.wait()
-        th.join()
-        return arrivals, {"offered_load": load, "events_per_s": total / (time.perf_counter() - start),
-                          "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))}
+        return _run_load(srv, reqs, data, total, capacity, load)
 
     runs = [run_load(x) for x in loads]
     gstats = srv.stats()
     srv.close()
-    # plain FP64 path, one batch at a time: service time of every request, then the
-    # same arrival times replayed through a single-server queue per load
+    # persistent family kernels (gg_ttgg on the slots), same arrivals at the same rates
+    psrv = me.Server(device=device, n_slots=n_slots, precision=me.ME_PREC_MIXED, persistent=True)
+    _warm_server(me, psrv, n_slots)
+    t0 = time.perf_counter()
+    ts = [psrv.submit(r["process"], SERVE_KIND[r["process"]], d.p, d.wgt) for r, d in zip(reqs, data)]
+    for t in ts:
+        psrv.poll(t)
+    pcap = total / (time.perf_counter() - t0)
+    pruns = [_run_load(psrv, reqs, data, total, capacity, x)[1] for x in loads]
+    pstats = psrv.stats()
+    psrv.close()
+    # the plain FP64 path, one batch at a time (no slots, no graphs), on the same arrivals,
+    # live: each request starts when it has arrived and the previous one has finished;
+    # latency = finish - arrival
     hs = {p: me.Handle(p, precision=me.ME_PREC_FP64, device=device) for p in SERVE_KIND}
-    for p, h in hs.items():
-        (h.born if SERVE_KIND[p] == "born" else h.real_subtracted)(synth.flat_points(p, 1024, 98).p)
-    svc = []
-    for r, d in zip(reqs, data):
-        h = hs[r["process"]]
-        f = h.born if SERVE_KIND[r["process"]] == "born" else h.real_subtracted
-        t1 = time.perf_counter()
-        f(d.p, d.wgt)
-        svc.append(time.perf_counter() - t1)
+    for p, h in hs.items():  # lane layouts of every batch-size class of the stream
+        f = h.born if SERVE_KIND[p] == "born" else h.real_subtracted
+        for size in (256, 512, 1024, 2048, 4096, 8192, 16384, 32768, 65536):
+            f(synth.flat_points(p, size, 98).p)
+    out = []
+    busy = 0.0
+    for arrivals, m in runs:
+        lat64 = []
+        start = time.perf_counter()
+        for a, r, d in zip(arrivals, reqs, data):
+            while time.perf_counter() - start < a:
+                time.sleep(5e-5)
+            h = hs[r["process"]]
+            f = h.born if SERVE_KIND[r["process"]] == "born" else h.real_subtracted
+            t1 = time.perf_counter()
+            f(d.p, d.wgt)
+            t2 = time.perf_counter()
+            busy += t2 - t1
+            lat64.append(1e3 * (t2 - start - a))
+        m["fp64_per_batch"] = {"events_per_s": total / (time.perf_counter() - start),
+                               "p50_ms": float(np.percentile(lat64, 50)), "p99_ms": float(np.percentile(lat64, 99)),
+                               "measured": "live, same arrival times, one batch at a time"}
+        out.append(m)
     for h in hs.values():
         h.close()
-    out = []
-    for arrivals, m in runs:
-        clock, lat64 = 0.0, []
-        for a, t in zip(arrivals, svc):
-            clock = max(clock, a) + t
-            lat64.append(1e3 * (clock - a))
-        m["fp64_per_batch"] = {"events_per_s": total / clock, "p50_ms": float(np.percentile(lat64, 50)),
-                               "p99_ms": float(np.percentile(lat64, 99))}
-        out.append(m)
     return {"requests": n_requests, "points": total, "slots": n_slots, "capacity_events_per_s": capacity,
-            "fp64_per_batch_events_per_s_busy": total / sum(svc), "loads": out,
-            "graph_replays": gstats["graph_runs"], "ordinary_runs": gstats["plain_runs"]}
+            "fp64_per_batch_events_per_s_busy": total * len(runs) / busy, "loads": out,
+            "graph_replays": gstats["graph_runs"], "ordinary_runs": gstats["plain_runs"],
+            "persistent": {"capacity_events_per_s": pcap, "loads": pruns,
+                           "kernel_launches": pstats["persistent_launches"],
+                           "idle_timeouts": pstats["persistent_idle_timeouts"],
+                           "requests_on_persistent_kernels": pstats["persistent_requests"],
+                           "note": "ee/gg/uu families on one persistent kernel each (half the SMs each), "
+                                   "gg_ttgg on the slots; arrival rates as for the graph-replay server"}}
 
 
 def _reference_chunk(args):
@@ -329,10 +394,11 @@ def run_reference(args):
     if rank != 0:
         return
     wl = WORKLOADS[args.workload]
-    workers = max(1, min(8, os.cpu_count() or 1))
-    per_worker = {"c2": 1024, "c0": 4096, "c1": 4096, "c3": 4}[args.workload]
+    workers = max(1, os.cpu_count() or 1)
+    per_worker = {"c2": 1024, "c0": 4096, "c1": 4096, "c3": 16}[args.workload]
     ctx = mp.get_context("spawn")
     t_total, points = 0.0, 0
+    old_env = _one_thread_per_worker()
     with ctx.Pool(workers) as pool:
         for s in range(args.warmup + args.steps):
             jobs = [(proc, entry, seed, (s * workers + i) * per_worker, per_worker)
@@ -343,6 +409,7 @@ def run_reference(args):
             if s >= args.warmup:
                 t_total += dt
                 points += workers * per_worker  # events per step (one per call, as in the GPU arm)
+    _restore_env(old_env)
     value = points / t_total
     sample = (f"{workers} spawned processes x {per_worker} points per call per step of the same workload "
               f"({len(wl['calls'])} call(s)), FP64 numpy oracle, wall clock")
@@ -356,53 +423,72 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=N_POINTS)
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--fp64-steps", type=int, default=2)
-    ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--lanes-per-event", type=int, default=0,
-                    help="pin the lane layout of every handle (0: autotune; profiling runs pin it, "
-                         "since launch timing under a profiler misleads the tuner)")
-    ap.add_argument("--queued-rescue", action="store_true",
-                    help="time the queued one-launch rescue kernel instead of the two launches (float32, then "
-                         "float64 over the compacted list)")
-    ap.add_argument("--workload", default="c2", choices=["c0", "c1", "c2", "c3"],
-                    help="c2 (default): gg->ttg real-minus-CT; c0: e+e- NLO (n-body + real-minus-CT); "
-                         "c1: gg->tt LO; c3: gg->ttgg tree with the tensor-core colour sum")
-    args = ap.parse_args()
-    if args.impl == "reference":
-        run_reference(args)
-        return
-    warmup = max(3, args.warmup)
+def _stage_roofline(ops, calls, stages, n, workload, queued=False):
+    """Roofline of the dominant kernel of a step: the stage (main kernel or float64
+    rescue, over all calls of the step) with the largest CUDA-event time.  The queued
+    one-launch kernel (float32 pass plus queued float64 re-evaluation) is limited by its
+    float64 work: its fraction counts the re-evaluated points' flops against the float64
+    peak (a lower bound: the float64 maps of the float32 pass are not counted)."""
+    peak32 = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    peak64 = SM_COUNT * FP64_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    note32 = ("fp32 FMA peak 152 SMs x 128 lanes x 2 flops x 2070 MHz (nominal units at max clock; "
+              "MEASURED_PEAKS.json has no fp32 figure)")
+    note64 = ("fp64 peak 152 SMs x 2 DFMA/clk x 2 flops x 2070 MHz (nominal units at max clock; "
+              "MEASURED_PEAKS.json has no fp64 figure)")
+    cands = []
+    for (proc, entry, _), (t_main, t_resc, _t_red, ncalls, resc_pts, work) in zip(calls, stages):
+        per = max(1, ncalls)
+        flops = ops["real_subtracted_per_event" if entry == "real_subtracted" else "born_per_event"][proc]
+        kname = WORKLOADS[workload]["kernels"][proc]
+        if entry == "real_subtracted" and (work[1] or work[2]) and t_resc > 0:
+            # item rescue: the float64 work is the real's helicity blocks and the counterterm
+            # Born sets actually re-evaluated (op counts: real = born_per_event[proc] over
+            # its live blocks; Born set = the rest of the subtracted real)
+            real = ops["born_per_event"][proc]
+            per_block = real / NB_REAL[proc]
+            born_set = flops - real
+            item_flops = work[1] * per_block + work[2] * born_set
+            cands.append({"bound": "alu", "achieved": item_flops / (t_resc / per * 1e-3) / 1e12, "peak": peak64,
+                          "unit": "TFLOP/s", "traffic": traffic_per_launch(workload, "items", resc_pts),
+                          "kernel": f"k_rescue_items<{proc}> + k_rescue_combine (float64 items of the flagged "
+                                    "points: real-emission helicity blocks and counterterm Born sets)",
+                          "peak_note": note64, "flops_per_block": per_block, "flops_per_born_set": born_set,
+                          "points": resc_pts, "real_blocks": work[1], "born_sets": work[2],
+                          "ms_per_launch": t_resc / per})
+            resc_pts = 0  # accounted for above
+        if queued and entry == "real_subtracted" and resc_pts > 0:
+            cands.append({"bound": "alu", "achieved": flops * resc_pts / (t_main / per * 1e-3) / 1e12,
+                          "peak": peak64, "unit": "TFLOP/s", "traffic": traffic_per_launch(workload, "queued", n),
+                          "kernel": kname.replace("k_real_sub<", "k_real_sub_queued<").replace(", float>", ">")
+                          + " (float32 pass over all points + queued float64 re-evaluation of the flagged points)",
+                          "peak_note": note64, "flops_per_event": flops, "points_per_launch": n,
+                          "fp64_points_per_launch": resc_pts, "ms_per_launch": t_main / per})
+            continue
+        cands.append({"bound": "alu", "achieved": flops * n / (t_main / per * 1e-3) / 1e12 if t_main else 0.0,
+                      "peak": peak32, "unit": "TFLOP/s", "traffic": traffic_per_launch(workload, "main", n),
+                      "kernel": kname, "peak_note": note32, "flops_per_event": flops, "points_per_launch": n,
+                      "ms_per_launch": t_main / per})
+        if resc_pts > 0 and t_resc > 0:
+            cands.append({"bound": "alu", "achieved": flops * resc_pts / (t_resc / per * 1e-3) / 1e12, "peak": peak64,
+                          "unit": "TFLOP/s", "traffic": traffic_per_launch(workload, "rescue", resc_pts),
+                          "kernel": kname.replace("float", "double") + " (float64 re-evaluation of the flagged points)",
+                          "peak_note": note64, "flops_per_event": flops, "points_per_launch": resc_pts,
+                          "ms_per_launch": t_resc / per})
+    for c in cands:
+        c["frac"] = c["achieved"] / c["peak"]
+    cands.sort(key=lambda c: -c["ms_per_launch"])
+    return cands[0], (cands[1] if len(cands) > 1 else None)
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    # CPU baseline first (spawned pool, before any CUDA work in this process)
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "c2":
-        cpu = cpu_baseline()
 
+def measure(me, mebuild, workload, args, n, rank, world, local, dist, full):
+    """One workload: warm-up, K timed steps (CUDA events on the launching stream, clocks
+    sampled meanwhile), the plain float64 GPU path on the same batches, the end-to-end
+    C-ABI call on pinned host buffers, and the roofline of the dominant kernel.  `full`
+    adds the comparisons of the headline workload (the other rescue organisation, the
+    step with device-generated points, unweighting)."""
     import torch
     import synth
-    import __graft_entry__
-    __graft_entry__.build()
-    import paper_2503_07439_gb300 as me
-    from paper_2503_07439_gb300 import build as mebuild
-
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    wl = WORKLOADS[args.workload]
-    n = args.n if args.workload == "c2" else wl["n"]
+    wl = WORKLOADS[workload]
     calls = []  # (process, entry point, batch)
     for proc, entry, seed in wl["calls"]:
         if proc == "gg_tt":
@@ -432,6 +518,7 @@ def main():
         if dist is not None:
             dist.barrier()
 
+    warmup = max(3, args.warmup)
     clk = Clocks(local).__enter__()  # sampling runs from before the warm-up
     for _ in range(warmup):
         step(handles)
@@ -454,12 +541,12 @@ def main():
     clk.mark(w0, w1)
     clk.__exit__()
     ms = e0.elapsed_time(e1)
-    # the dominant kernel is the first call's main kernel
-    stages = [hh.stage_times() for hh, *_ in handles]
-    t_main, t_resc, t_red, ncalls = stages[0]
+    stages = []
     for hh, *_ in handles:
+        t_main, t_resc, t_red, ncalls = hh.stage_times()
         hh.enable_stage_timers(False)
-    rescued = sum(hh.last_rescued() for hh, *_ in handles)
+        stages.append((t_main, t_resc, t_red, ncalls, hh.last_rescued(), hh.last_rescue_work()))
+    rescued = sum(st[4] for st in stages)
     ms, events = reduce_replicas(ms, float(n * args.steps), dist, device="cuda")
     value = events / (ms * 1e-3)
 
@@ -475,22 +562,18 @@ def main():
         torch.cuda.synchronize()
         return f0.elapsed_time(f1) / k
 
-    # plain float64 GPU path on the same batches
     fp64_ms = time_steps(make(me.ME_PREC_FP64), args.fp64_steps)
     fp64_value = n / (fp64_ms * 1e-3)
-    # the other rescue organisation, for comparison (same batches, same results)
     has_real = any(entry == "real_subtracted" for _, entry, _ in calls)
-    alt = None
-    if has_real:
+    alt = devgen = unw = None
+    if full and has_real:
         alt_ms = time_steps(make(me.ME_PREC_MIXED, queued=not args.queued_rescue), max(3, args.fp64_steps))
         alt = {"value": n / (alt_ms * 1e-3), "unit": UNIT, "ms_per_step": alt_ms,
                "rescue": "float32 launch, then float64 launch over the compacted list" if args.queued_rescue else
                          "queued one-launch kernel"}
-
-    # the same step with the points generated on the device every step (Philox4x32-10 +
-    # RAMBO, me_generate_flat), for the workloads drawn from flat RAMBO points
-    devgen = None
-    if all(proc != "gg_tt" for proc, _, _ in calls):
+    if full and all(proc != "gg_tt" for proc, _, _ in calls):
+        # the same step with the points generated on the device every step (Philox4x32-10
+        # + RAMBO, me_generate_flat)
         def gen_step(step_no):
             for (_, _, seed), (_, _, bb), (hh, f, pd, wd, od) in zip(wl["calls"], calls, handles):
                 hh.generate_flat(n, seed, bb.sqrt_s, first_point=(rank + world * step_no) * n, out=(pd, wd))
@@ -507,11 +590,9 @@ def main():
         gms = g0.elapsed_time(g1) / args.steps
         devgen = {"value": n / (gms * 1e-3), "unit": UNIT, "ms_per_step": gms,
                   "note": "momenta and weights generated on the device each step, then evaluated"}
-
-    # unweighted events from the step's subtracted-real weights (me_unweight: accept/reject
-    # against the batch maximum of |w|, on the device; synchronous, so timed on the host)
-    unw = None
-    if calls[0][1] == "real_subtracted":
+    if full and calls[0][1] == "real_subtracted":
+        # unweighted events from the step's subtracted-real weights (me_unweight: accept/
+        # reject against the batch maximum of |w|, on the device; synchronous, host-timed)
         hh0, _, _, _, od0 = handles[0]
         hh0.unweight(od0, seed=SEED, stream=9)
         torch.cuda.synchronize()
@@ -544,82 +625,120 @@ def main():
     barrier()
     h2d = sum(bb.p.nbytes + bb.wgt.nbytes for _, _, bb in calls)
     d2h = len(calls) * n * 8
+    ops = mebuild.op_counts()
+    roofline, other = _stage_roofline(ops, calls, stages, n, workload, queued=args.queued_rescue)
+    # per call: the main kernel, the float64 work of the two-launch subtracted real (item
+    # rescue: items + recombination; whole points: one launch) and the two reduction kernels
+    launches_per_step = sum(1 + ((2 if st[5][1] or st[5][2] else 1) if entry == "real_subtracted" and
+                                 not args.queued_rescue else 0) + 2 for (_, entry, _), st in zip(calls, stages))
+    return {
+        "metric": wl["metric"], "value": value, "unit": UNIT, "ms_per_step": ms / args.steps, "steps": args.steps,
+        "warmup": warmup, "n_points": n, "processes": [c[0] for c in calls], "workload": wl["workload"],
+        "l2": wl["l2"],
+        "fp64_path": {"value": fp64_value, "unit": UNIT, "ms_per_step": fp64_ms,
+                      "mixed_over_fp64": value / world / fp64_value},
+        "other_rescue_path": alt, "rescued_per_step": rescued,
+        "rescue_work_per_step": [{"process": c[0], "points": st[5][0], "real_blocks": st[5][1],
+                                  "born_sets": st[5][2]} for c, st in zip(calls, stages)],
+        "stage_ms_per_step": [{"process": c[0], "main_kernel": st[0] / max(1, st[3]),
+                               "rescue_kernel": st[1] / max(1, st[3]), "reduction": st[2] / max(1, st[3])}
+                              for c, st in zip(calls, stages)],
+        "roofline": roofline, "roofline_other_kernel": other,
+        "e2e": {"value": n / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "path": "C-ABI call on pinned host buffers: the kernels read the inputs and write the results in "
+                        "place over the CPU-GPU link (no staging copy); the call returns with results on the host"},
+        "device_generated": devgen, "unweighting": unw,
+        "gpu_launches": launches_per_step * args.steps, "clocks": clk.summary(),
+    }
 
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_POINTS)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the c0, c1 and c3 sub-lines of the default (c2) run")
+    ap.add_argument("--lanes-per-event", type=int, default=0,
+                    help="pin the lane layout of every handle (0: autotune; profiling runs pin it, "
+                         "since launch timing under a profiler misleads the tuner)")
+    ap.add_argument("--queued-rescue", action="store_true",
+                    help="time the queued one-launch rescue kernel instead of the two launches (float32, then "
+                         "float64 over the compacted list)")
+    ap.add_argument("--workload", default="c2", choices=["c0", "c1", "c2", "c3"],
+                    help="c2 (default): gg->ttg real-minus-CT; c0: e+e- NLO (n-body + real-minus-CT); "
+                         "c1: gg->tt LO; c3: gg->ttgg tree with the tensor-core colour sum")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    # CPU baseline first (spawned pool, before any CUDA work in this process)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "c2":
+        cpu = cpu_baseline()
+
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2503_07439_gb300 as me
+    from paper_2503_07439_gb300 import build as mebuild
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    n = args.n if args.workload == "c2" else WORKLOADS[args.workload]["n"]
+    head = measure(me, mebuild, args.workload, args, n, rank, world, local, dist, full=True)
+    # the other configurations of the method, measured in the same run (sub-lines), before
+    # the serving run, so that every lane layout is tuned on an otherwise idle GPU
+    configs = None
+    if args.workload == "c2" and not args.no_configs:
+        configs = {}
+        for wk in ("c0", "c1", "c3"):
+            m = measure(me, mebuild, wk, args, WORKLOADS[wk]["n"], rank, world, local, dist, full=False)
+            configs[wk] = {k: m[k] for k in ("metric", "value", "unit", "ms_per_step", "n_points", "processes",
+                                             "workload", "l2", "fp64_path", "rescued_per_step",
+                                             "rescue_work_per_step", "stage_ms_per_step",
+                                             "roofline", "roofline_other_kernel", "e2e", "gpu_launches", "clocks")}
     serve = None
     if rank == 0 and not args.no_serving and args.workload == "c2":
         serve = serving_metrics(me, device=local)
     if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
         return
-    ops = mebuild.op_counts()
-    proc0, entry0, _ = calls[0]
-    flops_event = ops["real_subtracted_per_event" if entry0 == "real_subtracted" else "born_per_event"][proc0]
-    main_ms = t_main / max(1, ncalls)
-    resc_ms = t_resc / max(1, ncalls)
-    resc_pts = handles[0][0].last_rescued()
-    queued0 = entry0 == "real_subtracted" and args.queued_rescue
-    peak32 = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    peak64 = SM_COUNT * FP64_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    note32 = ("fp32 FMA peak 152 SMs x 128 lanes x 2 flops x 2070 MHz (nominal units at max clock; "
-              "MEASURED_PEAKS.json has no fp32 figure)")
-    note64 = ("fp64 peak 152 SMs x 2 DFMA/clk x 2 flops x 2070 MHz (nominal units at max clock; "
-              "MEASURED_PEAKS.json has no fp64 figure)")
-    # roofline of the dominant kernel of the step (by its CUDA-event time)
-    rl_main = {"bound": "alu", "achieved": flops_event * n / (main_ms * 1e-3) / 1e12, "peak": peak32,
-               "unit": "TFLOP/s", "traffic": traffic_per_launch(args.workload, "main", n), "kernel": wl["kernel"],
-               "peak_note": note32, "flops_per_event": flops_event, "ms_per_launch": main_ms}
-    rl_main["frac"] = rl_main["achieved"] / peak32
-    roofline, other = rl_main, None
-    if queued0 and resc_pts > 0:
-        # one kernel: float32 pass over every point + float64 re-evaluation of the flagged
-        # ones; the float64 unit limits it, so the fraction is taken against the fp64 peak
-        # and counts only the float64 work of the re-evaluated points (the float64 maps of
-        # the float32 pass are not counted: a lower bound)
-        roofline = {"bound": "alu", "achieved": flops_event * resc_pts / (main_ms * 1e-3) / 1e12, "peak": peak64,
-                    "unit": "TFLOP/s", "traffic": traffic_per_launch(args.workload, "queued", n),
-                    "kernel": wl["kernel"].replace("k_real_sub<", "k_real_sub_queued<").replace(", float>", ">")
-                    + " (float32 pass over all points + queued float64 re-evaluation of the flagged points)",
-                    "peak_note": note64, "flops_per_event": flops_event, "points_per_launch": n,
-                    "fp64_points_per_launch": resc_pts, "ms_per_launch": main_ms,
-                    "fp32_pass": {"achieved": flops_event * n / (main_ms * 1e-3) / 1e12, "peak": peak32,
-                                  "frac": flops_event * n / (main_ms * 1e-3) / 1e12 / peak32}}
-        roofline["frac"] = roofline["achieved"] / peak64
-    elif resc_pts > 0 and resc_ms > main_ms:
-        rl_resc = {"bound": "alu", "achieved": flops_event * resc_pts / (resc_ms * 1e-3) / 1e12, "peak": peak64,
-                   "unit": "TFLOP/s", "traffic": traffic_per_launch(args.workload, "rescue", resc_pts),
-                   "kernel": wl["kernel"].replace("float", "double") + " (float64 rescue of the flagged points)",
-                   "peak_note": note64, "flops_per_event": flops_event, "points_per_launch": resc_pts,
-                   "ms_per_launch": resc_ms}
-        rl_resc["frac"] = rl_resc["achieved"] / peak64
-        roofline, other = rl_resc, rl_main
-    # kernels per step: per call the main kernel, the float64 rescue launch (two-launch
-    # mixed subtracted real only) and the two reduction kernels
-    launches_per_step = sum(1 + (1 if entry == "real_subtracted" and not args.queued_rescue else 0) + 2
-                            for _, entry, _ in calls)
-    clocks = clk.summary()
     line = {
-        "metric": wl["metric"], "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "metric": head["metric"], "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": head["warmup"], "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic (seeded Philox + RAMBO phase space)",
-        "config": {"workload": wl["workload"], "processes": [c[0] for c in calls], "n_points": n,
-                   "precision": "mixed", "l2": wl["l2"],
+        "config": {"workload": head["workload"], "processes": head["processes"], "n_points": n,
+                   "precision": "mixed", "l2": head["l2"],
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "fp64_path": {"value": fp64_value, "unit": UNIT, "ms_per_step": fp64_ms,
-                      "mixed_over_fp64": value / world / fp64_value},
-        "other_rescue_path": alt,
-        "rescued_per_step": rescued,
-        "stage_ms_per_step": {"main_kernel": main_ms, "rescue_kernel": t_resc / max(1, ncalls),
-                              "reduction": t_red / max(1, ncalls)},
-        "roofline": roofline,
-        "roofline_other_kernel": other,
-        "e2e": {"value": n / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "path": "C-ABI call on pinned host buffers: the kernels read the inputs and write the results in "
-                        "place over the CPU-GPU link (no staging copy); the call returns with results on the host"},
-        "device_generated": devgen,
-        "unweighting": unw,
-        "gpu_launches": launches_per_step * args.steps,
-        "clocks": clocks,
+        "fp64_path": head["fp64_path"],
+        "other_rescue_path": head["other_rescue_path"],
+        "rescued_per_step": head["rescued_per_step"],
+        "rescue_work_per_step": head["rescue_work_per_step"],
+        "stage_ms_per_step": head["stage_ms_per_step"],
+        "roofline": head["roofline"],
+        "roofline_other_kernel": head["roofline_other_kernel"],
+        "e2e": head["e2e"],
+        "device_generated": head["device_generated"],
+        "unweighting": head["unweighting"],
+        "gpu_launches": head["gpu_launches"],
+        "clocks": head["clocks"],
         "cpu_baseline": cpu,
         "serving": serve,
+        "configs": configs,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
