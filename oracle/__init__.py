@@ -16,7 +16,9 @@ What it computes (hep-ph background of arXiv:2503.07439):
   * the FKS real-minus-counterterm weight in the sector parametrisation
     (Sec. 2.2 subtraction schemes; Sec. 4.2 FKS sectors; Algorithm 2 evaluates
     Born, real, soft and collinear terms unconditionally, then masks them);
-  * for e+e- -> u ubar the analytic virtual plus integrated FKS counterterms.
+  * for e+e- -> u ubar the analytic virtual plus integrated FKS counterterms;
+  * infrared-safe cuts applied to each term at its own kinematics (Algorithm 2's
+    passCuts(a, p)): heavy-quark p_T and rapidity, e+e- thrust and thrust axis.
 
 The paper prints no formulas for any of this; every formula here is standard
 physics restated in the modules' docstrings, and each is pinned by the tests in

@@ -44,6 +44,7 @@ from dataclasses import dataclass
 import numpy as np
 
 from . import colour
+from .cuts import Cuts, passes
 from .dirac import dot
 from .matrix_element import (MT, Couplings, colour_correlated, coloured_legs, me2,
                              spin_correlated)
@@ -206,10 +207,15 @@ def born_leg_name(born: str, j: int) -> str:
 
 
 def real_subtracted(real: str, k: np.ndarray, fp: FKSParams = FKSParams(),
-                    cp: Couplings = Couplings(), detail: bool = False):
+                    cp: Couplings = Couplings(), detail: bool = False, cuts: Cuts | None = None):
     """Sum over sectors of the subtracted real weight per point (ME units; multiply by
-    the phase-space weight of the generator).  ``k``: real momenta (N, n, 4)."""
+    the phase-space weight of the generator).  ``k``: real momenta (N, n, 4).
+
+    ``cuts`` (oracle.cuts): each term is kept only where its own kinematics pass
+    (Algorithm 2): the real at k, the soft and soft-collinear terms at the sector's soft
+    Born counter-event, the collinear term at the sector's collinear Born counter-event."""
     born, i_fks, partners, mass = REAL_PROCESSES[real]
+    cut_on = cuts is not None and cuts.active(real)
     rs = k[:, 0, 0] + k[:, 1, 0]
     s = rs * rs
     S = sector_functions(k, i_fks, partners)
@@ -240,6 +246,11 @@ def real_subtracted(real: str, k: np.ndarray, fp: FKSParams = FKSParams(),
                                             kin.born_soft, kin.e_perp, s, cp)
         th_s = (xi < fp.xi_cut).astype(float)
         th_c = (y > 1.0 - fp.delta).astype(float)
+        if cut_on:
+            c_r = passes(real, k, cuts).astype(float)
+            c_s = passes(born, kin.born_soft, cuts).astype(float)
+            c_c = passes(born, kin.born_coll, cuts).astype(float)
+            G, G_soft, G_coll, G_sc = G * c_r, G_soft * c_s, G_coll * c_c, G_sc * c_s
         W = (G - th_s * G_soft - th_c * G_coll + th_s * th_c * G_sc) / (xi * xi * (1.0 - y) * kin.K)
         total += W
         with np.errstate(invalid="ignore"):

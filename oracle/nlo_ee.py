@@ -38,7 +38,10 @@ def nbody_coefficient(xi_cut: float, delta: float) -> float:
 
 
 def nbody_nlo(p: np.ndarray, xi_cut: float = 0.5, delta: float = 1.0,
-              cp: Couplings = Couplings()) -> np.ndarray:
-    """B (1 + a_s c(xi_c, delta)) for e+e- -> u ubar Born points p (N, 4, 4)."""
+              cp: Couplings = Couplings(), cuts=None) -> np.ndarray:
+    """B (1 + a_s c(xi_c, delta)) for e+e- -> u ubar Born points p (N, 4, 4); with
+    ``cuts`` (oracle.cuts), 0 where the Born point fails them (Algorithm 2's n-body term)."""
+    from .cuts import passes
     a_s = cp.alpha_s * colour.CF / (2.0 * math.pi)
-    return me2("ee_uu", p, cp) * (1.0 + a_s * nbody_coefficient(xi_cut, delta))
+    w = me2("ee_uu", p, cp) * (1.0 + a_s * nbody_coefficient(xi_cut, delta))
+    return np.where(passes("ee_uu", p, cuts), w, 0.0) if cuts is not None else w
