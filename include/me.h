@@ -47,7 +47,7 @@ extern "C" {
 #define ME_ERR_CUDA (-5)     /* a CUDA call failed; see me_last_error() */
 #define ME_ERR_BUSY (-6)     /* request rejected: queue full or over the memory budget */
 
-#define ME_PARAMS_VERSION 3u
+#define ME_PARAMS_VERSION 4u
 #define ME_PREC_FP64 0   /* every amplitude in float64 */
 #define ME_PREC_MIXED 1  /* float32 amplitudes; float64 FKS maps, combination and rescue */
 #define ME_RESCUE_POINTS 0 /* mixed precision: every flagged point re-evaluated whole in float64 */
@@ -96,6 +96,34 @@ extern "C" {
  *                    float64.  Points inside xi_thr / y_thr take every ingredient in
  *                    float64.  ME_RESCUE_POINTS re-evaluates every flagged point whole in
  *                    float64.  me_last_rescued counts the flagged points either way.
+ *   term_queues      subtracted real (both precisions): 0 (default) = Algorithm 2 of the
+ *                    paper (Sec. 4.3): every term -- real, soft, collinear -- is evaluated
+ *                    for every point, and the terms whose cuts fail are zeroed afterwards;
+ *                    1 = per-term queues, the variant discussed after Algorithm 2: a
+ *                    float64 pass maps every point, decides the cuts and the counterterm
+ *                    regions, and queues only the amplitudes a point needs (the real's
+ *                    helicity blocks if the real passes its cuts; the soft Born set and
+ *                    the collinear Born set if that counterterm is active and passes);
+ *                    each kind of amplitude is then evaluated over its queue in one
+ *                    launch, and the weight is recombined (mixed precision: with the same
+ *                    stability test and float64 item rescue).  Tree-level entries
+ *                    (me_eval_born, me_eval_nbody_nlo) queue the points that pass the cuts.
+ *                    Results agree with term_queues 0 to rounding.  The allocation-free
+ *                    entry and the persistent serving kernels always run term_queues 0.
+ *   cut_pt_min, cut_abs_y_max
+ *                    cuts on both heavy quarks (legs 2, 3 of the t tbar processes and of
+ *                    their Born counter-events): p_T >= cut_pt_min [GeV] and |rapidity
+ *                    along the z axis| <= cut_abs_y_max.  0 and +infinity: no cut.
+ *   cut_abs_cos_axis_max, cut_thrust_max
+ *                    e+e- processes: |cos| of the thrust axis (the direction of the most
+ *                    energetic final parton) with the z axis <= cut_abs_cos_axis_max, and
+ *                    thrust T = max_i 2 E_i / sqrt(s) <= cut_thrust_max.  Values >= 1: no cut.
+ *                    Each cut is applied to every term at that term's own kinematics (the
+ *                    real point, or the soft or collinear Born counter-event); cuts that do
+ *                    not belong to the handle's process are ignored.  Decisions are taken
+ *                    in float64 without square roots or logarithms: px*px + py*py >=
+ *                    pt_min^2, E + |pz| <= exp(2 y_max) (E - |pz|), pz^2 <= c^2 |p|^2,
+ *                    2 E_m <= T_max (E_0 + E_1).
  */
 typedef struct me_params {
   uint32_t version;
@@ -113,13 +141,20 @@ typedef struct me_params {
   int32_t lanes_per_event;
   int32_t queued_rescue;
   int32_t rescue;
+  int32_t term_queues;
+  double cut_pt_min;
+  double cut_abs_y_max;
+  double cut_abs_cos_axis_max;
+  double cut_thrust_max;
 } me_params;
 
 typedef struct me_handle me_handle;
 
 /* Fill `p` with the defaults: FP64, alpha = 1/132.507, alpha_s = 0.118, mt = 173,
  * xi_cut = 0.5, delta = 1, xi_thr = 1e-3, y_thr = 1e-3, tol = 1e-5, me_eps = 4e-7,
- * device 0, lanes_per_event 0, queued_rescue 0, rescue ME_RESCUE_ITEMS.  Never fails. */
+ * device 0, lanes_per_event 0, queued_rescue 0, rescue ME_RESCUE_ITEMS, term_queues 0,
+ * no cuts (cut_pt_min 0, cut_abs_y_max +infinity, cut_abs_cos_axis_max 1,
+ * cut_thrust_max 1).  Never fails. */
 void me_default_params(me_params* p);
 
 /*

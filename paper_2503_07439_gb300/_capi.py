@@ -16,7 +16,7 @@ ME_ERR_CUDA = -5
 ME_ERR_BUSY = -6
 ME_PREC_FP64 = 0
 ME_PREC_MIXED = 1
-ME_PARAMS_VERSION = 3
+ME_PARAMS_VERSION = 4
 ME_RESCUE_POINTS = 0
 ME_RESCUE_ITEMS = 1
 ME_KIND_BORN = 0
@@ -41,7 +41,9 @@ class MEParams(ctypes.Structure):
                 ("delta", ctypes.c_double), ("xi_thr", ctypes.c_double), ("y_thr", ctypes.c_double),
                 ("tol", ctypes.c_double), ("me_eps", ctypes.c_double), ("device", ctypes.c_int32),
                 ("lanes_per_event", ctypes.c_int32), ("queued_rescue", ctypes.c_int32),
-                ("rescue", ctypes.c_int32)]
+                ("rescue", ctypes.c_int32), ("term_queues", ctypes.c_int32), ("cut_pt_min", ctypes.c_double),
+                ("cut_abs_y_max", ctypes.c_double), ("cut_abs_cos_axis_max", ctypes.c_double),
+                ("cut_thrust_max", ctypes.c_double)]
 
 
 class MEServerParams(ctypes.Structure):

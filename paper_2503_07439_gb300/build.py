@@ -18,7 +18,7 @@ LIB = os.path.join(PKG, "libme_gb300.so")
 FLOPS_TOOL = os.path.join(BUILD, "me_flops")
 SOURCES = ["me_core.cu", "me_serve.cu", "me_inst_ee.cu", "me_inst_gg.cu", "me_inst_ggg.cu",
            "me_inst_ggg64.cu", "me_inst_uu.cu", "me_inst_queued.cu", "me_inst_queued_gg.cu", "me_noalloc.cu",
-           "me_phase.cu", "me_inst_serve.cu", "me_inst_serve_gg.cu"]
+           "me_phase.cu", "me_inst_serve.cu", "me_inst_serve_gg.cu", "me_inst_terms.cu", "me_inst_terms_gg.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 

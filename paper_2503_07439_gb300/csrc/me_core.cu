@@ -405,10 +405,14 @@ struct me_handle {
   size_t cap = 0;
   int* d_resc = nullptr;     // rescue index list (capacity cap)
   int* d_nresc = nullptr;    // [0]: points re-evaluated in float64, [1]: tile counter (queued kernel),
-                             // [2] / [3]: real-block / Born items of the item rescue
+                             // [2] / [3]: real-block / Born items of the item rescue,
+                             // [8]: points passing the cuts (tree entries with per-term queues)
   // item rescue (mixed-precision subtracted real): records and item lists, capacity icap
   ItemBufs ib{};
   size_t icap = 0;
+  // per-term queues (term_queues = 1): records, configurations and queues, capacity tcap
+  TermBufs tb{};
+  size_t tcap = 0;
   double* d_part = nullptr;  // reduction partials
   double* d_acc = nullptr;   // accumulators (3)
   int lpe[2][2] = {{0, 0}, {0, 0}};  // [kind][fp64] chosen lanes per event
@@ -448,6 +452,43 @@ static int ensure_item_capacity(me_handle* h, size_t n) {
   }
   b.cap = (long)c;
   h->icap = c;
+  return ME_OK;
+}
+
+static void free_terms(me_handle* h) {
+  TermBufs& t = h->tb;
+  void* ptrs[] = {t.ev, t.flags, t.grow, t.a, t.v, t.m, t.cfg, t.bp, t.bx, t.bslot, t.q_real, t.r_real, t.r_born,
+                  t.flagged, t.cnt};
+  for (void* q : ptrs) cudaFree(q);
+  h->tb = TermBufs{};
+  h->tcap = 0;
+}
+
+// Records, Born configurations and queues of the per-term queues for n points.
+static int ensure_term_capacity(me_handle* h, size_t n) {
+  if (n <= h->tcap) return ME_OK;
+  free_terms(h);
+  const size_t c = std::max(n, (size_t)1024);
+  TermBufs& t = h->tb;
+  bool ok = cudaMalloc(&t.ev, c * sizeof(int)) == cudaSuccess && cudaMalloc(&t.flags, c * sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&t.grow, c * sizeof(float)) == cudaSuccess &&
+            cudaMalloc(&t.a, c * MAX_ITEMS * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&t.v, c * MAX_ITEMS * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&t.m, c * 6 * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&t.cfg, c * 2 * sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&t.bp, c * 2 * 16 * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&t.bx, c * 2 * 4 * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&t.bslot, c * 2 * sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&t.q_real, c * 4 * sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&t.r_real, c * 4 * sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&t.r_born, c * 2 * sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&t.flagged, c * sizeof(int)) == cudaSuccess && cudaMalloc(&t.cnt, 8 * sizeof(int)) == cudaSuccess;
+  if (!ok) {
+    free_terms(h);
+    return fail(ME_ERR_OOM, "per-term queue scratch allocation failed");
+  }
+  t.cap = (long)c;
+  h->tcap = c;
   return ME_OK;
 }
 
@@ -528,6 +569,17 @@ static cudaError_t launch_rescue(me_handle* h, const LaunchArgs& a, int lpe64) {
   return dispatch(h->proc->pid, K_REAL, true, lpe64, r, h->stream);
 }
 
+// Per-term queues of the subtracted real (phase 0: float64 pass, bulk items and
+// recombination; phase 1: float64 rescue and recombination of the flagged points).
+static cudaError_t launch_terms(me_handle* h, int phase, bool mixed, const LaunchArgs& a) {
+  switch (h->proc->pid) {
+    case P_EE_UUG: return launch_terms_ee(phase, mixed, a, h->tb, h->d_nresc, h->stream);
+    case P_GG_TTG: return launch_terms_gg(phase, mixed, a, h->tb, h->d_nresc, h->stream);
+    case P_UU_TTG: return launch_terms_uu(phase, mixed, a, h->tb, h->d_nresc, h->stream);
+  }
+  return cudaErrorInvalidValue;
+}
+
 // pick lanes-per-event by timing each candidate once on the caller's batch (first use)
 // Lane layouts chosen by timing, shared by every handle of the process (key: device,
 // process, kind, precision, batch-size class), so that later handles -- e.g. the slots
@@ -596,6 +648,37 @@ static int choose_lpe(me_handle* h, int kind, bool fp64, const LaunchArgs& a) {
   return slot = pick;
 }
 
+// The cuts of me_params as the kernels take them (Cuts in me_kernels.cuh), for process pid.
+static bool cuts_valid(const me_params* p) {
+  return std::isfinite(p->cut_pt_min) && p->cut_pt_min >= 0.0 && p->cut_abs_y_max > 0.0 &&
+         !std::isnan(p->cut_abs_y_max) && p->cut_abs_cos_axis_max > 0.0 && !std::isnan(p->cut_abs_cos_axis_max) &&
+         p->cut_thrust_max > 0.0 && !std::isnan(p->cut_thrust_max) && (p->term_queues == 0 || p->term_queues == 1);
+}
+static Cuts cuts_of(int pid, const me_params* p) {
+  Cuts c{};
+  const bool heavy = pid == P_GG_TT || pid == P_GG_TTG || pid == P_GG_TTGG || pid == P_UU_TT || pid == P_UU_TTG;
+  if (heavy) {
+    if (p->cut_pt_min > 0.0) {
+      c.mask |= CUT_PT;
+      c.pt2_min = p->cut_pt_min * p->cut_pt_min;
+    }
+    if (std::isfinite(p->cut_abs_y_max)) {
+      c.mask |= CUT_Y;
+      c.ey2 = std::exp(2.0 * p->cut_abs_y_max);
+    }
+  } else {
+    if (p->cut_abs_cos_axis_max < 1.0) {
+      c.mask |= CUT_AXIS;
+      c.cos2_max = p->cut_abs_cos_axis_max * p->cut_abs_cos_axis_max;
+    }
+    if (p->cut_thrust_max < 1.0) {
+      c.mask |= CUT_THRUST;
+      c.thrust_max = p->cut_thrust_max;
+    }
+  }
+  return c;
+}
+
 extern "C" {
 
 void me_default_params(me_params* p) {
@@ -615,6 +698,11 @@ void me_default_params(me_params* p) {
   p->device = 0;
   p->lanes_per_event = 0;
   p->rescue = ME_RESCUE_ITEMS;
+  p->term_queues = 0;
+  p->cut_pt_min = 0.0;
+  p->cut_abs_y_max = HUGE_VAL;
+  p->cut_abs_cos_axis_max = 1.0;
+  p->cut_thrust_max = 1.0;
 }
 
 const char* me_last_error(void) { return g_err.c_str(); }
@@ -632,6 +720,7 @@ int me_init(const char* process, const me_params* params, me_handle** out) {
   if (l != 0 && l != 1 && l != 2 && l != 4 && l != 8 && l != 16) return fail(ME_ERR_ARG, "me_init: lanes_per_event");
   if (params->rescue != ME_RESCUE_POINTS && params->rescue != ME_RESCUE_ITEMS)
     return fail(ME_ERR_ARG, "me_init: rescue must be ME_RESCUE_POINTS or ME_RESCUE_ITEMS");
+  if (!cuts_valid(params)) return fail(ME_ERR_ARG, "me_init: cut or term_queues parameter out of range");
   const ProcDesc* pd = nullptr;
   for (const auto& d : kProcs)
     if (std::strcmp(d.name, process) == 0) pd = &d;
@@ -648,7 +737,7 @@ int me_init(const char* process, const me_params* params, me_handle** out) {
     return fail(ME_ERR_CUDA, "me_init: stream creation failed");
   }
   h->stream = h->own_stream;
-  if (cudaMalloc(&h->d_nresc, 4 * sizeof(int)) != cudaSuccess || cudaMalloc(&h->d_part, 2 * RED_BLOCKS * sizeof(double)) != cudaSuccess ||
+  if (cudaMalloc(&h->d_nresc, 16 * sizeof(int)) != cudaSuccess || cudaMalloc(&h->d_part, 2 * RED_BLOCKS * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&h->d_acc, 3 * sizeof(double)) != cudaSuccess) {
     me_destroy(h);
     return fail(ME_ERR_OOM, "me_init: allocation failed");
@@ -668,11 +757,12 @@ int me_init(const char* process, const me_params* params, me_handle** out) {
   kp.me_eps = params->me_eps;
   kp.tol = params->tol;
   kp.item_budget = kItemBudget;
+  kp.cut = cuts_of(pd->pid, params);
   kp.tab = d_tab;
   // stream-ordered on the handle's own stream: no device-wide synchronisation, so a
   // handle can be created while other threads capture CUDA graphs
   if (cudaMemsetAsync(h->d_acc, 0, 3 * sizeof(double), h->own_stream) != cudaSuccess ||
-      cudaMemsetAsync(h->d_nresc, 0, 4 * sizeof(int), h->own_stream) != cudaSuccess ||
+      cudaMemsetAsync(h->d_nresc, 0, 16 * sizeof(int), h->own_stream) != cudaSuccess ||
       cudaStreamSynchronize(h->own_stream) != cudaSuccess) {
     me_destroy(h);
     return fail(ME_ERR_CUDA, "me_init: device error");
@@ -724,10 +814,13 @@ static int run(me_handle* h, int kind, double nlo_factor, const double* momenta,
   a.resc_list = h->d_resc;
   a.resc_count = h->d_nresc;
   a.tiles = h->d_nresc + 1;
-  const bool queued = kind == K_REAL && mixed && h->prm.queued_rescue;
+  const bool terms = kind == K_REAL && h->prm.term_queues;
+  const bool cut_list = kind == K_TREE && h->prm.term_queues && a.kp.cut.mask;
+  const bool queued = kind == K_REAL && mixed && h->prm.queued_rescue && !terms;
+  if (terms && (rc = ensure_term_capacity(h, (size_t)n)) != ME_OK) return rc;
   if (kind == K_REAL && mixed) {
     a.kp.flag_unstable = 1;
-    if (!queued && use_items(h, n)) {
+    if (!queued && !terms && use_items(h, n)) {
       if ((rc = ensure_item_capacity(h, (size_t)n)) != ME_OK) return rc;
       a.kp.item_rescue = 1;
       a.items = h->ib;
@@ -737,10 +830,10 @@ static int run(me_handle* h, int kind, double nlo_factor, const double* momenta,
   }
   // the first call per (kind, precision) times the lane layouts (synchronising);
   // both are chosen before the launches whose results are kept.  The queued kernel
-  // runs one lane per point in both precisions.
-  if (queued) h->lpe[kind][0] = h->lpe[kind][1] = 1;
-  const int lpe64 = (kind == K_REAL && mixed && !queued) ? choose_lpe(h, kind, true, a) : 0;
-  const int lpe = queued ? 1 : choose_lpe(h, kind, !mixed, a);
+  // runs one lane per point in both precisions; the per-term queues one lane per item.
+  if (queued || terms) h->lpe[kind][0] = h->lpe[kind][1] = 1;
+  const int lpe64 = (kind == K_REAL && mixed && !queued && !terms) ? choose_lpe(h, kind, true, a) : 0;
+  const int lpe = (queued || terms) ? 1 : choose_lpe(h, kind, !mixed, a);
   std::array<cudaEvent_t, 4> ev{};
   const bool timed = h->timers && h->ev_used.size() < 4096;
   if (timed) {
@@ -756,12 +849,22 @@ static int run(me_handle* h, int kind, double nlo_factor, const double* momenta,
     h->ev_used.push_back(ev);
     ME_CUDA(cudaEventRecord(ev[0], h->stream));
   }
-  if (queued)
+  if (terms) {
+    ME_CUDA(launch_terms(h, 0, mixed, a));
+  } else if (queued) {
     ME_CUDA(launch_queued(h->proc->pid, a, h->stream));
-  else
+  } else {
+    if (cut_list) {
+      // per-term queues of a tree entry: only the points that pass the cuts are evaluated
+      ME_CUDA(launch_cut_list(h->proc->pid, a, h->d_resc, h->d_nresc + 8, h->stream));
+      a.idx = h->d_resc;
+      a.count = h->d_nresc + 8;
+    }
     ME_CUDA(dispatch(h->proc->pid, kind, !mixed, lpe, a, h->stream));
+  }
   if (timed) ME_CUDA(cudaEventRecord(ev[1], h->stream));
-  if (kind == K_REAL && mixed && !queued) ME_CUDA(launch_rescue(h, a, lpe64));
+  if (terms && mixed) ME_CUDA(launch_terms(h, 1, mixed, a));
+  if (kind == K_REAL && mixed && !queued && !terms) ME_CUDA(launch_rescue(h, a, lpe64));
   if (timed) ME_CUDA(cudaEventRecord(ev[2], h->stream));
   k_partials<<<RED_BLOCKS, 256, 0, h->stream>>>(O, n, h->d_part, nullptr);
   k_finish<<<1, 32, 0, h->stream>>>(h->d_part, RED_BLOCKS, h->d_acc, n, nullptr);
@@ -885,6 +988,7 @@ void me_destroy(me_handle* h) {
   cudaFree(h->d_resc);
   cudaFree(h->d_nresc);
   free_items(h);
+  free_terms(h);
   cudaFree(h->d_part);
   cudaFree(h->d_acc);
   for (auto& ev : h->ev_used)
@@ -919,6 +1023,7 @@ int me_internal_prepare_counted(me_handle* h, int me_kind, int64_t cap) {
     return fail(ME_ERR_ARG, "counted launch: run one ordinary call of this kind first");
   ME_CUDA(cudaSetDevice(h->device));
   int rc = ensure_capacity(h, (size_t)cap);
+  if (rc == ME_OK && kind == K_REAL && h->prm.term_queues) return ensure_term_capacity(h, (size_t)cap);
   if (rc == ME_OK && kind == K_REAL && mixed && !h->prm.queued_rescue && use_items(h, cap))
     rc = ensure_item_capacity(h, (size_t)cap);
   return rc;
@@ -944,11 +1049,14 @@ int me_internal_launch_counted(me_handle* h, int me_kind, const double* d_p, con
   a.resc_list = h->d_resc;
   a.resc_count = h->d_nresc;
   a.tiles = h->d_nresc + 1;
-  const bool queued = kind == K_REAL && mixed && h->prm.queued_rescue;
+  const bool terms = kind == K_REAL && h->prm.term_queues;
+  const bool cut_list = kind == K_TREE && h->prm.term_queues && a.kp.cut.mask;
+  const bool queued = kind == K_REAL && mixed && h->prm.queued_rescue && !terms;
   h->last_kind = K_TREE;
+  if (terms && (size_t)cap > h->tcap) return fail(ME_ERR_ARG, "counted launch: handle not prepared");
   if (kind == K_REAL && mixed) {
     a.kp.flag_unstable = 1;
-    if (!queued && use_items(h, cap)) {
+    if (!queued && !terms && use_items(h, cap)) {
       if ((size_t)cap > h->icap) return fail(ME_ERR_ARG, "counted launch: handle not prepared");
       a.kp.item_rescue = 1;
       a.items = h->ib;
@@ -956,11 +1064,20 @@ int me_internal_launch_counted(me_handle* h, int me_kind, const double* d_p, con
     ME_CUDA(cudaMemsetAsync(h->d_nresc, 0, 4 * sizeof(int), h->stream));
     h->last_kind = K_REAL;
   }
-  if (queued)
+  if (terms) {
+    ME_CUDA(launch_terms(h, 0, mixed, a));
+    if (mixed) ME_CUDA(launch_terms(h, 1, mixed, a));
+  } else if (queued) {
     ME_CUDA(launch_queued(h->proc->pid, a, h->stream));
-  else
+  } else {
+    if (cut_list) {
+      ME_CUDA(launch_cut_list(h->proc->pid, a, h->d_resc, h->d_nresc + 8, h->stream));
+      a.idx = h->d_resc;
+      a.count = h->d_nresc + 8;
+    }
     ME_CUDA(dispatch(h->proc->pid, kind, !mixed, lpe, a, h->stream));
-  if (kind == K_REAL && mixed && !queued) ME_CUDA(launch_rescue(h, a, lpe64));
+  }
+  if (kind == K_REAL && mixed && !queued && !terms) ME_CUDA(launch_rescue(h, a, lpe64));
   k_partials<<<RED_BLOCKS, 256, 0, h->stream>>>(d_out, cap, h->d_part, d_n);
   k_finish<<<1, 32, 0, h->stream>>>(h->d_part, RED_BLOCKS, h->d_acc, cap, d_n);
   ME_CUDA(cudaGetLastError());
@@ -1002,7 +1119,7 @@ int me_internal_kparams(const char* process, const me_params* params, me::KParam
   if (params->precision != ME_PREC_FP64 && params->precision != ME_PREC_MIXED)
     return fail(ME_ERR_ARG, "precision must be ME_PREC_FP64 or ME_PREC_MIXED");
   if (!(params->xi_cut > 0 && params->xi_cut <= 1) || !(params->delta > 0 && params->delta <= 2) ||
-      !(params->alpha_s > 0) || !(params->alpha > 0) || !(params->mt > 0))
+      !(params->alpha_s > 0) || !(params->alpha > 0) || !(params->mt > 0) || !cuts_valid(params))
     return fail(ME_ERR_ARG, "parameter out of range");
   const ProcDesc* pd = nullptr;
   for (const auto& d : kProcs)
@@ -1021,6 +1138,7 @@ int me_internal_kparams(const char* process, const me_params* params, me::KParam
   kp->y_thr = params->y_thr;
   kp->me_eps = params->me_eps;
   kp->tol = params->tol;
+  kp->cut = cuts_of(pd->pid, params);
   *pid = pd->pid;
   return ME_OK;
 }

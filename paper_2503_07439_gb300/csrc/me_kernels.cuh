@@ -44,6 +44,21 @@ struct ColourTables {
   double Ccorr[2][N_PAIRS][4];
 };
 
+// Cuts of one configuration (Algorithm 2's passCuts, applied to each term at its own
+// kinematics).  Each decision is an integer result taken in float64 with the operations
+// in a fixed order and no contraction, so that any implementation doing the same
+// operations on the same momenta decides alike:
+//   CUT_PT      both heavy quarks (legs 2, 3):  px*px + py*py >= pt2_min
+//   CUT_Y       both heavy quarks:  E + |pz| <= ey2 * (E - |pz|),  ey2 = exp(2 y_max)
+//   CUT_AXIS    e+e-: the most energetic final parton m (first of equal energies):
+//               pz*pz <= cos2_max * ((px*px + py*py) + pz*pz)  (thrust axis along p_m)
+//   CUT_THRUST  e+e-: 2 E_m <= thrust_max * (E_0 + E_1)  (thrust T = 2 E_m / sqrt(s))
+enum : unsigned { CUT_PT = 1u, CUT_Y = 2u, CUT_AXIS = 4u, CUT_THRUST = 8u };
+struct Cuts {
+  unsigned mask;  // 0: no cut
+  double pt2_min, ey2, cos2_max, thrust_max;
+};
+
 struct KParams {
   Couplings cp;
   double avg_inv;       // 1 / (initial spin x colour average), x identical-particle factor
@@ -56,6 +71,7 @@ struct KParams {
   int flag_unstable;    // 1: append unstable points to the rescue list
   int item_rescue;      // with flag_unstable: records and float64 items instead of the point list
   double item_budget;   // item rescue: residual error allowed, as a fraction of tol |W|
+  Cuts cut;             // cuts of every term (mask 0: none)
   const ColourTables* tab;
 };
 
@@ -136,6 +152,38 @@ __device__ __forceinline__ void load_event(const double* __restrict__ p, long n,
   }
 }
 
+// ---------------------------------------------------------------- cuts
+__device__ __forceinline__ bool heavy_pass(const r4<double>& q, const Cuts& c) {
+  bool ok = true;
+  if (c.mask & CUT_PT) ok = ok && __dadd_rn(__dmul_rn(q.x, q.x), __dmul_rn(q.y, q.y)) >= c.pt2_min;
+  if (c.mask & CUT_Y) {
+    const double a = fabs(q.z);
+    ok = ok && __dadd_rn(q.e, a) <= __dmul_rn(c.ey2, __dsub_rn(q.e, a));
+  }
+  return ok;
+}
+
+// passCuts of a configuration k of process PID (or of a Born counter-event of it)
+template <int PID>
+__device__ __forceinline__ bool pass_cuts(const r4<double>* k, const Cuts& c) {
+  if constexpr (PID == P_EE_UU || PID == P_EE_UUG) {
+    r4<double> m = k[2];
+#pragma unroll
+    for (int i = 3; i < Proc<PID>::NEXT; ++i)
+      if (k[i].e > m.e) m = k[i];
+    bool ok = true;
+    if (c.mask & CUT_AXIS) {
+      const double t = __dadd_rn(__dmul_rn(m.x, m.x), __dmul_rn(m.y, m.y));
+      const double z2 = __dmul_rn(m.z, m.z);
+      ok = ok && z2 <= __dmul_rn(c.cos2_max, __dadd_rn(t, z2));
+    }
+    if (c.mask & CUT_THRUST) ok = ok && 2.0 * m.e <= __dmul_rn(c.thrust_max, __dadd_rn(k[0].e, k[1].e));
+    return ok;
+  } else {
+    return heavy_pass(k[2], c) && heavy_pass(k[3], c);
+  }
+}
+
 // ---------------------------------------------------------------- tree |M|^2
 // float32 trees of 2 -> 2 processes fit 128 registers: 4 blocks per SM (16 warps) hide
 // their float64 preparation better than the 2 blocks of the heavier kernels
@@ -162,6 +210,8 @@ __global__ void __launch_bounds__(128, tree_min_blocks<PID, T>()) k_tree(const d
   const long ev = idx ? (long)idx[gid] : gid;
   r4<double> k[NEXT];
   load_event<NEXT>(p, n, ev, k);
+  // Algorithm 2: every point is evaluated, and zeroed below where it fails the cuts
+  const bool pass = !kp.cut.mask || pass_cuts<PID>(k, kp.cut);
   const Kin<PID, T> K = prepare<PID, T>(k, kp.cp);
   T acc = T(0);
   for (int b = lane; b < n_live_blocks<PID>(); b += LPE)
@@ -170,7 +220,7 @@ __global__ void __launch_bounds__(128, tree_min_blocks<PID, T>()) k_tree(const d
   const double tot = 2.0 * (double)group_sum<LPE>(acc, group_mask<LPE>());
   if (lane == 0) {
     const double w = wgt ? wgt[ev] : 1.0;
-    out[ev] = w * tot * kp.avg_inv * kp.nlo_factor;
+    out[ev] = pass ? w * tot * kp.avg_inv * kp.nlo_factor : 0.0;
   }
 }
 
@@ -386,7 +436,13 @@ __global__ void __launch_bounds__(TC4_THREADS, 2) k_tree_tc4(const double* __res
   const double tot = 2.0 * (double)group_sum<4>(acc, group_mask<4>());
   if (active && lane == 0) {
     const double w8 = wgt ? wgt[ev] : 1.0;
-    out[ev] = w8 * tot * kp.avg_inv * kp.nlo_factor;
+    bool pass = true;
+    if (kp.cut.mask) {
+      r4<double> kc[6];
+      load_event<6>(p, n, ev, kc);
+      pass = pass_cuts<P_GG_TTGG>(kc, kp.cut);
+    }
+    out[ev] = pass ? w8 * tot * kp.avg_inv * kp.nlo_factor : 0.0;
   }
 }
 
@@ -429,9 +485,13 @@ struct IsrKin {
   r4<double> coll[4];
   double qdir[3];         // gluon direction
   double cphi, sphi;      // gluon azimuth
+  // cuts (Algorithm 2) of the soft counter-event and of each sector's collinear one (its
+  // beam scaled by z): the two collinear Borns differ by a boost along the beam, which
+  // changes the heavy quarks' rapidities
+  bool cut_s, cut_c[2];
 };
 
-__device__ __forceinline__ void isr_map(const r4<double>* k, double mass, IsrKin& o) {
+__device__ __forceinline__ void isr_map(const r4<double>* k, double mass, IsrKin& o, const Cuts& cut) {
   const double rs = k[0].e + k[1].e, s = rs * rs, is = 1.0 / s;
   o.xi = 2.0 * k[4].e / rs;
   unit3(k[4], o.qdir[0], o.qdir[1], o.qdir[2]);
@@ -473,6 +533,15 @@ __device__ __forceinline__ void isr_map(const r4<double>* k, double mass, IsrKin
   const double Mc2 = mdot(Qc, Qc), iMc = rsqrt(Mc2);
   o.coll[2] = boost_by(tr, Qc, iMc, Mc2 * iMc, 1.0);
   o.coll[3] = boost_by(tbr, Qc, iMc, Mc2 * iMc, 1.0);
+  o.cut_s = o.cut_c[0] = o.cut_c[1] = true;
+  if (cut.mask) {
+    o.cut_s = heavy_pass(o.soft[2], cut) && heavy_pass(o.soft[3], cut);
+    o.cut_c[0] = heavy_pass(o.coll[2], cut) && heavy_pass(o.coll[3], cut);
+    const r4<double> Q1 = k[0] + scale(z, k[1]);
+    const double M12 = mdot(Q1, Q1), iM1 = rsqrt(M12);
+    o.cut_c[1] = heavy_pass(boost_by(tr, Q1, iM1, M12 * iM1, 1.0), cut) &&
+                 heavy_pass(boost_by(tbr, Q1, iM1, M12 * iM1, 1.0), cut);
+  }
   constexpr double i64pi3 = 1.0 / (64.0 * PI * PI * PI);
   o.K = s * bQ * i64pi3 / beta;
   o.K0 = s * i64pi3;
@@ -555,91 +624,112 @@ struct RealItems {
   double born_scale;    // error scale of the Born values together (as in RealSubOut::mag)
 };
 
-// Born values of the initial-state counterterms: v[0] = E (eikonal-weighted soft Born,
-// multiplies -4 g^2 / s in the soft limit), v[1] = B_s (soft Born), v[2] = B_c
-// (collinear Born), v[3], v[4] = B_p (spin-correlated Borns, g g only); every sum ran
-// over one helicity of each flipped pair (|M(h)|^2 = |M(-h)|^2), hence bav.
+// Eikonal-weighted colour-correlation matrix of the soft counter-event (2x2, row-major):
+// E = sum_{k,l} w_kl C^{kl}, w_kl = (p_k.p_l) / ((p_k.q)(p_l.q)), q = (1, gluon direction),
+// over the four coloured legs of the 2 -> 2 Born (k = l included); four reciprocals.
+template <int BPID>
+__device__ __forceinline__ void isr_eikonal_matrix(const IsrKin& f, const KParams& kp, double* E) {
+  const int ci = (BPID == P_GG_TT) ? 0 : 1;
+  E[0] = E[1] = E[2] = E[3] = 0.0;
+  const r4<double> qq{1.0, f.qdir[0], f.qdir[1], f.qdir[2]};
+  double iaq[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) iaq[a] = 1.0 / mdot(f.soft[a], qq);
+  int pr = 0;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = a; b < 4; ++b, ++pr) {
+      const double w = mdot(f.soft[a], f.soft[b]) * iaq[a] * iaq[b] * (a == b ? 1.0 : 2.0);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) E[q] += w * kp.tab->Ccorr[ci][pr][q];
+    }
+}
+
+// Born values of the soft counter-event kb: vE = E-weighted correlated Born (multiplies
+// -4 g^2 / s in the soft limit), vS = plain Born.  Every sum ran over one helicity of
+// each flipped pair (|M(h)|^2 = |M(-h)|^2), hence the factor 2.
+template <int BPID, typename T, int LPE>
+__device__ __forceinline__ void isr_soft_pair(const r4<double>* kb, const double* E, const KParams& kp, int lane,
+                                              unsigned mask, double& vE, double& vS) {
+  const T Et[4] = {(T)E[0], (T)E[1], (T)E[2], (T)E[3]};
+  T aE = T(0), aS = T(0);
+  const Kin<BPID, T> KB = prepare<BPID, T>(kb, kp.cp);
+  for (int b = lane; b < n_live_blocks<BPID>(); b += LPE)
+    amplitude_block<BPID, T>(KB, live_block_hel<BPID>(b), kp.cp, [&](int, const cx<T>* J) {
+      aE += quad2(Et, J);
+      aS += colour_sum<BPID, T>(kp.tab, J);
+    });
+  const double bav = 2.0 * kp.born_avg_inv;
+  vE = (double)group_sum<LPE>(aE, mask) * bav;
+  vS = (double)group_sum<LPE>(aS, mask) * bav;
+}
+
+// Born values of the collinear counter-event kb: v[0] = B_c (plain), and for g g the
+// spin-correlated Borns v[1], v[2] with gluon 0 or 1 polarised along the transverse
+// direction (0, cos phi, sin phi, 0) of the emission.
+template <int BPID, typename T, int LPE>
+__device__ __forceinline__ void isr_coll_set(const r4<double>* kb, double cphi, double sphi, const KParams& kp,
+                                             int lane, unsigned mask, double* v) {
+  c4<T> eperp;
+  eperp.v[0] = cx<T>{T(0), T(0)};
+  eperp.v[1] = cx<T>{(T)cphi, T(0)};
+  eperp.v[2] = cx<T>{(T)sphi, T(0)};
+  eperp.v[3] = cx<T>{T(0), T(0)};
+  T aC = T(0), aP[2] = {T(0), T(0)};
+  const Kin<BPID, T> KB = prepare<BPID, T>(kb, kp.cp);
+  for (int b = lane; b < n_live_blocks<BPID>(); b += LPE)
+    amplitude_block<BPID, T>(KB, live_block_hel<BPID>(b), kp.cp,
+                             [&](int, const cx<T>* J) { aC += colour_sum<BPID, T>(kp.tab, J); });
+  if constexpr (BPID == P_GG_TT) {
+    // polarised gluon 0; gluon 1 fixed to +, the heavy pair free (the flip covers the rest)
+    if (lane == 0)
+      amplitude_block<BPID, T>(
+          KB, 2, kp.cp, [&](int, const cx<T>* J) { aP[0] += colour_sum<BPID, T>(kp.tab, J); }, &eperp, 0);
+    // polarised gluon 1, gluon 0 fixed to +: sector 2's spin-correlated Born, at the
+    // same kinematics (invariant under the boost that relates the two sectors)
+    if (lane == 1 % LPE)
+      amplitude_block<BPID, T>(
+          KB, 1, kp.cp, [&](int, const cx<T>* J) { aP[1] += colour_sum<BPID, T>(kp.tab, J); }, &eperp, 1);
+  }
+  const double bav = 2.0 * kp.born_avg_inv;
+  v[0] = (double)group_sum<LPE>(aC, mask) * bav;
+  if constexpr (BPID == P_GG_TT) {
+    v[1] = (double)group_sum<LPE>(aP[0], mask) * bav;
+    v[2] = (double)group_sum<LPE>(aP[1], mask) * bav;
+  }
+}
+
+// Born values of the initial-state counterterms: v[0] = E (eikonal-weighted soft Born),
+// v[1] = B_s (soft Born), v[2] = B_c (collinear Born), v[3], v[4] = B_p (spin-correlated
+// Borns, g g only).
 template <int PID, typename T, int LPE>
 __device__ __forceinline__ void isr_born_values(const IsrKin& f, const KParams& kp, int lane, unsigned mask,
                                                 double* v) {
   constexpr int BPID = PID == P_GG_TTG ? P_GG_TT : P_UU_TT;
-  // eikonal-weighted colour-correlation matrix E = sum_{k,l} w_kl C^{kl} (2x2)
-  const int ci = (BPID == P_GG_TT) ? 0 : 1;
-  double E[4] = {0.0, 0.0, 0.0, 0.0};
-  {
-    // w_ab = (p_a.p_b) / ((p_a.q)(p_b.q)), q = (1, gluon direction): four reciprocals
-    const r4<double> qq{1.0, f.qdir[0], f.qdir[1], f.qdir[2]};
-    double iaq[4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) iaq[a] = 1.0 / mdot(f.soft[a], qq);
-    int pr = 0;
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = a; b < 4; ++b, ++pr) {
-        const double w = mdot(f.soft[a], f.soft[b]) * iaq[a] * iaq[b] * (a == b ? 1.0 : 2.0);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) E[q] += w * kp.tab->Ccorr[ci][pr][q];
-      }
-  }
-  const T Et[4] = {(T)E[0], (T)E[1], (T)E[2], (T)E[3]};
-  c4<T> eperp;
-  eperp.v[0] = cx<T>{T(0), T(0)};
-  eperp.v[1] = cx<T>{(T)f.cphi, T(0)};
-  eperp.v[2] = cx<T>{(T)f.sphi, T(0)};
-  eperp.v[3] = cx<T>{T(0), T(0)};
-  // Born tasks: soft Born (eikonal-weighted correlators and plain), collinear Born,
-  // and for g g the spin-correlated Born of each beam (the polarised gluon's bit unused)
-  T aE = T(0), aS = T(0), aC = T(0), aP[2] = {T(0), T(0)};
-  {
-    const Kin<BPID, T> KB = prepare<BPID, T>(f.soft, kp.cp);
-    for (int b = lane; b < n_live_blocks<BPID>(); b += LPE)
-      amplitude_block<BPID, T>(KB, live_block_hel<BPID>(b), kp.cp, [&](int, const cx<T>* J) {
-        aE += quad2(Et, J);
-        aS += colour_sum<BPID, T>(kp.tab, J);
-      });
-  }
-  {
-    const Kin<BPID, T> KB = prepare<BPID, T>(f.coll, kp.cp);
-    for (int b = lane; b < n_live_blocks<BPID>(); b += LPE)
-      amplitude_block<BPID, T>(KB, live_block_hel<BPID>(b), kp.cp,
-                               [&](int, const cx<T>* J) { aC += colour_sum<BPID, T>(kp.tab, J); });
-    if constexpr (BPID == P_GG_TT) {
-      // polarised gluon 0; gluon 1 fixed to +, the heavy pair free (the flip covers the rest)
-      if (lane == 0)
-        amplitude_block<BPID, T>(
-            KB, 2, kp.cp, [&](int, const cx<T>* J) { aP[0] += colour_sum<BPID, T>(kp.tab, J); }, &eperp, 0);
-      // polarised gluon 1, gluon 0 fixed to +: sector 2's spin-correlated Born, at the
-      // same kinematics (invariant under the boost that relates the two sectors)
-      if (lane == 1 % LPE)
-        amplitude_block<BPID, T>(
-            KB, 1, kp.cp, [&](int, const cx<T>* J) { aP[1] += colour_sum<BPID, T>(kp.tab, J); }, &eperp, 1);
-    }
-  }
-  const double bav = 2.0 * kp.born_avg_inv;
-  v[0] = (double)group_sum<LPE>(aE, mask) * bav;
-  v[1] = (double)group_sum<LPE>(aS, mask) * bav;
-  v[2] = (double)group_sum<LPE>(aC, mask) * bav;
-  if constexpr (BPID == P_GG_TT) {
-    v[3] = (double)group_sum<LPE>(aP[0], mask) * bav;
-    v[4] = (double)group_sum<LPE>(aP[1], mask) * bav;
-  }
+  double E[4];
+  isr_eikonal_matrix<BPID>(f, kp, E);
+  isr_soft_pair<BPID, T, LPE>(f.soft, E, kp, lane, mask, v[0], v[1]);
+  isr_coll_set<BPID, T, LPE>(f.coll, f.cphi, f.sphi, kp, lane, mask, v + 2);
+}
+
+// The Born |M|^2 of e+e- -> u ubar at kb (a final-state counterterm's Born).
+template <typename T, int LPE>
+__device__ __forceinline__ double fsr_born_one(const r4<double>* kb, const KParams& kp, int lane, unsigned mask) {
+  T aB = T(0);
+  const Kin<P_EE_UU, T> KB = prepare<P_EE_UU, T>(kb, kp.cp);
+  for (int b = lane; b < n_live_blocks<P_EE_UU>(); b += LPE)
+    amplitude_block<P_EE_UU, T>(KB, live_block_hel<P_EE_UU>(b), kp.cp,
+                                [&](int, const cx<T>* J) { aB += colour_sum<P_EE_UU, T>(kp.tab, J); });
+  return 2.0 * (double)group_sum<LPE>(aB, mask) * kp.born_avg_inv;
 }
 
 // Born values of the final-state counterterms: v[j] = the Born at sector j's kinematics.
 template <typename T, int LPE>
 __device__ __forceinline__ void fsr_born_values(const FsrKin& f, const KParams& kp, int lane, unsigned mask,
                                                 double* v) {
-  T aB[2] = {T(0), T(0)};
 #pragma unroll
-  for (int j = 0; j < 2; ++j) {
-    const Kin<P_EE_UU, T> KB = prepare<P_EE_UU, T>(f.born[j], kp.cp);
-    for (int b = lane; b < n_live_blocks<P_EE_UU>(); b += LPE)
-      amplitude_block<P_EE_UU, T>(KB, live_block_hel<P_EE_UU>(b), kp.cp,
-                                  [&](int, const cx<T>* J) { aB[j] += colour_sum<P_EE_UU, T>(kp.tab, J); });
-  }
-  v[0] = 2.0 * (double)group_sum<LPE>(aB[0], mask) * kp.born_avg_inv;
-  v[1] = 2.0 * (double)group_sum<LPE>(aB[1], mask) * kp.born_avg_inv;
+  for (int j = 0; j < 2; ++j) v[j] = fsr_born_one<T, LPE>(f.born[j], kp, lane, mask);
 }
 
 // One helicity block b of the real matrix element, colour-summed and averaged:
@@ -663,6 +753,8 @@ __device__ __forceinline__ RealSubOut real_sub_event(const double* __restrict__ 
   load_event<NEXT>(p, n, ev, k);
   const double rs = k[0].e + k[1].e, s = rs * rs;
   const double g2 = kp.cp.gs * kp.cp.gs;
+  // Algorithm 2's cut of the real term, at the real point
+  const double cR = (!kp.cut.mask || pass_cuts<PID>(k, kp.cut)) ? 1.0 : 0.0;
 
   // real matrix element; lane l holds blocks l, l + LPE, ... (one copy of the block code:
   // the loop is not unrolled)
@@ -694,39 +786,44 @@ __device__ __forceinline__ RealSubOut real_sub_event(const double* __restrict__ 
     xi_pt = f.xi;
     fsr_born_values<T, LPE>(f, kp, lane, mask, bv);
     const double* B = bv;
-    const double th_s = f.xi < kp.xi_cut ? 1.0 : 0.0;
+    // Algorithm 2's cuts: both counterterms of sector j at sector j's Born
+    const bool cuts = kp.cut.mask != 0;
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
+      const double cB = (!cuts || pass_cuts<P_EE_UU>(f.born[j], kp.cut)) ? 1.0 : 0.0;
+      const double th_s = f.xi < kp.xi_cut ? cB : 0.0;
       // soft: sum_{kl} w_kl B_kl with B_23 = B_32 = -C_F B (massless diagonal terms vanish)
       const double cs = (1.0 - f.y[j]) * 0.5 * (1.0 + f.y[j]) * f.K0 * (-(4.0 * g2 / s) * 2.0 * eik(f.born[j][2], f.born[j][3], f.qdir) * (-CF_));
       const double cc = f.K1 * (2.0 / (s * (1.0 - f.xi))) * 2.0 * g2 * CF_ * (1.0 + (1.0 - f.xi) * (1.0 - f.xi));
       const double csc = f.K0 * (2.0 / s) * 2.0 * g2 * 2.0 * CF_;
       const double Gs = cs * B[j], Gc = cc * B[j], Gsc = csc * B[j];
-      const double th_c = f.y[j] > 1.0 - kp.delta ? 1.0 : 0.0;
+      const double th_c = f.y[j] > 1.0 - kp.delta ? cB : 0.0;
       const double iden = 1.0 / (f.xi * f.xi * (1.0 - f.y[j]) * f.K[j]);
       const double ct = (th_s * Gs + th_c * Gc - th_s * th_c * Gsc) * iden;
-      const double rsj = R * f.S[j];
+      const double rsj = R * f.S[j] * cR;
       W += rsj - ct;
       // error scale: the real, the collinear term, and the soft pair (whose Borns are shared)
       mag += fabs(rsj) + fabs(th_c * Gc * iden) + fabs(th_s * (Gs - th_c * Gsc) * iden);
       near |= (th_s > 0.0 && f.xi < kp.xi_thr) || (th_c > 0.0 && 1.0 - f.y[j] < kp.y_thr);
-      a_R += f.S[j];
+      a_R += f.S[j] * cR;
       ab[j] = -(th_s * cs + th_c * cc - th_s * th_c * csc) * iden;
     }
   } else {
     constexpr int BPID = PID == P_GG_TTG ? P_GG_TT : P_UU_TT;
     IsrKin f;
-    isr_map(k, kp.cp.mt, f);
+    isr_map(k, kp.cp.mt, f, kp.cut);
     ysec[0] = f.y[0];
     ysec[1] = f.y[1];
     xi_pt = f.xi;
     isr_born_values<PID, T, LPE>(f, kp, lane, mask, bv);
+    // Algorithm 2's cuts (isr_map): soft and soft-collinear terms at the soft
+    // counter-event, the collinear term of sector j at sector j's collinear counter-event
     const double x2R = -(4.0 * g2 / s) * bv[0];
     const double Bs = bv[1], Bc = bv[2];
     const double Bp[2] = {BPID == P_GG_TT ? bv[3 % RealLayout<PID>::NBV] : 0.0,
                           BPID == P_GG_TT ? bv[4 % RealLayout<PID>::NBV] : 0.0};
     const double xi = f.xi, z = 1.0 - xi, iz = 1.0 / z, is2 = 2.0 / s;
-    const double th_s = xi < kp.xi_cut ? 1.0 : 0.0;
+    const double th_s = xi < kp.xi_cut && f.cut_s ? 1.0 : 0.0;
     // 1 / (xi^2 (1 - y_j) K) of both sectors from one reciprocal
     const double den0 = xi * xi * (1.0 - f.y[0]) * f.K, den1 = xi * xi * (1.0 - f.y[1]) * f.K;
     const double rden = 1.0 / (den0 * den1);
@@ -742,15 +839,16 @@ __device__ __forceinline__ RealSubOut real_sub_event(const double* __restrict__ 
       const double xiP0 = ks * Bs;
       const double Gc = f.K * is2 * iz * 2.0 * g2 * xiP;
       const double Gsc = f.K0 * is2 * 2.0 * g2 * xiP0;
-      const double th_c = f.y[j] > 1.0 - kp.delta ? 1.0 : 0.0;
-      const double ct = (th_s * Gs + th_c * Gc - th_s * th_c * Gsc) * iden[j];
-      const double rsj = R * f.S[j];
+      const double th_c = f.y[j] > 1.0 - kp.delta ? 1.0 : 0.0;  // soft-collinear term's
+      const double th_cc = f.cut_c[j] ? th_c : 0.0;             // collinear term's
+      const double ct = (th_s * Gs + th_cc * Gc - th_s * th_c * Gsc) * iden[j];
+      const double rsj = R * f.S[j] * cR;
       W += rsj - ct;
       // error scale: the real, the collinear term, and the soft pair (whose Borns are shared)
-      mag += fabs(rsj) + fabs(th_c * Gc * iden[j]) + fabs(th_s * (Gs - th_c * Gsc) * iden[j]);
-      near |= (th_s > 0.0 && xi < kp.xi_thr) || (th_c > 0.0 && 1.0 - f.y[j] < kp.y_thr);
-      a_R += f.S[j];
-      const double gcj = th_c * f.K * is2 * iz * 2.0 * g2 * iden[j];
+      mag += fabs(rsj) + fabs(th_cc * Gc * iden[j]) + fabs(th_s * (Gs - th_c * Gsc) * iden[j]);
+      near |= (th_s > 0.0 && xi < kp.xi_thr) || ((th_cc > 0.0 || th_s * th_c > 0.0) && 1.0 - f.y[j] < kp.y_thr);
+      a_R += f.S[j] * cR;
+      const double gcj = th_cc * f.K * is2 * iz * 2.0 * g2 * iden[j];
       ab[0] -= th_s * (1.0 - f.y[j]) * f.S[j] * f.K0 * (-(4.0 * g2 / s)) * iden[j];
       ab[1] += th_s * th_c * f.K0 * is2 * 2.0 * g2 * ks * iden[j];
       ab[2] -= gcj * kc;
@@ -944,7 +1042,7 @@ __global__ void __launch_bounds__(128, ME_MINB) k_rescue_items(const double* __r
         fsr_born_values<double, 1>(f, kp, 0, self, bv);
       } else {
         IsrKin f;
-        isr_map(k, kp.cp.mt, f);
+        isr_map(k, kp.cp.mt, f, Cuts{});  // the cuts are in the coefficients already
         isr_born_values<PID, double, 1>(f, kp, 0, self, bv);
       }
 #pragma unroll
@@ -1026,6 +1124,416 @@ __global__ void __launch_bounds__(QT, ME_MINB) k_real_sub_queued(const double* _
     if (last) break;
   }
   if (threadIdx.x == 0 && done > 0) atomicAdd(resc_count, done);
+}
+
+// ---------------------------------------------------------------- per-term queues
+// The variant of Algorithm 2 discussed after it (Sec. 4.3): rather than evaluating every
+// term of every point and masking the ones whose cuts fail, a float64 pass (k_terms) maps
+// each point, decides its cuts and counterterm regions, stores the coefficients of W =
+// sum_i a_i v_i, and queues only the amplitudes the point needs -- the real's helicity
+// blocks if the real passes its cuts, the soft Born set if the soft term is active and its
+// counter-event passes, the collinear Born set likewise, each with its counter-event
+// momenta.  k_term_items then evaluates every queued amplitude, one lane each, in one
+// launch over all queues; k_terms_combine recombines W (and, in mixed precision, applies
+// the stability test and queues the float64 items of the flagged points, which the same
+// item kernel evaluates in float64; k_terms_final recombines those).
+//
+// Value layout per record: v[b], b < NB, the real's blocks; then the Born values: initial
+// state v[NB] = E, v[NB+1] = B_s (set 0, soft counter-event), v[NB+2] = B_c, v[NB+3],
+// v[NB+4] = B_p (set 1, collinear counter-event); final state v[NB+j] = B_j (set j).
+struct TermBufs {
+  int* ev;      // [cap] point of the record
+  int* flags;   // [cap] bit 0: inside xi_thr / y_thr of an active counterterm
+  float* grow;  // [cap] error growth factor of the stability test
+  double* a;    // [MAX_ITEMS][cap] coefficients
+  double* v;    // [MAX_ITEMS][cap] values
+  double* m;    // [6][cap] error-scale coefficients of the Born values (term_born_scale)
+  int* cfg;     // [2][cap] the record's Born configurations, -1 for none
+  double* bp;   // [16][2 cap] configuration momenta, index (component * 4 + leg)
+  double* bx;   // [4][2 cap] set 0 (initial state): eikonal correlator matrix; set 1: cos, sin phi
+  int* bslot;   // [2 cap] record slot | set << 30
+  int* q_real;  // [4 cap] queued real blocks: slot * 4 + b (Born configurations are
+                //   queued as they are stored: 0 .. cnt[TC_QB] - 1)
+  int* r_real;  // [4 cap] float64 rescue: real blocks
+  int* r_born;  // [2 cap] float64 rescue: Born configurations
+  int* flagged; // [cap] records that failed the stability test
+  int* cnt;     // [8]: records, q_real, q_born, flagged, r_real, r_born
+  long cap;
+};
+enum : int { TC_REC = 0, TC_QR = 1, TC_QB = 2, TC_FLAG = 3, TC_RR = 4, TC_RB = 5 };
+
+// Reserve `c` consecutive entries of counter `ctr` for each lane of a full warp (every
+// lane calls it; c = 0 reserves nothing): one atomic per warp.  Returns the lane's base.
+__device__ __forceinline__ int warp_reserve(int* ctr, int c) {
+  const int lane = threadIdx.x & 31;
+  int incl = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  int base = 0;
+  if (lane == 31 && total > 0) base = atomicAdd(ctr, total);
+  base = __shfl_sync(0xffffffffu, base, 31);
+  return base + incl - c;
+}
+
+// Error scale of the Born values of a record (as RealSubOut::mag without the real):
+// initial state sum_j |m_2j E + m_2j+1 B_s| + |m_4+j B_c + cp_j B_p,j| with cp_j =
+// -a[NB+3+j] (g g); final state sum_j m_j |B_j|.
+template <int PID>
+__device__ __forceinline__ double term_born_scale(const TermBufs& tb, long slot) {
+  constexpr int NB = RealLayout<PID>::NB;
+  const long c = tb.cap;
+  const double* v = tb.v + NB * c + slot;
+  const double* m = tb.m + slot;
+  if constexpr (PID == P_EE_UUG) {
+    return m[0] * fabs(v[0]) + m[c] * fabs(v[c]);
+  } else {
+    const double E = v[0], Bs = v[c], Bc = v[2 * c];
+    double sc = fabs(m[0] * E + m[c] * Bs) + fabs(m[2 * c] * E + m[3 * c] * Bs);
+    if constexpr (PID == P_GG_TTG) {
+      const double* a = tb.a + NB * c + slot;
+      sc += fabs(m[4 * c] * Bc - a[3 * c] * v[3 * c]) + fabs(m[5 * c] * Bc - a[4 * c] * v[4 * c]);
+    } else {
+      sc += fabs(m[4 * c] * Bc) + fabs(m[5 * c] * Bc);
+    }
+    return sc;
+  }
+}
+
+// Float64 pass of the per-term queues: one thread per point (the counter-event maps,
+// the cuts of every term, the coefficients, and the queues).  Points with nothing left
+// to evaluate get weight 0 here.
+template <int PID>
+__global__ void __launch_bounds__(128) k_terms(const double* __restrict__ p, long n, double* __restrict__ out,
+                                               KParams kp, const int* __restrict__ count, TermBufs tb) {
+  constexpr int NEXT = Proc<PID>::NEXT, NB = RealLayout<PID>::NB, NBV = RealLayout<PID>::NBV;
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long nev = count ? (long)*count : n;
+  const bool act = i < nev;
+  r4<double> k[NEXT];
+  if (act) {
+    load_event<NEXT>(p, n, i, k);
+  } else {
+#pragma unroll
+    for (int l = 0; l < NEXT; ++l) k[l] = r4<double>{1.0, 0.0, 0.0, 0.0};
+  }
+  const double rs = k[0].e + k[1].e, s = rs * rs;
+  const double g2 = kp.cp.gs * kp.cp.gs;
+  const double cR = (!kp.cut.mask || pass_cuts<PID>(k, kp.cut)) ? 1.0 : 0.0;
+  double a_R = 0.0, ab[NBV] = {}, m[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  bool need[2] = {false, false}, near = false;
+  double xi, y0, y1;
+  r4<double> kb[2][4];
+  double bx[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+  double E[4] = {0.0, 0.0, 0.0, 0.0};
+  if constexpr (PID == P_EE_UUG) {
+    FsrKin f;
+    fsr_map(k, f);
+    xi = f.xi;
+    y0 = f.y[0];
+    y1 = f.y[1];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const double cB = (!kp.cut.mask || pass_cuts<P_EE_UU>(f.born[j], kp.cut)) ? 1.0 : 0.0;
+      const double th_s = f.xi < kp.xi_cut ? cB : 0.0;
+      const double th_c = f.y[j] > 1.0 - kp.delta ? cB : 0.0;
+      const double cs = (1.0 - f.y[j]) * 0.5 * (1.0 + f.y[j]) * f.K0 * (-(4.0 * g2 / s) * 2.0 * eik(f.born[j][2], f.born[j][3], f.qdir) * (-CF_));
+      const double cc = f.K1 * (2.0 / (s * (1.0 - f.xi))) * 2.0 * g2 * CF_ * (1.0 + (1.0 - f.xi) * (1.0 - f.xi));
+      const double csc = f.K0 * (2.0 / s) * 2.0 * g2 * 2.0 * CF_;
+      const double iden = 1.0 / (f.xi * f.xi * (1.0 - f.y[j]) * f.K[j]);
+      ab[j] = -(th_s * cs + th_c * cc - th_s * th_c * csc) * iden;
+      m[j] = fabs(th_c * cc * iden) + fabs(th_s * (cs - th_c * csc) * iden);
+      near |= (th_s > 0.0 && f.xi < kp.xi_thr) || (th_c > 0.0 && 1.0 - f.y[j] < kp.y_thr);
+      a_R += f.S[j] * cR;
+      need[j] = th_s > 0.0 || th_c > 0.0;
+#pragma unroll
+      for (int l = 0; l < 4; ++l) kb[j][l] = f.born[j][l];
+    }
+  } else {
+    constexpr int BPID = PID == P_GG_TTG ? P_GG_TT : P_UU_TT;
+    IsrKin f;
+    isr_map(k, kp.cp.mt, f, kp.cut);
+    xi = f.xi;
+    y0 = f.y[0];
+    y1 = f.y[1];
+    const double z = 1.0 - xi, iz = 1.0 / z, is2 = 2.0 / s;
+    const double th_s = xi < kp.xi_cut && f.cut_s ? 1.0 : 0.0;
+    const double den0 = xi * xi * (1.0 - f.y[0]) * f.K, den1 = xi * xi * (1.0 - f.y[1]) * f.K;
+    const double rden = 1.0 / (den0 * den1);
+    const double iden[2] = {den1 * rden, den0 * rden};
+    const double kc = BPID == P_GG_TT ? 2.0 * CA_ * (z + xi * xi * z) : CF_ * (1.0 + z * z);
+    const double kp_ = BPID == P_GG_TT ? 2.0 * CA_ * 2.0 * (xi * xi * iz) : 0.0;
+    const double ks = BPID == P_GG_TT ? 2.0 * CA_ : 2.0 * CF_;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const double th_c = f.y[j] > 1.0 - kp.delta ? 1.0 : 0.0;
+      const double th_cc = f.cut_c[j] ? th_c : 0.0;
+      a_R += f.S[j] * cR;
+      const double sE = th_s * (1.0 - f.y[j]) * f.S[j] * f.K0 * (-(4.0 * g2 / s)) * iden[j];
+      const double sB = -th_s * th_c * f.K0 * is2 * 2.0 * g2 * ks * iden[j];
+      const double gcj = th_cc * f.K * is2 * iz * 2.0 * g2 * iden[j];
+      ab[0] -= sE;
+      ab[1] -= sB;
+      ab[2] -= gcj * kc;
+      if constexpr (BPID == P_GG_TT) ab[3 + j] = -gcj * kp_;
+      m[2 * j] = sE;
+      m[2 * j + 1] = sB;
+      m[4 + j] = gcj * kc;
+      near |= (th_s > 0.0 && xi < kp.xi_thr) || ((th_cc > 0.0 || th_s * th_c > 0.0) && 1.0 - f.y[j] < kp.y_thr);
+      need[1] |= th_cc > 0.0;
+    }
+    need[0] = th_s > 0.0;
+    if (need[0]) isr_eikonal_matrix<BPID>(f, kp, E);
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      kb[0][l] = f.soft[l];
+      kb[1][l] = f.coll[l];
+    }
+    bx[1][0] = f.cphi;
+    bx[1][1] = f.sphi;
+  }
+  // the boundary of the FKS domain has measure zero and weight 0 (see real_sub_event)
+  const bool inside = act && xi > 0.0 && xi < 1.0 && 1.0 - y0 > 0.0 && 1.0 - y1 > 0.0;
+  const bool need_real = inside && cR > 0.0;
+  need[0] = need[0] && inside;
+  need[1] = need[1] && inside;
+  const bool rec = need_real || need[0] || need[1];
+  if (act && !rec) out[i] = 0.0;
+  const int slot = warp_reserve(tb.cnt + TC_REC, rec ? 1 : 0);
+  const int qr = warp_reserve(tb.cnt + TC_QR, need_real ? NB : 0);
+  const int qb = warp_reserve(tb.cnt + TC_QB, (need[0] ? 1 : 0) + (need[1] ? 1 : 0));
+  if (!rec) return;
+  const long c = tb.cap, c2 = 2 * tb.cap;
+  tb.ev[slot] = (int)i;
+  tb.flags[slot] = near ? 1 : 0;
+  const float rho = fmaxf((float)fmin(1.0 - y0, 1.0 - y1), 1e-30f);
+  tb.grow[slot] = 1.0f + sqrtf(0.01f / rho);
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    tb.a[b * c + slot] = need_real ? a_R : 0.0;
+    tb.v[b * c + slot] = 0.0;
+  }
+#pragma unroll
+  for (int t = 0; t < NBV; ++t) {
+    tb.a[(NB + t) * c + slot] = ab[t];
+    tb.v[(NB + t) * c + slot] = 0.0;
+  }
+#pragma unroll
+  for (int r = 0; r < 6; ++r) tb.m[r * c + slot] = m[r];
+  if (need_real)
+#pragma unroll
+    for (int b = 0; b < NB; ++b) tb.q_real[qr + b] = slot * 4 + b;
+  int ci = qb;
+#pragma unroll
+  for (int set = 0; set < 2; ++set) {
+    tb.cfg[set * c + slot] = need[set] ? ci : -1;
+    if (!need[set]) continue;
+    tb.bslot[ci] = slot | (set << 30);
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      tb.bp[(0 * 4 + l) * c2 + ci] = kb[set][l].e;
+      tb.bp[(1 * 4 + l) * c2 + ci] = kb[set][l].x;
+      tb.bp[(2 * 4 + l) * c2 + ci] = kb[set][l].y;
+      tb.bp[(3 * 4 + l) * c2 + ci] = kb[set][l].z;
+    }
+    if constexpr (PID != P_EE_UUG) {
+      if (set == 0) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) tb.bx[q * c2 + ci] = E[q];
+      } else {
+        tb.bx[0 * c2 + ci] = bx[1][0];
+        tb.bx[1 * c2 + ci] = bx[1][1];
+      }
+    }
+    ++ci;
+  }
+}
+
+// Every queued amplitude, one lane each, in precision T: real blocks (from the point's
+// momenta) and Born configurations (from the stored counter-event momenta), in one index
+// space (real blocks first).  `rescue` selects the float64 rescue queues.
+template <int PID, typename T>
+__global__ void __launch_bounds__(128, ME_MINB) k_term_items(const double* __restrict__ p, long n, KParams kp,
+                                                             int rescue, TermBufs tb) {
+  constexpr int NEXT = Proc<PID>::NEXT, NB = RealLayout<PID>::NB;
+  const int* qr = rescue ? tb.r_real : tb.q_real;
+  const long nr = tb.cnt[rescue ? TC_RR : TC_QR];
+  const long nt = nr + tb.cnt[rescue ? TC_RB : TC_QB];
+  const long c = tb.cap, c2 = 2 * tb.cap;
+  const unsigned self = 1u << (threadIdx.x & 31u);
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += (long)gridDim.x * blockDim.x) {
+    if (t < nr) {
+      const int item = qr[t], slot = item >> 2, b = item & 3;
+      r4<double> k[NEXT];
+      load_event<NEXT>(p, n, tb.ev[slot], k);
+      const Kin<PID, T> K = prepare<PID, T>(k, kp.cp);
+      tb.v[b * c + slot] = real_block_value<PID, T>(K, b, kp);
+    } else {
+      const int ci = rescue ? tb.r_born[t - nr] : (int)(t - nr);
+      const int bs = tb.bslot[ci], slot = bs & 0x3fffffff, set = bs >> 30;
+      r4<double> kb[4];
+#pragma unroll
+      for (int l = 0; l < 4; ++l)
+        kb[l] = r4<double>{tb.bp[(0 * 4 + l) * c2 + ci], tb.bp[(1 * 4 + l) * c2 + ci], tb.bp[(2 * 4 + l) * c2 + ci],
+                           tb.bp[(3 * 4 + l) * c2 + ci]};
+      if constexpr (PID == P_EE_UUG) {
+        tb.v[(NB + set) * c + slot] = fsr_born_one<T, 1>(kb, kp, 0, self);
+      } else {
+        constexpr int BPID = PID == P_GG_TTG ? P_GG_TT : P_UU_TT;
+        if (set == 0) {
+          const double E[4] = {tb.bx[0 * c2 + ci], tb.bx[1 * c2 + ci], tb.bx[2 * c2 + ci], tb.bx[3 * c2 + ci]};
+          double vE, vS;
+          isr_soft_pair<BPID, T, 1>(kb, E, kp, 0, self, vE, vS);
+          tb.v[NB * c + slot] = vE;
+          tb.v[(NB + 1) * c + slot] = vS;
+        } else {
+          double vc[3];
+          isr_coll_set<BPID, T, 1>(kb, tb.bx[0 * c2 + ci], tb.bx[1 * c2 + ci], kp, 0, self, vc);
+          tb.v[(NB + 2) * c + slot] = vc[0];
+          if constexpr (BPID == P_GG_TT) {
+            tb.v[(NB + 3) * c + slot] = vc[1];
+            tb.v[(NB + 4) * c + slot] = vc[2];
+          }
+        }
+      }
+    }
+  }
+}
+
+// W of every record; in mixed precision (kp.flag_unstable) the stability test of
+// real_sub_event and the item selection of rescue_mask, with the flagged records' float64
+// items queued (whole warps iterate together for the aggregated appends).
+template <int PID>
+__global__ void __launch_bounds__(128) k_terms_combine(const double* __restrict__ wgt, double* __restrict__ out,
+                                                       KParams kp, TermBufs tb) {
+  constexpr int NB = RealLayout<PID>::NB, NI = RealLayout<PID>::NI;
+  const long nrec = tb.cnt[TC_REC];
+  const long c = tb.cap;
+  const int lane = threadIdx.x & 31;
+  const long stride = (long)gridDim.x * blockDim.x;
+  for (long t0 = (long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); t0 < nrec; t0 += stride) {
+    const long slot = t0 + lane;
+    const bool act = slot < nrec;
+    double W = 0.0;
+    bool flag = false;
+    unsigned msk = 0;
+    int ev = 0;
+    if (act) {
+#pragma unroll
+      for (int q = 0; q < NI; ++q) W += tb.a[q * c + slot] * tb.v[q * c + slot];
+      ev = tb.ev[slot];
+      if (kp.flag_unstable) {
+        double R = 0.0;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) R += tb.v[b * c + slot];
+        const double bsc = term_born_scale<PID>(tb, slot);
+        const double mag = fabs(tb.a[slot] * R) + bsc;
+        const double grow = (double)tb.grow[slot];
+        const bool near = tb.flags[slot] & 1;
+        flag = near || !(mag * grow * kp.me_eps <= kp.tol * fabs(W));
+        if (flag) {
+          constexpr unsigned all = (1u << (NB + 1)) - 1u;
+          if (near) {
+            msk = all;
+          } else {
+            double e[NB + 1];
+            double rest = 0.0;
+#pragma unroll
+            for (int b = 0; b < NB; ++b) rest += (e[b] = fabs(tb.a[b * c + slot] * tb.v[b * c + slot]));
+            rest += (e[NB] = bsc);
+            const double budget = kp.item_budget * kp.tol * fabs(W) / (grow * kp.me_eps);
+#pragma unroll
+            for (int kk = 0; kk <= NB; ++kk) {
+              if (!(rest > budget)) break;
+              int pick = -1;
+              double best = -1.0;
+#pragma unroll
+              for (int b = 0; b <= NB; ++b)
+                if (!(msk >> b & 1u) && e[b] > best) {
+                  best = e[b];
+                  pick = b;
+                }
+              if (pick < 0) break;
+              msk |= 1u << pick;
+              rest -= best;
+            }
+            if (!msk) msk = all;
+          }
+          // real blocks with a zero coefficient (the real failed its cuts) stay as they are
+          if (tb.a[slot] == 0.0) msk &= ~((1u << NB) - 1u);
+        }
+      }
+      if (!flag) out[ev] = (wgt ? wgt[ev] : 1.0) * W;
+    }
+    // queue the flagged records' float64 items (every lane of the warp takes part)
+    const int nbl = __popc(msk & ((1u << NB) - 1u));
+    int ncf = 0;
+    if (msk >> NB & 1u) ncf = (tb.cfg[slot] >= 0 ? 1 : 0) + (tb.cfg[c + slot] >= 0 ? 1 : 0);
+    const int fb = warp_reserve(tb.cnt + TC_FLAG, flag ? 1 : 0);
+    const int rb = warp_reserve(tb.cnt + TC_RR, nbl);
+    const int cb = warp_reserve(tb.cnt + TC_RB, ncf);
+    if (flag) {
+      tb.flagged[fb] = (int)slot;
+      int r = rb;
+#pragma unroll
+      for (int b = 0; b < NB; ++b)
+        if (msk >> b & 1u) tb.r_real[r++] = (int)slot * 4 + b;
+      int q = cb;
+      if (msk >> NB & 1u)
+#pragma unroll
+        for (int set = 0; set < 2; ++set) {
+          const int ci = tb.cfg[set * c + slot];
+          if (ci >= 0) tb.r_born[q++] = ci;
+        }
+    }
+  }
+}
+
+// W of the flagged records after their float64 items; thread 0 of block 0 copies the
+// rescue counts to `counts` ([0] flagged points, [2] real blocks, [3] Born configurations,
+// the layout me_last_rescue_work reads).
+template <int PID>
+__global__ void k_terms_final(const double* __restrict__ wgt, double* __restrict__ out, TermBufs tb,
+                              int* __restrict__ counts) {
+  constexpr int NI = RealLayout<PID>::NI;
+  const long nf = tb.cnt[TC_FLAG];
+  const long c = tb.cap;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && counts) {
+    counts[0] = tb.cnt[TC_FLAG];
+    counts[2] = tb.cnt[TC_RR];
+    counts[3] = tb.cnt[TC_RB];
+  }
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < nf; t += (long)gridDim.x * blockDim.x) {
+    const long slot = tb.flagged[t];
+    double W = 0.0;
+#pragma unroll
+    for (int q = 0; q < NI; ++q) W += tb.a[q * c + slot] * tb.v[q * c + slot];
+    const int ev = tb.ev[slot];
+    out[ev] = (wgt ? wgt[ev] : 1.0) * W;
+  }
+}
+
+// Tree-level entries with per-term queues: the points that pass the cuts are listed
+// (list, *listed); the others get weight 0.
+template <int PID>
+__global__ void __launch_bounds__(128) k_cut_list(const double* __restrict__ p, long n, const int* __restrict__ count,
+                                                  double* __restrict__ out, KParams kp, int* __restrict__ list,
+                                                  int* __restrict__ listed) {
+  constexpr int NEXT = Proc<PID>::NEXT;
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long nev = count ? (long)*count : n;
+  bool pass = false;
+  if (i < nev) {
+    r4<double> k[NEXT];
+    load_event<NEXT>(p, n, i, k);
+    pass = pass_cuts<PID>(k, kp.cut);
+    if (!pass) out[i] = 0.0;
+  }
+  const int at = warp_reserve(listed, pass ? 1 : 0);
+  if (pass) list[at] = (int)i;
 }
 
 // ---------------------------------------------------------------- weight accumulation
@@ -1158,6 +1666,56 @@ cudaError_t launch_queued_one(const LaunchArgs& a, cudaStream_t st) {
   k_real_sub_queued<PID><<<blocks, QT, 0, st>>>(a.p, a.wgt, a.n, a.out, a.kp, a.count, a.tiles, a.resc_count);
   return cudaGetLastError();
 }
+
+// Per-term queues (k_terms ... k_terms_final): phase 0 enqueues the float64 pass, the
+// bulk-precision items and the recombination (with the stability test in mixed
+// precision); phase 1 the float64 rescue items and the flagged points' recombination
+// (mixed precision only), and copies the rescue counts to `counts`.
+template <int PID>
+cudaError_t launch_terms_one(int phase, bool mixed, const LaunchArgs& a, const TermBufs& tb, int* counts,
+                             cudaStream_t st) {
+  (void)cudaGetLastError();
+  static std::atomic<int> resident[2][64];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  const bool f64 = phase == 1 || !mixed;
+  int g = resident[f64][dev].load(std::memory_order_relaxed);
+  if (g == 0) {
+    int per = 0, sms = 0;
+    e = f64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_term_items<PID, double>, 128, 0)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_term_items<PID, float>, 128, 0);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    g = (per > 0 ? per : 1) * (sms > 0 ? sms : 1);
+    resident[f64][dev].store(g, std::memory_order_relaxed);
+  }
+  const long items_cap = (RealLayout<PID>::NB + 2) * tb.cap;
+  const unsigned gi = (unsigned)std::max(1L, std::min<long>(g, (items_cap + 127) / 128));
+  const unsigned gc = (unsigned)std::max(1L, std::min<long>(4 * g, (tb.cap + 127) / 128));
+  if (phase == 0) {
+    if ((e = cudaMemsetAsync(tb.cnt, 0, 8 * sizeof(int), st)) != cudaSuccess) return e;
+    const long blocks = (a.groups + 127) / 128;
+    if (blocks <= 0) return cudaSuccess;
+    k_terms<PID><<<(unsigned)blocks, 128, 0, st>>>(a.p, a.n, a.out, a.kp, a.count, tb);
+    if (mixed)
+      k_term_items<PID, float><<<gi, 128, 0, st>>>(a.p, a.n, a.kp, 0, tb);
+    else
+      k_term_items<PID, double><<<gi, 128, 0, st>>>(a.p, a.n, a.kp, 0, tb);
+    k_terms_combine<PID><<<gc, 128, 0, st>>>(a.wgt, a.out, a.kp, tb);
+  } else {
+    k_term_items<PID, double><<<gi, 128, 0, st>>>(a.p, a.n, a.kp, 1, tb);
+    k_terms_final<PID><<<gc, 128, 0, st>>>(a.wgt, a.out, tb, counts);
+  }
+  return cudaGetLastError();
+}
+cudaError_t launch_terms_ee(int phase, bool mixed, const LaunchArgs& a, const TermBufs& tb, int* counts, cudaStream_t st);
+cudaError_t launch_terms_gg(int phase, bool mixed, const LaunchArgs& a, const TermBufs& tb, int* counts, cudaStream_t st);
+cudaError_t launch_terms_uu(int phase, bool mixed, const LaunchArgs& a, const TermBufs& tb, int* counts, cudaStream_t st);
+// tree entries with per-term queues: list the points that pass the cuts (k_cut_list)
+cudaError_t launch_cut_list(int pid, const LaunchArgs& a, int* list, int* listed, cudaStream_t st);
 
 }  // namespace me
 

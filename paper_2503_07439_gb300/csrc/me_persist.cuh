@@ -87,7 +87,8 @@ __device__ __forceinline__ double tree_point(const double* __restrict__ p, long 
   T acc = T(0);
   for (int b = 0; b < n_live_blocks<PID>(); ++b)
     amplitude_block<PID, T>(K, live_block_hel<PID>(b), kp.cp, [&](int, const cx<T>* J) { acc += colour_sum<PID, T>(kp.tab, J); });
-  return 2.0 * (double)acc * kp.avg_inv;
+  // Algorithm 2: evaluated, then zeroed where the point fails the cuts
+  return (!kp.cut.mask || pass_cuts<PID>(k, kp.cut)) ? 2.0 * (double)acc * kp.avg_inv : 0.0;
 }
 
 // Family (BPID: its Born process, RPID: its real process), precision fixed per server.

@@ -57,3 +57,34 @@ def test_noalloc_buffer_rule_refuses_other_devices(lib):
     assert f(device, 1, 0) == 0 and f(device, 0, 1) == 0
     assert f(managed, 0, 1) == 1
     assert f(host, 0, 0) == 0 and f(unregistered, 0, 0) == 0
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Field offsets and sizes of the ctypes structures equal those of the C header
+    (compiled with the host C compiler)."""
+    import shutil
+    import subprocess
+    import paper_2503_07439_gb300 as me
+    from paper_2503_07439_gb300 import _capi
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    structs = {"me_params": _capi.MEParams, "me_server_params": _capi.MEServerParams,
+               "me_request": _capi.MERequest, "me_result": _capi.MEResult}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "me.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append(f'  printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines.append("  return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, cls in structs.items():
+        assert got[(cname, "sizeof")] == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
+    assert me.default_params().cut_abs_y_max == float("inf") and me.default_params().term_queues == 0
