@@ -817,6 +817,8 @@ static int run(me_handle* h, int kind, double nlo_factor, const double* momenta,
   const bool terms = kind == K_REAL && h->prm.term_queues;
   const bool cut_list = kind == K_TREE && h->prm.term_queues && a.kp.cut.mask;
   const bool queued = kind == K_REAL && mixed && h->prm.queued_rescue && !terms;
+  // the queues encode slot * 4 + block in 32 bits
+  if (terms && n >= (int64_t)1 << 29) return fail(ME_ERR_ARG, "term_queues: at most 2^29 - 1 points per call");
   if (terms && (rc = ensure_term_capacity(h, (size_t)n)) != ME_OK) return rc;
   if (kind == K_REAL && mixed) {
     a.kp.flag_unstable = 1;
@@ -1023,7 +1025,10 @@ int me_internal_prepare_counted(me_handle* h, int me_kind, int64_t cap) {
     return fail(ME_ERR_ARG, "counted launch: run one ordinary call of this kind first");
   ME_CUDA(cudaSetDevice(h->device));
   int rc = ensure_capacity(h, (size_t)cap);
-  if (rc == ME_OK && kind == K_REAL && h->prm.term_queues) return ensure_term_capacity(h, (size_t)cap);
+  if (rc == ME_OK && kind == K_REAL && h->prm.term_queues) {
+    if (cap >= (int64_t)1 << 29) return fail(ME_ERR_ARG, "term_queues: at most 2^29 - 1 points per call");
+    return ensure_term_capacity(h, (size_t)cap);
+  }
   if (rc == ME_OK && kind == K_REAL && mixed && !h->prm.queued_rescue && use_items(h, cap))
     rc = ensure_item_capacity(h, (size_t)cap);
   return rc;
