@@ -37,6 +37,7 @@ SEED = 4
 N_POINTS = 1 << 20
 METRIC = "NLO real-minus-counterterm events/s (gg->ttg, FKS, 1 GB300)"
 UNIT = "events/s"
+CUT_PT_MIN, CUT_ABS_Y_MAX = 100.0, 1.0  # heavy-quark cuts of the per-term queue comparison
 WORKLOAD = ("gg->ttg real-emission minus FKS soft/collinear counterterms, sqrt(s)=1 TeV, m_t=173, "
             "2^20 flat massive-RAMBO points, mixed precision (fp32 amplitudes; fp64 re-evaluation of the "
             "flagged points' real-emission blocks and counterterm Borns that their tolerance needs)")
@@ -498,11 +499,11 @@ def measure(me, mebuild, workload, args, n, rank, world, local, dist, full):
         calls.append((proc, entry, bb))
     stream = torch.cuda.Stream()
 
-    def make(prec, queued=args.queued_rescue):
+    def make(prec, queued=args.queued_rescue, **extra):
         hs = []
         for proc, entry, bb in calls:
             hh = me.Handle(proc, precision=prec, device=local, lanes_per_event=args.lanes_per_event,
-                           queued_rescue=int(queued))
+                           queued_rescue=int(queued), **extra)
             hh.set_stream(stream.cuda_stream)
             hs.append((hh, getattr(hh, entry), torch.from_numpy(bb.p).cuda(), torch.from_numpy(bb.wgt).cuda(),
                        torch.empty(n, dtype=torch.float64, device="cuda")))
@@ -571,6 +572,20 @@ def measure(me, mebuild, workload, args, n, rank, world, local, dist, full):
         alt = {"value": n / (alt_ms * 1e-3), "unit": UNIT, "ms_per_step": alt_ms,
                "rescue": "float32 launch, then float64 launch over the compacted list" if args.queued_rescue else
                          "queued one-launch kernel"}
+    terms = None
+    if full and has_real:
+        # cuts of every term (Algorithm 2, masked) against the per-term queues, without
+        # and with the cuts of a t tbar analysis (both heavy quarks: p_T >= 100 GeV,
+        # |y| <= 1); mixed precision, the same batches
+        cut = dict(cut_pt_min=CUT_PT_MIN, cut_abs_y_max=CUT_ABS_Y_MAX)
+        terms = {"cuts": {"heavy_quark_pt_min_gev": CUT_PT_MIN, "heavy_quark_abs_y_max": CUT_ABS_Y_MAX}}
+        for label, extra in (("masked", {}), ("queued", {"term_queues": 1}), ("masked_cuts", cut),
+                             ("queued_cuts", dict(cut, term_queues=1))):
+            hs = make(me.ME_PREC_MIXED, **extra)
+            t_ms = time_steps(hs, max(3, args.fp64_steps))
+            kept = float(sum(torch.count_nonzero(od).item() for *_, od in hs)) / (n * len(hs))
+            terms[label] = {"value": n / (t_ms * 1e-3), "unit": UNIT, "ms_per_step": t_ms,
+                            "points_with_weight": kept}
     if full and all(proc != "gg_tt" for proc, _, _ in calls):
         # the same step with the points generated on the device every step (Philox4x32-10
         # + RAMBO, me_generate_flat)
@@ -637,7 +652,7 @@ def measure(me, mebuild, workload, args, n, rank, world, local, dist, full):
         "l2": wl["l2"],
         "fp64_path": {"value": fp64_value, "unit": UNIT, "ms_per_step": fp64_ms,
                       "mixed_over_fp64": value / world / fp64_value},
-        "other_rescue_path": alt, "rescued_per_step": rescued,
+        "other_rescue_path": alt, "per_term_queues": terms, "rescued_per_step": rescued,
         "rescue_work_per_step": [{"process": c[0], "points": st[5][0], "real_blocks": st[5][1],
                                   "born_sets": st[5][2]} for c, st in zip(calls, stages)],
         "stage_ms_per_step": [{"process": c[0], "main_kernel": st[0] / max(1, st[3]),
@@ -726,6 +741,7 @@ def main():
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "fp64_path": head["fp64_path"],
         "other_rescue_path": head["other_rescue_path"],
+        "per_term_queues": head["per_term_queues"],
         "rescued_per_step": head["rescued_per_step"],
         "rescue_work_per_step": head["rescue_work_per_step"],
         "stage_ms_per_step": head["stage_ms_per_step"],
