@@ -479,7 +479,7 @@ static int ensure_term_capacity(me_handle* h, size_t n) {
             cudaMalloc(&t.bp, c * 2 * 16 * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&t.bx, c * 2 * 4 * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&t.bslot, c * 2 * sizeof(int)) == cudaSuccess &&
-            cudaMalloc(&t.q_real, c * 4 * sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&t.q_real, c * sizeof(int)) == cudaSuccess &&
             cudaMalloc(&t.r_real, c * 4 * sizeof(int)) == cudaSuccess &&
             cudaMalloc(&t.r_born, c * 2 * sizeof(int)) == cudaSuccess &&
             cudaMalloc(&t.flagged, c * sizeof(int)) == cudaSuccess && cudaMalloc(&t.cnt, 8 * sizeof(int)) == cudaSuccess;

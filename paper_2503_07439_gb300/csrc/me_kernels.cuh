@@ -1152,9 +1152,9 @@ struct TermBufs {
   double* bp;   // [16][2 cap] configuration momenta, index (component * 4 + leg)
   double* bx;   // [4][2 cap] set 0 (initial state): eikonal correlator matrix; set 1: cos, sin phi
   int* bslot;   // [2 cap] record slot | set << 30
-  int* q_real;  // [4 cap] queued real blocks: slot * 4 + b (Born configurations are
-                //   queued as they are stored: 0 .. cnt[TC_QB] - 1)
-  int* r_real;  // [4 cap] float64 rescue: real blocks
+  int* q_real;  // [cap] records whose real is evaluated (every block in one lane; Born
+                //   configurations are queued as they are stored: 0 .. cnt[TC_QB] - 1)
+  int* r_real;  // [4 cap] float64 rescue: real blocks, slot * 4 + b
   int* r_born;  // [2 cap] float64 rescue: Born configurations
   int* flagged; // [cap] records that failed the stability test
   int* cnt;     // [8]: records, q_real, q_born, flagged, r_real, r_born
@@ -1303,7 +1303,7 @@ __global__ void __launch_bounds__(128) k_terms(const double* __restrict__ p, lon
   const bool rec = need_real || need[0] || need[1];
   if (act && !rec) out[i] = 0.0;
   const int slot = warp_reserve(tb.cnt + TC_REC, rec ? 1 : 0);
-  const int qr = warp_reserve(tb.cnt + TC_QR, need_real ? NB : 0);
+  const int qr = warp_reserve(tb.cnt + TC_QR, need_real ? 1 : 0);
   const int qb = warp_reserve(tb.cnt + TC_QB, (need[0] ? 1 : 0) + (need[1] ? 1 : 0));
   if (!rec) return;
   const long c = tb.cap, c2 = 2 * tb.cap;
@@ -1323,9 +1323,7 @@ __global__ void __launch_bounds__(128) k_terms(const double* __restrict__ p, lon
   }
 #pragma unroll
   for (int r = 0; r < 6; ++r) tb.m[r * c + slot] = m[r];
-  if (need_real)
-#pragma unroll
-    for (int b = 0; b < NB; ++b) tb.q_real[qr + b] = slot * 4 + b;
+  if (need_real) tb.q_real[qr] = slot;
   int ci = qb;
 #pragma unroll
   for (int set = 0; set < 2; ++set) {
@@ -1352,12 +1350,14 @@ __global__ void __launch_bounds__(128) k_terms(const double* __restrict__ p, lon
   }
 }
 
-// Every queued amplitude, one lane each, in precision T: real blocks (from the point's
-// momenta) and Born configurations (from the stored counter-event momenta), in one index
-// space (real blocks first).  `rescue` selects the float64 rescue queues.
-template <int PID, typename T>
+// Every queued amplitude, one lane each, in precision T: reals (from the point's momenta;
+// all helicity blocks of a point in one lane, or one block per lane in the rescue queue)
+// and Born configurations (from the stored counter-event momenta), in one index space
+// (reals first).  RESCUE selects the float64 rescue queues.
+template <int PID, typename T, bool RESCUE>
 __global__ void __launch_bounds__(128, ME_MINB) k_term_items(const double* __restrict__ p, long n, KParams kp,
-                                                             int rescue, TermBufs tb) {
+                                                             TermBufs tb) {
+  constexpr bool rescue = RESCUE;
   constexpr int NEXT = Proc<PID>::NEXT, NB = RealLayout<PID>::NB;
   const int* qr = rescue ? tb.r_real : tb.q_real;
   const long nr = tb.cnt[rescue ? TC_RR : TC_QR];
@@ -1366,11 +1366,18 @@ __global__ void __launch_bounds__(128, ME_MINB) k_term_items(const double* __res
   const unsigned self = 1u << (threadIdx.x & 31u);
   for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += (long)gridDim.x * blockDim.x) {
     if (t < nr) {
-      const int item = qr[t], slot = item >> 2, b = item & 3;
+      const int item = qr[t];
+      const int slot = rescue ? item >> 2 : item;
       r4<double> k[NEXT];
       load_event<NEXT>(p, n, tb.ev[slot], k);
       const Kin<PID, T> K = prepare<PID, T>(k, kp.cp);
-      tb.v[b * c + slot] = real_block_value<PID, T>(K, b, kp);
+      if constexpr (RESCUE) {
+        const int b = item & 3;
+        tb.v[b * c + slot] = real_block_value<PID, T>(K, b, kp);
+      } else {
+#pragma unroll 1
+        for (int b = 0; b < NB; ++b) tb.v[b * c + slot] = real_block_value<PID, T>(K, b, kp);
+      }
     } else {
       const int ci = rescue ? tb.r_born[t - nr] : (int)(t - nr);
       const int bs = tb.bslot[ci], slot = bs & 0x3fffffff, set = bs >> 30;
@@ -1684,8 +1691,8 @@ cudaError_t launch_terms_one(int phase, bool mixed, const LaunchArgs& a, const T
   int g = resident[f64][dev].load(std::memory_order_relaxed);
   if (g == 0) {
     int per = 0, sms = 0;
-    e = f64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_term_items<PID, double>, 128, 0)
-            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_term_items<PID, float>, 128, 0);
+    e = f64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_term_items<PID, double, true>, 128, 0)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_term_items<PID, float, false>, 128, 0);
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
@@ -1701,12 +1708,12 @@ cudaError_t launch_terms_one(int phase, bool mixed, const LaunchArgs& a, const T
     if (blocks <= 0) return cudaSuccess;
     k_terms<PID><<<(unsigned)blocks, 128, 0, st>>>(a.p, a.n, a.out, a.kp, a.count, tb);
     if (mixed)
-      k_term_items<PID, float><<<gi, 128, 0, st>>>(a.p, a.n, a.kp, 0, tb);
+      k_term_items<PID, float, false><<<gi, 128, 0, st>>>(a.p, a.n, a.kp, tb);
     else
-      k_term_items<PID, double><<<gi, 128, 0, st>>>(a.p, a.n, a.kp, 0, tb);
+      k_term_items<PID, double, false><<<gi, 128, 0, st>>>(a.p, a.n, a.kp, tb);
     k_terms_combine<PID><<<gc, 128, 0, st>>>(a.wgt, a.out, a.kp, tb);
   } else {
-    k_term_items<PID, double><<<gi, 128, 0, st>>>(a.p, a.n, a.kp, 1, tb);
+    k_term_items<PID, double, true><<<gi, 128, 0, st>>>(a.p, a.n, a.kp, tb);
     k_terms_final<PID><<<gc, 128, 0, st>>>(a.wgt, a.out, tb, counts);
   }
   return cudaGetLastError();

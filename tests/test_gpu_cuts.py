@@ -115,9 +115,19 @@ def test_real_subtracted_with_cuts_mixed(me, name, icut, queues):
     zero = uniq & (ref == 0.0)
     assert np.all(got[zero] == 0.0)
     live = uniq & ~zero
-    rel = np.abs(got[live] - ref[live]) / np.abs(ref[live])
-    assert np.quantile(rel, 0.999) <= 1e-5, np.sort(rel)[-8:]
-    assert np.all(np.abs(got[live] - ref[live]) <= 1e-4 * mag[live])
+    # within 1e-5 of the weight, or, where the float64 inputs fix the weight less well
+    # than that (points the sampler put near a collinear limit), within the conditioning
+    # bound of the float64 parity rule against the extended-precision oracle
+    g, r, kl = got[live], ref[live], k[live]
+    off = ~(np.abs(g - r) <= 1e-5 * np.abs(r))
+    idx = np.flatnonzero(off)
+    if idx.size:
+        fx, cond = arb.extended(lambda q: fks.real_subtracted(name, q, cuts=c), kl[idx])
+        with np.errstate(all="ignore"):
+            err = (np.abs(g[idx] - fx) / np.abs(fx)).astype(float)
+        off[idx[err <= np.maximum(1e-5, arb.C_COND * cond * arb.U)]] = False
+    assert np.mean(off) <= 1e-3, (int(off.sum()), live.sum())
+    assert np.all(np.abs(g - r) <= 1e-4 * mag[live])
     assert np.all(_either(got[~uniq], lo[~uniq], hi[~uniq], 1e-4))
     assert abs(got.sum() - got64.sum()) <= 1e-6 * np.abs(got64).sum()
     assert 0 <= h.last_rescued() <= b.n
