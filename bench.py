@@ -481,6 +481,23 @@ def _stage_roofline(ops, calls, stages, n, workload, queued=False):
     return cands[0], (cands[1] if len(cands) > 1 else None)
 
 
+def _link_rate(host, torch):
+    """GB/s of a plain pinned-host -> device copy of `host` (the copy engine's rate over
+    the CPU-GPU link): the ceiling of an end-to-end step whose inputs start on the host."""
+    dev = torch.empty_like(host, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        for _ in range(2):
+            dev.copy_(host, non_blocking=True)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        for _ in range(5):
+            dev.copy_(host, non_blocking=True)
+        b.record(s)
+    torch.cuda.synchronize()
+    return host.numel() * host.element_size() * 5 / (a.elapsed_time(b) * 1e-3) / 1e9
+
+
 def measure(me, mebuild, workload, args, n, rank, world, local, dist, full):
     """One workload: warm-up, K timed steps (CUDA events on the launching stream, clocks
     sampled meanwhile), the plain float64 GPU path on the same batches, the end-to-end
@@ -640,6 +657,7 @@ def measure(me, mebuild, workload, args, n, rank, world, local, dist, full):
     barrier()
     h2d = sum(bb.p.nbytes + bb.wgt.nbytes for _, _, bb in calls)
     d2h = len(calls) * n * 8
+    link = _link_rate(hosts[0][1], torch)
     ops = mebuild.op_counts()
     roofline, other = _stage_roofline(ops, calls, stages, n, workload, queued=args.queued_rescue)
     # per call: the main kernel, the float64 work of the two-launch subtracted real (item
@@ -660,6 +678,8 @@ def measure(me, mebuild, workload, args, n, rank, world, local, dist, full):
                               for c, st in zip(calls, stages)],
         "roofline": roofline, "roofline_other_kernel": other,
         "e2e": {"value": n / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "link_gbs": link, "h2d_gbs": h2d / e2e_s / 1e9,
+                "h2d_frac_of_link": h2d / e2e_s / 1e9 / link,
                 "path": "C-ABI call on pinned host buffers: the kernels read the inputs and write the results in "
                         "place over the CPU-GPU link (no staging copy); the call returns with results on the host"},
         "device_generated": devgen, "unweighting": unw,

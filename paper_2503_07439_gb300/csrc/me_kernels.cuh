@@ -1153,14 +1153,16 @@ struct TermBufs {
   double* bx;   // [4][2 cap] set 0 (initial state): eikonal correlator matrix; set 1: cos, sin phi
   int* bslot;   // [2 cap] record slot | set << 30
   int* q_real;  // [cap] records whose real is evaluated (every block in one lane; Born
-                //   configurations are queued as they are stored: 0 .. cnt[TC_QB] - 1)
+                //   configurations are queued as they are stored: set 0 at 0 .. cnt[TC_QB] - 1,
+                //   set 1 at cap .. cap + cnt[TC_QB1] - 1, so that a warp runs one kind)
   int* r_real;  // [4 cap] float64 rescue: real blocks, slot * 4 + b
-  int* r_born;  // [2 cap] float64 rescue: Born configurations
+  int* r_born;  // [2 cap] float64 rescue: Born configurations, set 0 from 0, set 1 from cap
   int* flagged; // [cap] records that failed the stability test
-  int* cnt;     // [8]: records, q_real, q_born, flagged, r_real, r_born
+  int* cnt;     // [8]: records, q_real, set-0 configurations, flagged, r_real, r_born set 0,
+                //   set-1 configurations, r_born set 1
   long cap;
 };
-enum : int { TC_REC = 0, TC_QR = 1, TC_QB = 2, TC_FLAG = 3, TC_RR = 4, TC_RB = 5 };
+enum : int { TC_REC = 0, TC_QR = 1, TC_QB = 2, TC_FLAG = 3, TC_RR = 4, TC_RB = 5, TC_QB1 = 6, TC_RB1 = 7 };
 
 // Reserve `c` consecutive entries of counter `ctr` for each lane of a full warp (every
 // lane calls it; c = 0 reserves nothing): one atomic per warp.  Returns the lane's base.
@@ -1304,7 +1306,8 @@ __global__ void __launch_bounds__(128) k_terms(const double* __restrict__ p, lon
   if (act && !rec) out[i] = 0.0;
   const int slot = warp_reserve(tb.cnt + TC_REC, rec ? 1 : 0);
   const int qr = warp_reserve(tb.cnt + TC_QR, need_real ? 1 : 0);
-  const int qb = warp_reserve(tb.cnt + TC_QB, (need[0] ? 1 : 0) + (need[1] ? 1 : 0));
+  const int qb0 = warp_reserve(tb.cnt + TC_QB, need[0] ? 1 : 0);
+  const int qb1 = warp_reserve(tb.cnt + TC_QB1, need[1] ? 1 : 0);
   if (!rec) return;
   const long c = tb.cap, c2 = 2 * tb.cap;
   tb.ev[slot] = (int)i;
@@ -1324,9 +1327,9 @@ __global__ void __launch_bounds__(128) k_terms(const double* __restrict__ p, lon
 #pragma unroll
   for (int r = 0; r < 6; ++r) tb.m[r * c + slot] = m[r];
   if (need_real) tb.q_real[qr] = slot;
-  int ci = qb;
 #pragma unroll
   for (int set = 0; set < 2; ++set) {
+    const int ci = set == 0 ? qb0 : (int)c + qb1;
     tb.cfg[set * c + slot] = need[set] ? ci : -1;
     if (!need[set]) continue;
     tb.bslot[ci] = slot | (set << 30);
@@ -1346,7 +1349,6 @@ __global__ void __launch_bounds__(128) k_terms(const double* __restrict__ p, lon
         tb.bx[1 * c2 + ci] = bx[1][1];
       }
     }
-    ++ci;
   }
 }
 
@@ -1361,7 +1363,8 @@ __global__ void __launch_bounds__(128, ME_MINB) k_term_items(const double* __res
   constexpr int NEXT = Proc<PID>::NEXT, NB = RealLayout<PID>::NB;
   const int* qr = rescue ? tb.r_real : tb.q_real;
   const long nr = tb.cnt[rescue ? TC_RR : TC_QR];
-  const long nt = nr + tb.cnt[rescue ? TC_RB : TC_QB];
+  const long n0 = tb.cnt[rescue ? TC_RB : TC_QB];
+  const long nt = nr + n0 + tb.cnt[rescue ? TC_RB1 : TC_QB1];
   const long c = tb.cap, c2 = 2 * tb.cap;
   const unsigned self = 1u << (threadIdx.x & 31u);
   for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += (long)gridDim.x * blockDim.x) {
@@ -1379,7 +1382,9 @@ __global__ void __launch_bounds__(128, ME_MINB) k_term_items(const double* __res
         for (int b = 0; b < NB; ++b) tb.v[b * c + slot] = real_block_value<PID, T>(K, b, kp);
       }
     } else {
-      const int ci = rescue ? tb.r_born[t - nr] : (int)(t - nr);
+      // set-0 configurations, then set-1 ones (stored from index cap)
+      const long u = t - nr < n0 ? t - nr : c + (t - nr - n0);
+      const int ci = rescue ? tb.r_born[u] : (int)u;
       const int bs = tb.bslot[ci], slot = bs & 0x3fffffff, set = bs >> 30;
       r4<double> kb[4];
 #pragma unroll
@@ -1477,24 +1482,20 @@ __global__ void __launch_bounds__(128) k_terms_combine(const double* __restrict_
     }
     // queue the flagged records' float64 items (every lane of the warp takes part)
     const int nbl = __popc(msk & ((1u << NB) - 1u));
-    int ncf = 0;
-    if (msk >> NB & 1u) ncf = (tb.cfg[slot] >= 0 ? 1 : 0) + (tb.cfg[c + slot] >= 0 ? 1 : 0);
+    const bool born = msk >> NB & 1u;
+    const int ci0 = born ? tb.cfg[slot] : -1, ci1 = born ? tb.cfg[c + slot] : -1;
     const int fb = warp_reserve(tb.cnt + TC_FLAG, flag ? 1 : 0);
     const int rb = warp_reserve(tb.cnt + TC_RR, nbl);
-    const int cb = warp_reserve(tb.cnt + TC_RB, ncf);
+    const int cb0 = warp_reserve(tb.cnt + TC_RB, ci0 >= 0 ? 1 : 0);
+    const int cb1 = warp_reserve(tb.cnt + TC_RB1, ci1 >= 0 ? 1 : 0);
     if (flag) {
       tb.flagged[fb] = (int)slot;
       int r = rb;
 #pragma unroll
       for (int b = 0; b < NB; ++b)
         if (msk >> b & 1u) tb.r_real[r++] = (int)slot * 4 + b;
-      int q = cb;
-      if (msk >> NB & 1u)
-#pragma unroll
-        for (int set = 0; set < 2; ++set) {
-          const int ci = tb.cfg[set * c + slot];
-          if (ci >= 0) tb.r_born[q++] = ci;
-        }
+      if (ci0 >= 0) tb.r_born[cb0] = ci0;
+      if (ci1 >= 0) tb.r_born[c + cb1] = ci1;
     }
   }
 }
@@ -1511,7 +1512,7 @@ __global__ void k_terms_final(const double* __restrict__ wgt, double* __restrict
   if (blockIdx.x == 0 && threadIdx.x == 0 && counts) {
     counts[0] = tb.cnt[TC_FLAG];
     counts[2] = tb.cnt[TC_RR];
-    counts[3] = tb.cnt[TC_RB];
+    counts[3] = tb.cnt[TC_RB] + tb.cnt[TC_RB1];
   }
   for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < nf; t += (long)gridDim.x * blockDim.x) {
     const long slot = tb.flagged[t];
