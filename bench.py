@@ -554,19 +554,45 @@ def measure(me, mebuild, workload, args, n, rank, world, local, dist, full):
         step(handles)
     e1.record(stream)
     torch.cuda.synchronize()
-    w1 = time.time()
     barrier()
-    clk.mark(w0, w1)
-    clk.__exit__()
-    ms = e0.elapsed_time(e1)
+    ms_direct = e0.elapsed_time(e1)
     stages = []
     for hh, *_ in handles:
         t_main, t_resc, t_red, ncalls = hh.stage_times()
         hh.enable_stage_timers(False)
         stages.append((t_main, t_resc, t_red, ncalls, hh.last_rescued(), hh.last_rescue_work()))
     rescued = sum(st[4] for st in stages)
+    # The same step captured once in a CUDA graph and replayed: the launch mode of the
+    # library's request loop for fixed-shape batches (the C-ABI calls of a step are
+    # stream-ordered launches with no host synchronisation once their first call has run).
+    # This is the headline: the step's kernels without per-launch host cost.
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream, capture_error_mode="relaxed"):
+        step(handles)
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            graph.replay()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    g0 = torch.cuda.Event(enable_timing=True)
+    g1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        g0.record(stream)
+        for _ in range(args.steps):
+            graph.replay()
+        g1.record(stream)
+    torch.cuda.synchronize()
+    w1 = time.time()
+    barrier()
+    clk.mark(w0, w1)
+    clk.__exit__()
+    ms = g0.elapsed_time(g1)
+    ms_direct, _ = reduce_replicas(ms_direct, float(n * args.steps), dist, device="cuda")
     ms, events = reduce_replicas(ms, float(n * args.steps), dist, device="cuda")
     value = events / (ms * 1e-3)
+    direct = {"value": events / (ms_direct * 1e-3), "unit": UNIT, "ms_per_step": ms_direct / args.steps,
+              "launch": "one C-ABI call per entry point per step (stream-ordered, no graph)"}
 
     def time_steps(hs, k):
         step(hs)  # first call: lane-layout tuning, scratch sizing
@@ -596,8 +622,8 @@ def measure(me, mebuild, workload, args, n, rank, world, local, dist, full):
         # |y| <= 1); mixed precision, the same batches
         cut = dict(cut_pt_min=CUT_PT_MIN, cut_abs_y_max=CUT_ABS_Y_MAX)
         terms = {"cuts": {"heavy_quark_pt_min_gev": CUT_PT_MIN, "heavy_quark_abs_y_max": CUT_ABS_Y_MAX}}
-        for label, extra in (("masked", {}), ("queued", {"term_queues": 1}), ("masked_cuts", cut),
-                             ("queued_cuts", dict(cut, term_queues=1))):
+        for label, extra in (("masked", {"term_queues": 0}), ("queued", {"term_queues": 1}),
+                             ("masked_cuts", dict(cut, term_queues=0)), ("queued_cuts", dict(cut, term_queues=1))):
             hs = make(me.ME_PREC_MIXED, **extra)
             t_ms = time_steps(hs, max(3, args.fp64_steps))
             kept = float(sum(torch.count_nonzero(od).item() for *_, od in hs)) / (n * len(hs))
@@ -666,6 +692,7 @@ def measure(me, mebuild, workload, args, n, rank, world, local, dist, full):
                                  not args.queued_rescue else 0) + 2 for (_, entry, _), st in zip(calls, stages))
     return {
         "metric": wl["metric"], "value": value, "unit": UNIT, "ms_per_step": ms / args.steps, "steps": args.steps,
+        "direct_calls": direct,
         "warmup": warmup, "n_points": n, "processes": [c[0] for c in calls], "workload": wl["workload"],
         "l2": wl["l2"],
         "fp64_path": {"value": fp64_value, "unit": UNIT, "ms_per_step": fp64_ms,
@@ -741,7 +768,8 @@ def main():
         configs = {}
         for wk in ("c0", "c1", "c3"):
             m = measure(me, mebuild, wk, args, WORKLOADS[wk]["n"], rank, world, local, dist, full=False)
-            configs[wk] = {k: m[k] for k in ("metric", "value", "unit", "ms_per_step", "n_points", "processes",
+            configs[wk] = {k: m[k] for k in ("metric", "value", "unit", "ms_per_step", "direct_calls", "n_points",
+                                             "processes",
                                              "workload", "l2", "fp64_path", "rescued_per_step",
                                              "rescue_work_per_step", "stage_ms_per_step",
                                              "roofline", "roofline_other_kernel", "e2e", "gpu_launches", "clocks")}
@@ -758,7 +786,9 @@ def main():
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic (seeded Philox + RAMBO phase space)",
         "config": {"workload": head["workload"], "processes": head["processes"], "n_points": n,
                    "precision": "mixed", "l2": head["l2"],
+                   "launch": "each step's C-ABI calls captured once in a CUDA graph, replayed per step",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
+        "direct_calls": head["direct_calls"],
         "fp64_path": head["fp64_path"],
         "other_rescue_path": head["other_rescue_path"],
         "per_term_queues": head["per_term_queues"],

@@ -52,6 +52,9 @@ extern "C" {
 #define ME_PREC_MIXED 1  /* float32 amplitudes; float64 FKS maps, combination and rescue */
 #define ME_RESCUE_POINTS 0 /* mixed precision: every flagged point re-evaluated whole in float64 */
 #define ME_RESCUE_ITEMS 1  /* mixed precision: the flagged points' float64 items (see me_params) */
+#define ME_TERMS_MASKED 0  /* subtracted real: Algorithm 2, every term evaluated, then masked */
+#define ME_TERMS_QUEUED 1  /* subtracted real: per-term queues (see me_params) */
+#define ME_TERMS_AUTO 2    /* queued for mixed-precision batches of at least 2^18 points, else masked */
 
 /*
  * Run parameters.  Start from me_default_params(); `version` must equal
@@ -96,10 +99,11 @@ extern "C" {
  *                    float64.  Points inside xi_thr / y_thr take every ingredient in
  *                    float64.  ME_RESCUE_POINTS re-evaluates every flagged point whole in
  *                    float64.  me_last_rescued counts the flagged points either way.
- *   term_queues      subtracted real (both precisions): 0 (default) = Algorithm 2 of the
+ *   term_queues      subtracted real (both precisions): ME_TERMS_MASKED = Algorithm 2 of the
  *                    paper (Sec. 4.3): every term -- real, soft, collinear -- is evaluated
  *                    for every point, and the terms whose cuts fail are zeroed afterwards;
- *                    1 = per-term queues, the variant discussed after Algorithm 2: a
+ *                    ME_TERMS_QUEUED = per-term queues, the variant discussed after
+ *                    Algorithm 2: a
  *                    float64 pass maps every point, decides the cuts and the counterterm
  *                    regions, and queues only the amplitudes a point needs (the real's
  *                    helicity blocks if the real passes its cuts; the soft Born set and
@@ -108,8 +112,12 @@ extern "C" {
  *                    launch, and the weight is recombined (mixed precision: with the same
  *                    stability test and float64 item rescue).  Tree-level entries
  *                    (me_eval_born, me_eval_nbody_nlo) queue the points that pass the cuts.
- *                    Results agree with term_queues 0 to rounding.  The allocation-free
- *                    entry and the persistent serving kernels always run term_queues 0.
+ *                    Results agree with ME_TERMS_MASKED to rounding.  ME_TERMS_AUTO
+ *                    (default) takes the queues for mixed-precision batches of at least
+ *                    2^18 points (on GB300 they are faster there, and slower on small
+ *                    batches, whose extra launches and float64 pass do not amortise) and
+ *                    the masked evaluation otherwise.  The allocation-free entry and the
+ *                    persistent serving kernels always run the masked evaluation.
  *   cut_pt_min, cut_abs_y_max
  *                    cuts on both heavy quarks (legs 2, 3 of the t tbar processes and of
  *                    their Born counter-events): p_T >= cut_pt_min [GeV] and |rapidity
@@ -152,7 +160,7 @@ typedef struct me_handle me_handle;
 
 /* Fill `p` with the defaults: FP64, alpha = 1/132.507, alpha_s = 0.118, mt = 173,
  * xi_cut = 0.5, delta = 1, xi_thr = 1e-3, y_thr = 1e-3, tol = 1e-5, me_eps = 4e-7,
- * device 0, lanes_per_event 0, queued_rescue 0, rescue ME_RESCUE_ITEMS, term_queues 0,
+ * device 0, lanes_per_event 0, queued_rescue 0, rescue ME_RESCUE_ITEMS, term_queues ME_TERMS_AUTO,
  * no cuts (cut_pt_min 0, cut_abs_y_max +infinity, cut_abs_cos_axis_max 1,
  * cut_thrust_max 1).  Never fails. */
 void me_default_params(me_params* p);

@@ -7,10 +7,10 @@ calling it without a CUDA device, raises.
 """
 from ._capi import (ME_ERR_ARG, ME_ERR_BUSY, ME_ERR_CUDA, ME_ERR_OOM, ME_ERR_PROCESS, ME_ERR_TIMEOUT,
                     ME_OK, ME_PARAMS_VERSION, ME_PREC_FP64, ME_PREC_MIXED, ME_RESCUE_ITEMS, ME_RESCUE_POINTS,
-                    MEError, Handle, Server, declared_symbols,
+                    ME_TERMS_AUTO, ME_TERMS_MASKED, ME_TERMS_QUEUED, MEError, Handle, Server, declared_symbols,
                     default_params, library, load_library)
 
 __all__ = ["Handle", "Server", "MEError", "default_params", "load_library", "library", "declared_symbols",
            "ME_OK", "ME_ERR_ARG", "ME_ERR_OOM", "ME_ERR_PROCESS", "ME_ERR_TIMEOUT", "ME_ERR_CUDA",
            "ME_ERR_BUSY", "ME_PREC_FP64", "ME_PREC_MIXED", "ME_RESCUE_ITEMS", "ME_RESCUE_POINTS",
-           "ME_PARAMS_VERSION"]
+           "ME_PARAMS_VERSION", "ME_TERMS_MASKED", "ME_TERMS_QUEUED", "ME_TERMS_AUTO"]

@@ -19,6 +19,7 @@ ME_PREC_MIXED = 1
 ME_PARAMS_VERSION = 4
 ME_RESCUE_POINTS = 0
 ME_RESCUE_ITEMS = 1
+ME_TERMS_MASKED, ME_TERMS_QUEUED, ME_TERMS_AUTO = 0, 1, 2
 ME_KIND_BORN = 0
 ME_KIND_REAL_SUBTRACTED = 1
 ME_KIND_NBODY_NLO = 2

@@ -569,6 +569,13 @@ static cudaError_t launch_rescue(me_handle* h, const LaunchArgs& a, int lpe64) {
   return dispatch(h->proc->pid, K_REAL, true, lpe64, r, h->stream);
 }
 
+// Whether a subtracted-real call of n points runs the per-term queues.
+constexpr int64_t kTermsAutoMin = (int64_t)1 << 18;
+static bool use_terms(const me_handle* h, int64_t n) {
+  const int t = h->prm.term_queues;
+  return t == ME_TERMS_QUEUED || (t == ME_TERMS_AUTO && h->prm.precision == ME_PREC_MIXED && n >= kTermsAutoMin);
+}
+
 // Per-term queues of the subtracted real (phase 0: float64 pass, bulk items and
 // recombination; phase 1: float64 rescue and recombination of the flagged points).
 static cudaError_t launch_terms(me_handle* h, int phase, bool mixed, const LaunchArgs& a) {
@@ -652,7 +659,8 @@ static int choose_lpe(me_handle* h, int kind, bool fp64, const LaunchArgs& a) {
 static bool cuts_valid(const me_params* p) {
   return std::isfinite(p->cut_pt_min) && p->cut_pt_min >= 0.0 && p->cut_abs_y_max > 0.0 &&
          !std::isnan(p->cut_abs_y_max) && p->cut_abs_cos_axis_max > 0.0 && !std::isnan(p->cut_abs_cos_axis_max) &&
-         p->cut_thrust_max > 0.0 && !std::isnan(p->cut_thrust_max) && (p->term_queues == 0 || p->term_queues == 1);
+         p->cut_thrust_max > 0.0 && !std::isnan(p->cut_thrust_max) && p->term_queues >= ME_TERMS_MASKED &&
+         p->term_queues <= ME_TERMS_AUTO;
 }
 static Cuts cuts_of(int pid, const me_params* p) {
   Cuts c{};
@@ -698,7 +706,7 @@ void me_default_params(me_params* p) {
   p->device = 0;
   p->lanes_per_event = 0;
   p->rescue = ME_RESCUE_ITEMS;
-  p->term_queues = 0;
+  p->term_queues = ME_TERMS_AUTO;
   p->cut_pt_min = 0.0;
   p->cut_abs_y_max = HUGE_VAL;
   p->cut_abs_cos_axis_max = 1.0;
@@ -814,8 +822,8 @@ static int run(me_handle* h, int kind, double nlo_factor, const double* momenta,
   a.resc_list = h->d_resc;
   a.resc_count = h->d_nresc;
   a.tiles = h->d_nresc + 1;
-  const bool terms = kind == K_REAL && h->prm.term_queues;
-  const bool cut_list = kind == K_TREE && h->prm.term_queues && a.kp.cut.mask;
+  const bool terms = kind == K_REAL && use_terms(h, n);
+  const bool cut_list = kind == K_TREE && h->prm.term_queues == ME_TERMS_QUEUED && a.kp.cut.mask;
   const bool queued = kind == K_REAL && mixed && h->prm.queued_rescue && !terms;
   // the queues encode slot * 4 + block in 32 bits
   if (terms && n >= (int64_t)1 << 29) return fail(ME_ERR_ARG, "term_queues: at most 2^29 - 1 points per call");
@@ -833,9 +841,10 @@ static int run(me_handle* h, int kind, double nlo_factor, const double* momenta,
   // the first call per (kind, precision) times the lane layouts (synchronising);
   // both are chosen before the launches whose results are kept.  The queued kernel
   // runs one lane per point in both precisions; the per-term queues one lane per item.
-  if (queued || terms) h->lpe[kind][0] = h->lpe[kind][1] = 1;
+  if (queued) h->lpe[kind][0] = h->lpe[kind][1] = 1;
   const int lpe64 = (kind == K_REAL && mixed && !queued && !terms) ? choose_lpe(h, kind, true, a) : 0;
-  const int lpe = (queued || terms) ? 1 : choose_lpe(h, kind, !mixed, a);
+  const int lpe = queued ? 1 : (terms ? std::max(1, h->lpe[kind][mixed ? 0 : 1]) : choose_lpe(h, kind, !mixed, a));
+  if (terms) h->lpe[kind][0] = h->lpe[kind][1] = lpe;  // a counted launch needs a layout on record
   std::array<cudaEvent_t, 4> ev{};
   const bool timed = h->timers && h->ev_used.size() < 4096;
   if (timed) {
@@ -1025,7 +1034,7 @@ int me_internal_prepare_counted(me_handle* h, int me_kind, int64_t cap) {
     return fail(ME_ERR_ARG, "counted launch: run one ordinary call of this kind first");
   ME_CUDA(cudaSetDevice(h->device));
   int rc = ensure_capacity(h, (size_t)cap);
-  if (rc == ME_OK && kind == K_REAL && h->prm.term_queues) {
+  if (rc == ME_OK && kind == K_REAL && use_terms(h, cap)) {
     if (cap >= (int64_t)1 << 29) return fail(ME_ERR_ARG, "term_queues: at most 2^29 - 1 points per call");
     return ensure_term_capacity(h, (size_t)cap);
   }
@@ -1054,8 +1063,8 @@ int me_internal_launch_counted(me_handle* h, int me_kind, const double* d_p, con
   a.resc_list = h->d_resc;
   a.resc_count = h->d_nresc;
   a.tiles = h->d_nresc + 1;
-  const bool terms = kind == K_REAL && h->prm.term_queues;
-  const bool cut_list = kind == K_TREE && h->prm.term_queues && a.kp.cut.mask;
+  const bool terms = kind == K_REAL && use_terms(h, cap);
+  const bool cut_list = kind == K_TREE && h->prm.term_queues == ME_TERMS_QUEUED && a.kp.cut.mask;
   const bool queued = kind == K_REAL && mixed && h->prm.queued_rescue && !terms;
   h->last_kind = K_TREE;
   if (terms && (size_t)cap > h->tcap) return fail(ME_ERR_ARG, "counted launch: handle not prepared");

@@ -87,4 +87,4 @@ def test_binding_structs_match_the_header(tmp_path):
         assert got[(cname, "sizeof")] == ctypes.sizeof(cls), cname
         for fname, _ in cls._fields_:
             assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
-    assert me.default_params().cut_abs_y_max == float("inf") and me.default_params().term_queues == 0
+    assert me.default_params().cut_abs_y_max == float("inf") and me.default_params().term_queues == me.ME_TERMS_AUTO

@@ -216,7 +216,7 @@ def test_edge_cases_with_queues(me):
         me.Handle("gg_ttg", cut_pt_min=-1.0)
     assert e.value.code == me.ME_ERR_ARG
     with pytest.raises(me.MEError) as e:
-        me.Handle("gg_ttg", term_queues=2)
+        me.Handle("gg_ttg", term_queues=3)
     assert e.value.code == me.ME_ERR_ARG
 
 
