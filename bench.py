@@ -437,10 +437,34 @@ def _stage_roofline(ops, calls, stages, n, workload, queued=False):
     note64 = ("fp64 peak 152 SMs x 2 DFMA/clk x 2 flops x 2070 MHz (nominal units at max clock; "
               "MEASURED_PEAKS.json has no fp64 figure)")
     cands = []
-    for (proc, entry, _), (t_main, t_resc, _t_red, ncalls, resc_pts, work) in zip(calls, stages):
+    for (proc, entry, _), (t_main, t_resc, _t_red, ncalls, resc_pts, work, cfg) in zip(calls, stages):
         per = max(1, ncalls)
         flops = ops["real_subtracted_per_event" if entry == "real_subtracted" else "born_per_event"][proc]
         kname = WORKLOADS[workload]["kernels"][proc]
+        if entry == "real_subtracted" and (cfg[0] or cfg[1]) and t_resc > 0:
+            # per-term queues (the default for large mixed-precision batches): the float64
+            # rescue queues hold real blocks and Born configurations of two kinds
+            real = ops["born_per_event"][proc]
+            per_block = real / NB_REAL[proc]
+            c_soft, c_coll = ops["term_config_per_event"][proc]
+            item_flops = work[1] * per_block + cfg[0] * c_soft + cfg[1] * c_coll
+            cands.append({"bound": "alu", "achieved": item_flops / (t_resc / per * 1e-3) / 1e12, "peak": peak64,
+                          "unit": "TFLOP/s", "traffic": traffic_per_launch(workload, "term_items", resc_pts),
+                          "kernel": f"k_term_items<{proc}, double> + k_terms_final (float64 rescue queues of "
+                                    "the per-term path: real-emission helicity blocks and counterterm Born "
+                                    "configurations of the flagged points)",
+                          "peak_note": note64, "flops_per_block": per_block,
+                          "flops_per_config": [c_soft, c_coll], "points": resc_pts, "real_blocks": work[1],
+                          "born_configs": list(cfg), "ms_per_launch": t_resc / per})
+            cands.append({"bound": "alu", "achieved": flops * n / (t_main / per * 1e-3) / 1e12 if t_main else 0.0,
+                          "peak": peak32, "unit": "TFLOP/s", "traffic": None,
+                          "kernel": f"k_terms<{proc}> + k_term_items<{proc}, float> + k_terms_combine (float64 "
+                                    "maps and queues, bulk amplitudes, recombination)",
+                          "peak_note": note32, "flops_per_event": flops, "points_per_launch": n,
+                          "ms_per_launch": t_main / per,
+                          "note": "flops counted as for the masked evaluation (every Born set); the queues "
+                                  "evaluate only the active ones"})
+            continue
         if entry == "real_subtracted" and (work[1] or work[2]) and t_resc > 0:
             # item rescue: the float64 work is the real's helicity blocks and the counterterm
             # Born sets actually re-evaluated (op counts: real = born_per_event[proc] over
@@ -560,7 +584,8 @@ def measure(me, mebuild, workload, args, n, rank, world, local, dist, full):
     for hh, *_ in handles:
         t_main, t_resc, t_red, ncalls = hh.stage_times()
         hh.enable_stage_timers(False)
-        stages.append((t_main, t_resc, t_red, ncalls, hh.last_rescued(), hh.last_rescue_work()))
+        stages.append((t_main, t_resc, t_red, ncalls, hh.last_rescued(), hh.last_rescue_work(),
+                       hh.last_rescue_configs()))
     rescued = sum(st[4] for st in stages)
     # The same step captured once in a CUDA graph and replayed: the launch mode of the
     # library's request loop for fixed-shape batches (the C-ABI calls of a step are
@@ -699,7 +724,9 @@ def measure(me, mebuild, workload, args, n, rank, world, local, dist, full):
                       "mixed_over_fp64": value / world / fp64_value},
         "other_rescue_path": alt, "per_term_queues": terms, "rescued_per_step": rescued,
         "rescue_work_per_step": [{"process": c[0], "points": st[5][0], "real_blocks": st[5][1],
-                                  "born_sets": st[5][2]} for c, st in zip(calls, stages)],
+                                  "born_sets": st[5][2], "born_configs_soft_coll": list(st[6]),
+                                  "path": "per-term queues" if st[6][0] or st[6][1] else "masked"}
+                                 for c, st in zip(calls, stages)],
         "stage_ms_per_step": [{"process": c[0], "main_kernel": st[0] / max(1, st[3]),
                                "rescue_kernel": st[1] / max(1, st[3]), "reduction": st[2] / max(1, st[3])}
                               for c, st in zip(calls, stages)],

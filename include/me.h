@@ -54,7 +54,7 @@ extern "C" {
 #define ME_RESCUE_ITEMS 1  /* mixed precision: the flagged points' float64 items (see me_params) */
 #define ME_TERMS_MASKED 0  /* subtracted real: Algorithm 2, every term evaluated, then masked */
 #define ME_TERMS_QUEUED 1  /* subtracted real: per-term queues (see me_params) */
-#define ME_TERMS_AUTO 2    /* queued for mixed-precision batches of at least 2^18 points, else masked */
+#define ME_TERMS_AUTO 2    /* queued for mixed-precision batches of at least 2^19 points, else masked */
 
 /*
  * Run parameters.  Start from me_default_params(); `version` must equal
@@ -114,7 +114,7 @@ extern "C" {
  *                    (me_eval_born, me_eval_nbody_nlo) queue the points that pass the cuts.
  *                    Results agree with ME_TERMS_MASKED to rounding.  ME_TERMS_AUTO
  *                    (default) takes the queues for mixed-precision batches of at least
- *                    2^18 points (on GB300 they are faster there, and slower on small
+ *                    2^19 points (on GB300 they are faster there, and slower on small
  *                    batches, whose extra launches and float64 pass do not amortise) and
  *                    the masked evaluation otherwise.  The allocation-free entry and the
  *                    persistent serving kernels always run the masked evaluation.
@@ -220,9 +220,17 @@ int me_last_rescued(me_handle* h, int64_t* n_rescued);
 /* Float64 work of the last me_eval_real_subtracted call in mixed precision with the item
  * rescue: the flagged points, the real-emission helicity blocks and the sets of
  * counterterm Born values re-evaluated in float64 (with ME_RESCUE_POINTS or the queued
- * kernel only the points are counted; the other two are 0).  Synchronises the handle's
- * stream. */
+ * kernel only the points are counted; the other two are 0).  With the per-term queues
+ * (me_params.term_queues) born_sets counts Born configurations, soft and collinear
+ * separately.  Synchronises the handle's stream. */
 int me_last_rescue_work(me_handle* h, int64_t* points, int64_t* real_blocks, int64_t* born_sets);
+
+/* The float64 Born configurations of the last mixed-precision me_eval_real_subtracted
+ * call that ran the per-term queues (Sec. 4.3), by kind: set0 = soft counter-events
+ * (initial state) or sector-1 Borns (final state), set1 = collinear counter-events or
+ * sector-2 Borns.  Both 0 after a call that ran the masked evaluation.  Synchronises
+ * the handle's stream. */
+int me_last_rescue_configs(me_handle* h, int64_t* set0, int64_t* set1);
 
 /* Monte-Carlo accumulators of all outputs since creation or the last set:
  * out[0] = sum w, out[1] = sum w^2, out[2] = number of points (as double).

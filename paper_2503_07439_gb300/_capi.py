@@ -87,6 +87,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "me_eval_real_subtracted": (ctypes.c_int, [vp, vp, vp, i64, vp]),
         "me_last_rescued": (ctypes.c_int, [vp, ctypes.POINTER(i64)]),
         "me_last_rescue_work": (ctypes.c_int, [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]),
+        "me_last_rescue_configs": (ctypes.c_int, [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
         "me_get_accumulators": (ctypes.c_int, [vp, dp]),
         "me_set_accumulators": (ctypes.c_int, [vp, dp]),
         "me_set_stream": (ctypes.c_int, [vp, vp]),
@@ -253,6 +254,13 @@ class Handle:
         last subtracted-real call (item rescue)."""
         v = [ctypes.c_int64() for _ in range(3)]
         _check(self.lib.me_last_rescue_work(self.h, *(ctypes.byref(x) for x in v)))
+        return tuple(x.value for x in v)
+
+    def last_rescue_configs(self) -> tuple[int, int]:
+        """Float64 Born configurations of the last subtracted-real call that ran the
+        per-term queues: (soft or sector-1, collinear or sector-2)."""
+        v = [ctypes.c_int64() for _ in range(2)]
+        _check(self.lib.me_last_rescue_configs(self.h, *(ctypes.byref(x) for x in v)))
         return tuple(x.value for x in v)
 
     def accumulators(self):

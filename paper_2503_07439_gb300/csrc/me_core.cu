@@ -570,7 +570,7 @@ static cudaError_t launch_rescue(me_handle* h, const LaunchArgs& a, int lpe64) {
 }
 
 // Whether a subtracted-real call of n points runs the per-term queues.
-constexpr int64_t kTermsAutoMin = (int64_t)1 << 18;
+constexpr int64_t kTermsAutoMin = (int64_t)1 << 19;
 static bool use_terms(const me_handle* h, int64_t n) {
   const int t = h->prm.term_queues;
   return t == ME_TERMS_QUEUED || (t == ME_TERMS_AUTO && h->prm.precision == ME_PREC_MIXED && n >= kTermsAutoMin);
@@ -835,7 +835,7 @@ static int run(me_handle* h, int kind, double nlo_factor, const double* momenta,
       a.kp.item_rescue = 1;
       a.items = h->ib;
     }
-    ME_CUDA(cudaMemsetAsync(h->d_nresc, 0, 4 * sizeof(int), h->stream));
+    ME_CUDA(cudaMemsetAsync(h->d_nresc, 0, 6 * sizeof(int), h->stream));
     h->last_kind = K_REAL;
   }
   // the first call per (kind, precision) times the lane layouts (synchronising);
@@ -932,6 +932,19 @@ int me_last_rescue_work(me_handle* h, int64_t* points, int64_t* real_blocks, int
   *points = c[0];
   *real_blocks = c[2];
   *born_sets = c[3];
+  return ME_OK;
+}
+
+int me_last_rescue_configs(me_handle* h, int64_t* set0, int64_t* set1) {
+  if (!h || !set0 || !set1) return fail(ME_ERR_ARG, "NULL argument");
+  ME_CUDA(cudaSetDevice(h->device));
+  int c[6] = {0, 0, 0, 0, 0, 0};
+  if (h->prm.precision == ME_PREC_MIXED && h->last_kind == K_REAL) {
+    ME_CUDA(cudaMemcpyAsync(c, h->d_nresc, sizeof(c), cudaMemcpyDeviceToHost, h->stream));
+    ME_CUDA(cudaStreamSynchronize(h->stream));
+  }
+  *set0 = c[4];
+  *set1 = c[5];
   return ME_OK;
 }
 
@@ -1075,7 +1088,7 @@ int me_internal_launch_counted(me_handle* h, int me_kind, const double* d_p, con
       a.kp.item_rescue = 1;
       a.items = h->ib;
     }
-    ME_CUDA(cudaMemsetAsync(h->d_nresc, 0, 4 * sizeof(int), h->stream));
+    ME_CUDA(cudaMemsetAsync(h->d_nresc, 0, 6 * sizeof(int), h->stream));
     h->last_kind = K_REAL;
   }
   if (terms) {

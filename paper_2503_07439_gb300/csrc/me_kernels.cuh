@@ -1502,7 +1502,8 @@ __global__ void __launch_bounds__(128) k_terms_combine(const double* __restrict_
 
 // W of the flagged records after their float64 items; thread 0 of block 0 copies the
 // rescue counts to `counts` ([0] flagged points, [2] real blocks, [3] Born configurations,
-// the layout me_last_rescue_work reads).
+// [4] / [5] those of set 0 / set 1: the layout me_last_rescue_work and
+// me_last_rescue_configs read).
 template <int PID>
 __global__ void k_terms_final(const double* __restrict__ wgt, double* __restrict__ out, TermBufs tb,
                               int* __restrict__ counts) {
@@ -1513,6 +1514,8 @@ __global__ void k_terms_final(const double* __restrict__ wgt, double* __restrict
     counts[0] = tb.cnt[TC_FLAG];
     counts[2] = tb.cnt[TC_RR];
     counts[3] = tb.cnt[TC_RB] + tb.cnt[TC_RB1];
+    counts[4] = tb.cnt[TC_RB];
+    counts[5] = tb.cnt[TC_RB1];
   }
   for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < nf; t += (long)gridDim.x * blockDim.x) {
     const long slot = tb.flagged[t];
