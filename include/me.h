@@ -95,7 +95,7 @@ extern "C" {
  *                    the real's helicity blocks and the counterterms' Born values -- with
  *                    float64 coefficients from the FKS maps; a flagged point takes its
  *                    ingredients in float64, largest error scale first, until the
- *                    float32 error left is within tol |W| / 4, and W is recombined in
+ *                    float32 error left is within tol |W| / 2, and W is recombined in
  *                    float64.  Points inside xi_thr / y_thr take every ingredient in
  *                    float64.  ME_RESCUE_POINTS re-evaluates every flagged point whole in
  *                    float64.  me_last_rescued counts the flagged points either way.

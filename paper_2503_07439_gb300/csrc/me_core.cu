@@ -84,10 +84,16 @@ __global__ void k_finish(const double* __restrict__ part, int nblk, double* __re
 }
 constexpr int RED_BLOCKS = 304;  // 2 x 152 SMs
 // Item rescue: a flagged point re-evaluates items in float64, largest error scale first,
-// until the float32 error left is at most this fraction of tol |W| -- a quarter of the
-// budget of an unflagged point, so that flagged points add little to the tail that the
-// calibration of me_eps bounds.
-constexpr double kItemBudget = 0.25;
+// until the float32 error left is at most this fraction of tol |W| -- half the budget of
+// an unflagged point, so that flagged points add little to the tail that the calibration
+// of me_eps bounds (2^20 flat points: the 99.9th percentile of the error stays at 8.2e-6
+// (g g -> t tbar g), 8.0e-6 (u ubar -> t tbar g) and 7.3e-6 (e+e- -> u ubar g) of tol =
+// 1e-5; at 1 it reaches 1.5e-5).  A compile-time setting, like ME_MINB, for calibration
+// studies: -DME_ITEM_BUDGET=x.
+#ifndef ME_ITEM_BUDGET
+#define ME_ITEM_BUDGET 0.5
+#endif
+constexpr double kItemBudget = ME_ITEM_BUDGET;
 
 // ---------------------------------------------------------------- colour algebra (host)
 using cd = std::complex<double>;

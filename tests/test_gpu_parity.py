@@ -261,7 +261,7 @@ def test_item_rescue_matches_point_rescue(me, name, seed):
     the reference.  Same lane layout, so the float32 pass and the flagged points are
     identical: the counts agree exactly, the item path does less float64 work, and the
     weights agree to the mixed-precision tolerance (1e-5 of |W|, 99.9 %; the residual
-    float32 error of a flagged point is budgeted at a quarter of that).  A ragged size
+    float32 error of a flagged point is budgeted at half of that).  A ragged size
     spans many blocks and warps."""
     n = 100003
     b = synth.flat_points(name, n, seed)
