@@ -302,11 +302,20 @@ def serving_metrics(me, n_requests: int = 400, loads=(0.5, 0.9, 1.2), seed: int 
     total = sum(r["n"] for r in reqs)
     srv = me.Server(device=device, n_slots=n_slots, precision=me.ME_PREC_MIXED)
     _warm_server(me, srv, n_slots)
-    t0 = time.perf_counter()
-    ts = [srv.submit(r["process"], SERVE_KIND[r["process"]], d.p, d.wgt) for r, d in zip(reqs, data)]
-    for t in ts:
-        srv.poll(t)
-    capacity = total / (time.perf_counter() - t0)
+
+    def burst(server):
+        # every request submitted at once; the fastest of three bursts (host threads of
+        # other processes only ever slow one down)
+        best = 0.0
+        for _ in range(3):
+            t0 = time.perf_counter()
+            ts = [server.submit(r["process"], SERVE_KIND[r["process"]], d.p, d.wgt) for r, d in zip(reqs, data)]
+            for t in ts:
+                server.poll(t)
+            best = max(best, total / (time.perf_counter() - t0))
+        return best
+
+    capacity = burst(srv)
 
     def run_load(load):
         return _run_load(srv, reqs, data, total, capacity, load)
@@ -317,11 +326,7 @@ def serving_metrics(me, n_requests: int = 400, loads=(0.5, 0.9, 1.2), seed: int 
     # persistent family kernels (gg_ttgg on the slots), same arrivals at the same rates
     psrv = me.Server(device=device, n_slots=n_slots, precision=me.ME_PREC_MIXED, persistent=True)
     _warm_server(me, psrv, n_slots)
-    t0 = time.perf_counter()
-    ts = [psrv.submit(r["process"], SERVE_KIND[r["process"]], d.p, d.wgt) for r, d in zip(reqs, data)]
-    for t in ts:
-        psrv.poll(t)
-    pcap = total / (time.perf_counter() - t0)
+    pcap = burst(psrv)
     pruns = [_run_load(psrv, reqs, data, total, capacity, x)[1] for x in loads]
     pstats = psrv.stats()
     psrv.close()
