@@ -92,3 +92,26 @@ def test_persistent_kernel_idle_timeout_and_relaunch(me):
     ref = _alone(me, {"process": "gg_ttg", "p": b.p, "w": b.wgt}, me.ME_PREC_FP64)
     rel = np.abs(r2["out"] - ref) / np.abs(ref)
     assert np.quantile(rel, 0.999) <= 1e-11 and rel.max() <= 1e-8
+
+
+def test_persistent_kernels_apply_the_cuts(me):
+    """The persistent family kernels evaluate the cuts of every term as the masked
+    evaluation does (Algorithm 2): with heavy-quark and thrust-axis cuts on, each request
+    equals the same request evaluated alone with the same cuts, exact zeros included."""
+    cuts = dict(cut_pt_min=100.0, cut_abs_y_max=1.0, cut_abs_cos_axis_max=0.7)
+    reqs = _requests(16, 53)
+    srv = me.Server(n_slots=2, precision=me.ME_PREC_FP64, persistent=True, **cuts)
+    tickets = [srv.submit(r["process"], KIND[r["process"]], r["p"], r["w"]) for r in reqs]
+    res = [srv.poll(t, timeout_us=120_000_000) for t in tickets]
+    srv.close()
+    zeros = 0
+    for r, out in zip(reqs, res):
+        assert out["status"] == me.ME_OK
+        ref = _alone(me, r, me.ME_PREC_FP64, **cuts)
+        z = ref == 0.0
+        zeros += int(z.sum())
+        assert np.all(out["out"][z] == 0.0), r["process"]
+        rel = np.abs(out["out"][~z] - ref[~z]) / np.abs(ref[~z])
+        if rel.size:
+            assert np.quantile(rel, 0.999) <= 1e-11 and rel.max() <= 1e-8, (r["process"], np.sort(rel)[-3:])
+    assert zeros > 0
