@@ -834,6 +834,9 @@ static int run(me_handle* h, int kind, double nlo_factor, const double* momenta,
   // the queues encode slot * 4 + block in 32 bits
   if (terms && n >= (int64_t)1 << 29) return fail(ME_ERR_ARG, "term_queues: at most 2^29 - 1 points per call");
   if (terms && (rc = ensure_term_capacity(h, (size_t)n)) != ME_OK) return rc;
+  // host momenta read in place: the float64 pass copies them to the device for the item
+  // kernels, so that they cross the CPU-GPU link once
+  if (terms && vp && pv.host) a.p_copy = h->d_p;
   if (kind == K_REAL && mixed) {
     a.kp.flag_unstable = 1;
     if (!queued && !terms && use_items(h, n)) {

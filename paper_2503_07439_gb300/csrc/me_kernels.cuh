@@ -1207,10 +1207,13 @@ __device__ __forceinline__ double term_born_scale(const TermBufs& tb, long slot)
 
 // Float64 pass of the per-term queues: one thread per point (the counter-event maps,
 // the cuts of every term, the coefficients, and the queues).  Points with nothing left
-// to evaluate get weight 0 here.
+// to evaluate get weight 0 here.  `pc` (optional, device memory, same layout as p): the
+// momenta are copied there, so that the item kernels read device memory when p is host
+// memory read in place over the CPU-GPU link (p is then read once).
 template <int PID>
 __global__ void __launch_bounds__(128) k_terms(const double* __restrict__ p, long n, double* __restrict__ out,
-                                               KParams kp, const int* __restrict__ count, TermBufs tb) {
+                                               KParams kp, const int* __restrict__ count, TermBufs tb,
+                                               double* __restrict__ pc) {
   constexpr int NEXT = Proc<PID>::NEXT, NB = RealLayout<PID>::NB, NBV = RealLayout<PID>::NBV;
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const long nev = count ? (long)*count : n;
@@ -1218,6 +1221,15 @@ __global__ void __launch_bounds__(128) k_terms(const double* __restrict__ p, lon
   r4<double> k[NEXT];
   if (act) {
     load_event<NEXT>(p, n, i, k);
+    if (pc) {
+#pragma unroll
+      for (int l = 0; l < NEXT; ++l) {
+        pc[(0L * NEXT + l) * n + i] = k[l].e;
+        pc[(1L * NEXT + l) * n + i] = k[l].x;
+        pc[(2L * NEXT + l) * n + i] = k[l].y;
+        pc[(3L * NEXT + l) * n + i] = k[l].z;
+      }
+    }
   } else {
 #pragma unroll
     for (int l = 0; l < NEXT; ++l) k[l] = r4<double>{1.0, 0.0, 0.0, 0.0};
@@ -1569,6 +1581,7 @@ struct LaunchArgs {
   ItemBufs items;    // item rescue records and lists
   long groups;       // number of event groups to launch (n, or the list capacity)
   int* tiles;        // queued kernel: tile counter, zero at launch
+  double* p_copy;    // per-term queues: device copy of p made by k_terms (p in host memory), or null
 };
 enum KernelKind : int { K_TREE = 0, K_REAL = 1 };
 
@@ -1710,14 +1723,15 @@ cudaError_t launch_terms_one(int phase, bool mixed, const LaunchArgs& a, const T
     if ((e = cudaMemsetAsync(tb.cnt, 0, 8 * sizeof(int), st)) != cudaSuccess) return e;
     const long blocks = (a.groups + 127) / 128;
     if (blocks <= 0) return cudaSuccess;
-    k_terms<PID><<<(unsigned)blocks, 128, 0, st>>>(a.p, a.n, a.out, a.kp, a.count, tb);
+    k_terms<PID><<<(unsigned)blocks, 128, 0, st>>>(a.p, a.n, a.out, a.kp, a.count, tb, a.p_copy);
+    const double* pi = a.p_copy ? a.p_copy : a.p;
     if (mixed)
-      k_term_items<PID, float, false><<<gi, 128, 0, st>>>(a.p, a.n, a.kp, tb);
+      k_term_items<PID, float, false><<<gi, 128, 0, st>>>(pi, a.n, a.kp, tb);
     else
-      k_term_items<PID, double, false><<<gi, 128, 0, st>>>(a.p, a.n, a.kp, tb);
+      k_term_items<PID, double, false><<<gi, 128, 0, st>>>(pi, a.n, a.kp, tb);
     k_terms_combine<PID><<<gc, 128, 0, st>>>(a.wgt, a.out, a.kp, tb);
   } else {
-    k_term_items<PID, double, true><<<gi, 128, 0, st>>>(a.p, a.n, a.kp, tb);
+    k_term_items<PID, double, true><<<gi, 128, 0, st>>>(a.p_copy ? a.p_copy : a.p, a.n, a.kp, tb);
     k_terms_final<PID><<<gc, 128, 0, st>>>(a.wgt, a.out, tb, counts);
   }
   return cudaGetLastError();

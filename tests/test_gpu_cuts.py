@@ -234,3 +234,21 @@ def test_served_requests_with_queues(me):
         srv.close()
     assert r["status"] == me.ME_OK
     np.testing.assert_allclose(r["out"], direct, rtol=1e-13, atol=0)
+
+
+def test_rescue_counts_of_the_queues_and_host_inputs(me):
+    """The per-term path reports its float64 Born configurations by kind (their sum is
+    the born_sets count of me_last_rescue_work; the masked path reports none), and host
+    inputs read in place give the same numbers as device inputs."""
+    b = synth.flat_points("gg_ttg", 3001, 78)
+    hq = me.Handle("gg_ttg", precision=me.ME_PREC_MIXED, term_queues=1)
+    got_dev = hq.real_subtracted(_dev(b.p)).cpu().numpy()
+    pts, blocks, configs = hq.last_rescue_work()
+    c0, c1 = hq.last_rescue_configs()
+    assert pts == hq.last_rescued() > 0 and configs == c0 + c1 > 0 and blocks > 0
+    pinned = torch.from_numpy(b.p).pin_memory()
+    got_host = hq.real_subtracted(pinned.numpy())
+    np.testing.assert_array_equal(got_host, got_dev)
+    hm = me.Handle("gg_ttg", precision=me.ME_PREC_MIXED, term_queues=0)
+    hm.real_subtracted(_dev(b.p))
+    assert hm.last_rescue_configs() == (0, 0)
