@@ -1367,20 +1367,22 @@ __global__ void __launch_bounds__(128) k_terms(const double* __restrict__ p, lon
 // Every queued amplitude, one lane each, in precision T: reals (from the point's momenta;
 // all helicity blocks of a point in one lane, or one block per lane in the rescue queue)
 // and Born configurations (from the stored counter-event momenta), in one index space
-// (reals first).  RESCUE selects the float64 rescue queues.
-template <int PID, typename T, bool RESCUE>
+// (reals first).  RESCUE selects the float64 rescue queues.  PART: 0 every queue, 1 the
+// reals only, 2 the Born configurations only (the bulk launches the two kinds apart, so
+// that each kernel's code is smaller and its instruction fetch misses less).
+template <int PID, typename T, bool RESCUE, int PART = 0>
 __global__ void __launch_bounds__(128, ME_MINB) k_term_items(const double* __restrict__ p, long n, KParams kp,
                                                              TermBufs tb) {
   constexpr bool rescue = RESCUE;
   constexpr int NEXT = Proc<PID>::NEXT, NB = RealLayout<PID>::NB;
   const int* qr = rescue ? tb.r_real : tb.q_real;
-  const long nr = tb.cnt[rescue ? TC_RR : TC_QR];
-  const long n0 = tb.cnt[rescue ? TC_RB : TC_QB];
-  const long nt = nr + n0 + tb.cnt[rescue ? TC_RB1 : TC_QB1];
+  const long nr = PART == 2 ? 0 : tb.cnt[rescue ? TC_RR : TC_QR];
+  const long n0 = PART == 1 ? 0 : tb.cnt[rescue ? TC_RB : TC_QB];
+  const long nt = nr + n0 + (PART == 1 ? 0 : tb.cnt[rescue ? TC_RB1 : TC_QB1]);
   const long c = tb.cap, c2 = 2 * tb.cap;
   const unsigned self = 1u << (threadIdx.x & 31u);
   for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += (long)gridDim.x * blockDim.x) {
-    if (t < nr) {
+    if (PART != 2 && t < nr) {
       const int item = qr[t];
       const int slot = rescue ? item >> 2 : item;
       r4<double> k[NEXT];
@@ -1393,7 +1395,7 @@ __global__ void __launch_bounds__(128, ME_MINB) k_term_items(const double* __res
 #pragma unroll 1
         for (int b = 0; b < NB; ++b) tb.v[b * c + slot] = real_block_value<PID, T>(K, b, kp);
       }
-    } else {
+    } else if constexpr (PART != 1) {
       // set-0 configurations, then set-1 ones (stored from index cap)
       const long u = t - nr < n0 ? t - nr : c + (t - nr - n0);
       const int ci = rescue ? tb.r_born[u] : (int)u;
@@ -1709,7 +1711,7 @@ cudaError_t launch_terms_one(int phase, bool mixed, const LaunchArgs& a, const T
   if (g == 0) {
     int per = 0, sms = 0;
     e = f64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_term_items<PID, double, true>, 128, 0)
-            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_term_items<PID, float, false>, 128, 0);
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_term_items<PID, float, false, 1>, 128, 0);
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
@@ -1725,10 +1727,12 @@ cudaError_t launch_terms_one(int phase, bool mixed, const LaunchArgs& a, const T
     if (blocks <= 0) return cudaSuccess;
     k_terms<PID><<<(unsigned)blocks, 128, 0, st>>>(a.p, a.n, a.out, a.kp, a.count, tb, a.p_copy);
     const double* pi = a.p_copy ? a.p_copy : a.p;
-    if (mixed)
-      k_term_items<PID, float, false><<<gi, 128, 0, st>>>(pi, a.n, a.kp, tb);
-    else
+    if (mixed) {
+      k_term_items<PID, float, false, 1><<<gi, 128, 0, st>>>(pi, a.n, a.kp, tb);
+      k_term_items<PID, float, false, 2><<<gi, 128, 0, st>>>(pi, a.n, a.kp, tb);
+    } else {
       k_term_items<PID, double, false><<<gi, 128, 0, st>>>(pi, a.n, a.kp, tb);
+    }
     k_terms_combine<PID><<<gc, 128, 0, st>>>(a.wgt, a.out, a.kp, tb);
   } else {
     k_term_items<PID, double, true><<<gi, 128, 0, st>>>(a.p_copy ? a.p_copy : a.p, a.n, a.kp, tb);
