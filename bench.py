@@ -718,8 +718,14 @@ def measure(me, mebuild, workload, args, n, rank, world, local, dist, full):
     roofline, other = _stage_roofline(ops, calls, stages, n, workload, queued=args.queued_rescue)
     # per call: the main kernel, the float64 work of the two-launch subtracted real (item
     # rescue: items + recombination; whole points: one launch) and the two reduction kernels
-    launches_per_step = sum(1 + ((2 if st[5][1] or st[5][2] else 1) if entry == "real_subtracted" and
-                                 not args.queued_rescue else 0) + 2 for (_, entry, _), st in zip(calls, stages))
+    # per-term queues (mixed precision): k_terms, the reals' and the Born configurations'
+    # float32 items, k_terms_combine, the float64 items, k_terms_final
+    def call_launches(entry, st):
+        if entry == "real_subtracted" and (st[6][0] or st[6][1]):
+            return 6 + 2
+        return 1 + ((2 if st[5][1] or st[5][2] else 1) if entry == "real_subtracted" and
+                    not args.queued_rescue else 0) + 2
+    launches_per_step = sum(call_launches(entry, st) for (_, entry, _), st in zip(calls, stages))
     return {
         "metric": wl["metric"], "value": value, "unit": UNIT, "ms_per_step": ms / args.steps, "steps": args.steps,
         "direct_calls": direct,
