@@ -65,11 +65,13 @@ extern "C" {
  *   xi_thr, y_thr    mixed mode: points with xi < xi_thr or 1-y < y_thr in an active
  *                    counterterm region are re-evaluated in float64
  *   tol, me_eps      mixed mode: a point is re-evaluated in float64 when
- *                    E (1 + sqrt(0.01 / rho)) me_eps > tol |W|, W = R S - CT summed
- *                    over sectors, E = sum over sectors of |R S| + |CT_coll| +
- *                    |CT_soft - CT_softcoll| (the soft pair shares its Born values, so
- *                    their errors cancel), rho = min over sectors of 1 - y (float32
- *                    amplitude errors grow towards the collinear limit); me_eps is
+ *                    (E_R (1 + sqrt(0.01 / rho)) + E_B) me_eps > tol |W|, W = R S - CT
+ *                    summed over sectors, E_R = sum over sectors of |R S|, E_B = sum
+ *                    over sectors of |CT_coll| + |CT_soft - CT_softcoll| (the soft pair
+ *                    shares its Born values, so their errors cancel), rho = min over
+ *                    sectors of 1 - y (the float32 errors of the real's amplitudes grow
+ *                    towards the collinear limit; the Born values at their regular 2 ->
+ *                    2 kinematics do not); me_eps is
  *                    calibrated so that, with the flagged points re-evaluated, 99.9 %
  *                    of flat points of each real process stay within 0.7 tol (a 30 %
  *                    margin) and points on soft/collinear approach sequences within tol

@@ -613,6 +613,7 @@ constexpr int MAX_ITEMS = 9;
 struct RealSubOut {
   double W;     // subtracted real, summed over sectors
   double mag;   // error scale: |R S| + |CT_coll| + |CT_soft - CT_softcoll| per sector
+  double magR;  // its real part, sum_j |R S_j|
   double y[2];  // y_j of both sectors (collinear resolution of the test)
   bool near;    // inside xi_thr / y_thr of an active counterterm
 };
@@ -883,18 +884,22 @@ __device__ __forceinline__ RealSubOut real_sub_event(const double* __restrict__ 
     }
     items->born_scale = mag - fabs(R) * a_R;
   }
-  return RealSubOut{W, mag, {ysec[0], ysec[1]}, near};
+  const double magR = mag > 0.0 ? fabs(R) * a_R : 0.0;
+  return RealSubOut{W, mag, magR, {ysec[0], ysec[1]}, near};
 }
 
 // Stability test of a bulk-precision result: the error of W is ~ me_eps x (error
-// scale); the float32 amplitude error per unit scale grows towards the collinear limit,
-// as 1 + sqrt(rho_0 / rho) with rho = min_j (1 - y_j), rho_0 = 0.01.
+// scale); the float32 error of the real's amplitudes per unit scale grows towards the
+// collinear limit, as 1 + sqrt(rho_0 / rho) with rho = min_j (1 - y_j), rho_0 = 0.01.
+// The counterterms' Born values are evaluated at regular 2 -> 2 kinematics, whose error
+// does not grow there: error ~ me_eps x (growth x real part + Born part).
 __device__ __forceinline__ double error_growth(const RealSubOut& r) {
   const float rho = fmaxf((float)fmin(1.0 - r.y[0], 1.0 - r.y[1]), 1e-30f);
   return 1.0 + (double)sqrtf(0.01f / rho);
 }
 __device__ __forceinline__ bool unstable_point(const RealSubOut& r, const KParams& kp) {
-  return r.near || !(r.mag * error_growth(r) * kp.me_eps <= kp.tol * fabs(r.W));
+  const double g = error_growth(r);
+  return r.near || !((r.magR * g + (r.mag - r.magR)) * kp.me_eps <= kp.tol * fabs(r.W));
 }
 
 // Items of a flagged point to re-evaluate in float64: bit b < NB for the real's block
@@ -910,8 +915,9 @@ __device__ __forceinline__ unsigned rescue_mask(const RealSubOut& r, const RealI
   double rest = 0.0;
 #pragma unroll
   for (int b = 0; b < NB; ++b) rest += (e[b] = fabs(it.a[b] * it.v[b]));
-  rest += (e[NB] = fabs(it.born_scale));
-  const double budget = kp.item_budget * kp.tol * fabs(r.W) / (error_growth(r) * kp.me_eps);
+  const double grow = error_growth(r);
+  rest += (e[NB] = fabs(it.born_scale) / grow);  // no growth for the Born part (see above)
+  const double budget = kp.item_budget * kp.tol * fabs(r.W) / (grow * kp.me_eps);
   unsigned m = 0;
 #pragma unroll
   for (int k = 0; k <= NB; ++k) {
@@ -1455,9 +1461,11 @@ __global__ void __launch_bounds__(128) k_terms_combine(const double* __restrict_
         double R = 0.0;
 #pragma unroll
         for (int b = 0; b < NB; ++b) R += tb.v[b * c + slot];
-        const double bsc = term_born_scale<PID>(tb, slot);
-        const double mag = fabs(tb.a[slot] * R) + bsc;
         const double grow = (double)tb.grow[slot];
+        // the growth of the float32 error towards the collinear limit is the real's; the
+        // Born part enters unscaled (unstable_point)
+        const double bsc = term_born_scale<PID>(tb, slot) / grow;
+        const double mag = fabs(tb.a[slot] * R) + bsc;
         const bool near = tb.flags[slot] & 1;
         flag = near || !(mag * grow * kp.me_eps <= kp.tol * fabs(W));
         if (flag) {
