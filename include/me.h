@@ -118,7 +118,9 @@ extern "C" {
  *                    (default) takes the queues for mixed-precision batches of at least
  *                    2^19 points (on GB300 they are faster there, and slower on small
  *                    batches, whose extra launches and float64 pass do not amortise) and
- *                    the masked evaluation otherwise.  The allocation-free entry and the
+ *                    the masked evaluation otherwise; queued_rescue 1 or rescue
+ *                    ME_RESCUE_POINTS, options of the masked evaluation, select it.  With
+ *                    ME_TERMS_QUEUED the queues always run their item rescue.  The allocation-free entry and the
  *                    persistent serving kernels always run the masked evaluation.
  *   cut_pt_min, cut_abs_y_max
  *                    cuts on both heavy quarks (legs 2, 3 of the t tbar processes and of

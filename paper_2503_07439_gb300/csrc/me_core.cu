@@ -579,7 +579,10 @@ static cudaError_t launch_rescue(me_handle* h, const LaunchArgs& a, int lpe64) {
 constexpr int64_t kTermsAutoMin = (int64_t)1 << 19;
 static bool use_terms(const me_handle* h, int64_t n) {
   const int t = h->prm.term_queues;
-  return t == ME_TERMS_QUEUED || (t == ME_TERMS_AUTO && h->prm.precision == ME_PREC_MIXED && n >= kTermsAutoMin);
+  // the automatic choice leaves the masked path's own rescue options (whole points, the
+  // per-block queue) to the masked path
+  return t == ME_TERMS_QUEUED || (t == ME_TERMS_AUTO && h->prm.precision == ME_PREC_MIXED && n >= kTermsAutoMin &&
+                                  h->prm.queued_rescue == 0 && h->prm.rescue == ME_RESCUE_ITEMS);
 }
 
 // Per-term queues of the subtracted real (phase 0: float64 pass, bulk items and
