@@ -20,14 +20,18 @@ def me():
     return m
 
 
-@pytest.mark.parametrize("name,entry,prec", [("gg_ttg", "real_subtracted", "mixed"), ("gg_tt", "born", "mixed"),
-                                             ("gg_ttgg", "born", "mixed"), ("uu_ttg", "real_subtracted", "fp64")])
-def test_capture_and_replay(me, name, entry, prec):
+@pytest.mark.parametrize("name,entry,prec,queues", [("gg_ttg", "real_subtracted", "mixed", 0),
+                                                    ("gg_tt", "born", "mixed", 0), ("gg_ttgg", "born", "mixed", 0),
+                                                    ("uu_ttg", "real_subtracted", "fp64", 0),
+                                                    ("gg_ttg", "real_subtracted", "mixed", 1),
+                                                    ("ee_uug", "real_subtracted", "fp64", 1)])
+def test_capture_and_replay(me, name, entry, prec, queues):
+    """queues 1: the per-term path (a counter reset and six kernels) is captured too."""
     b = synth.flat_points(name, 3000, 17)
     p = torch.from_numpy(b.p).cuda()
     w = torch.from_numpy(b.wgt).cuda()
     out = torch.empty(b.n, dtype=torch.float64, device="cuda")
-    h = me.Handle(name, precision=me.ME_PREC_MIXED if prec == "mixed" else me.ME_PREC_FP64)
+    h = me.Handle(name, precision=me.ME_PREC_MIXED if prec == "mixed" else me.ME_PREC_FP64, term_queues=queues)
     s = torch.cuda.Stream()
     h.set_stream(s.cuda_stream)
     f = getattr(h, entry)

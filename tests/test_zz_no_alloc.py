@@ -89,3 +89,25 @@ def test_noalloc_keeps_the_callers_current_device(me):
                                              out.data_ptr(), None)
     assert rc == me.ME_OK, lib.me_last_error()
     assert torch.cuda.current_device() == before
+
+
+def test_noalloc_applies_the_cuts(me):
+    """The cuts of the parameters reach the allocation-free entry too: with heavy-quark
+    cuts its weights equal those of a handle with the same cuts (the masked evaluation),
+    exact zeros included."""
+    lib = me.library()
+    cuts = dict(cut_pt_min=100.0, cut_abs_y_max=1.0)
+    b = synth.flat_points("gg_ttg", 2053, 27)
+    p = torch.from_numpy(b.p).cuda()
+    ref = me.Handle("gg_ttg", precision=me.ME_PREC_FP64, term_queues=0, **cuts).real_subtracted(p).cpu().numpy()
+    params = me.default_params(precision=me.ME_PREC_FP64, **cuts)
+    out = torch.full((b.n,), np.nan, dtype=torch.float64, device="cuda")
+    rc = lib.me_eval_real_subtracted_noalloc(b"gg_ttg", ctypes.byref(params), p.data_ptr(), None, b.n,
+                                             out.data_ptr(), None)
+    assert rc == me.ME_OK, lib.me_last_error()
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    z = ref == 0.0
+    assert 0.05 < z.mean() < 0.95 and np.all(got[z] == 0.0)
+    rel = np.abs(got[~z] - ref[~z]) / np.abs(ref[~z])
+    assert np.quantile(rel, 0.999) <= 1e-11 and rel.max() <= 1e-8
