@@ -93,10 +93,10 @@ int main() {
   std::printf(" \"real_subtracted_per_event\": {\"ee_uug\": %.0f, \"gg_ttg\": %.0f, \"uu_ttg\": %.0f},\n", real_ee,
               real_gg, real_uu);
   // per-term queues: one Born configuration per lane -- soft (Born with the eikonal
-  // form), collinear (Born plus the two spin-correlated blocks for g g), or a final-state
-  // sector's Born
-  const double soft_gg = born_ops<P_GG_TT>(p) + 8 * quad2, coll_gg = born_ops<P_GG_TT>(p) +
-                         block_ops<P_GG_TT>(p, 2, &e, 0) + block_ops<P_GG_TT>(p, 1, &e, 1);
+  // form), collinear (Born plus, for g g, the spin-correlated block of the one sector
+  // whose collinear term is active, delta <= 1), or a final-state sector's Born
+  const double soft_gg = born_ops<P_GG_TT>(p) + 8 * quad2,
+               coll_gg = born_ops<P_GG_TT>(p) + block_ops<P_GG_TT>(p, 2, &e, 0);
   const double soft_uu = born_ops<P_UU_TT>(p) + 8 * quad2, coll_uu = born_ops<P_UU_TT>(p);
   std::printf(" \"term_config_per_event\": {\"ee_uug\": [%.0f, %.0f], \"gg_ttg\": [%.0f, %.0f], "
               "\"uu_ttg\": [%.0f, %.0f]},\n", b[0], b[0], soft_gg, coll_gg, soft_uu, coll_uu);

@@ -671,7 +671,8 @@ __device__ __forceinline__ void isr_soft_pair(const r4<double>* kb, const double
 // direction (0, cos phi, sin phi, 0) of the emission.
 template <int BPID, typename T, int LPE>
 __device__ __forceinline__ void isr_coll_set(const r4<double>* kb, double cphi, double sphi, const KParams& kp,
-                                             int lane, unsigned mask, double* v) {
+                                             int lane, unsigned mask, double* v, bool want0 = true,
+                                             bool want1 = true) {
   c4<T> eperp;
   eperp.v[0] = cx<T>{T(0), T(0)};
   eperp.v[1] = cx<T>{(T)cphi, T(0)};
@@ -684,12 +685,12 @@ __device__ __forceinline__ void isr_coll_set(const r4<double>* kb, double cphi, 
                              [&](int, const cx<T>* J) { aC += colour_sum<BPID, T>(kp.tab, J); });
   if constexpr (BPID == P_GG_TT) {
     // polarised gluon 0; gluon 1 fixed to +, the heavy pair free (the flip covers the rest)
-    if (lane == 0)
+    if (lane == 0 && want0)
       amplitude_block<BPID, T>(
           KB, 2, kp.cp, [&](int, const cx<T>* J) { aP[0] += colour_sum<BPID, T>(kp.tab, J); }, &eperp, 0);
     // polarised gluon 1, gluon 0 fixed to +: sector 2's spin-correlated Born, at the
     // same kinematics (invariant under the boost that relates the two sectors)
-    if (lane == 1 % LPE)
+    if (lane == 1 % LPE && want1)
       amplitude_block<BPID, T>(
           KB, 1, kp.cp, [&](int, const cx<T>* J) { aP[1] += colour_sum<BPID, T>(kp.tab, J); }, &eperp, 1);
   }
@@ -1247,7 +1248,7 @@ __global__ void __launch_bounds__(128) k_terms(const double* __restrict__ p, lon
   bool need[2] = {false, false}, near = false;
   double xi, y0, y1;
   r4<double> kb[2][4];
-  double bx[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+  double bx[2][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
   double E[4] = {0.0, 0.0, 0.0, 0.0};
   if constexpr (PID == P_EE_UUG) {
     FsrKin f;
@@ -1307,13 +1308,22 @@ __global__ void __launch_bounds__(128) k_terms(const double* __restrict__ p, lon
     }
     need[0] = th_s > 0.0;
     if (need[0]) isr_eikonal_matrix<BPID>(f, kp, E);
+    // spin-correlated Borns the collinear configuration needs (g g): sector j's has a
+    // nonzero coefficient only where sector j's collinear term is active, which with
+    // delta <= 1 is one sector at most.  If only sector 2's is needed, the beams are
+    // stored swapped: by Bose symmetry the Born with gluon 1 polarised at (k0, k1, ..)
+    // is the Born with gluon 0 polarised at (k1, k0, ..), and the plain Born is
+    // symmetric, so every lane then evaluates gluon 0 polarised (one code path).
+    const bool p0 = BPID == P_GG_TT && ab[3 % NBV] != 0.0, p1 = BPID == P_GG_TT && ab[4 % NBV] != 0.0;
+    const bool swap = p1 && !p0;
 #pragma unroll
     for (int l = 0; l < 4; ++l) {
       kb[0][l] = f.soft[l];
-      kb[1][l] = f.coll[l];
+      kb[1][l] = f.coll[swap && l < 2 ? 1 - l : l];
     }
     bx[1][0] = f.cphi;
     bx[1][1] = f.sphi;
+    bx[1][2] = (double)((p0 ? 1 : 0) | (p1 ? 2 : 0) | (swap ? 4 : 0));
   }
   // the boundary of the FKS domain has measure zero and weight 0 (see real_sub_event)
   const bool inside = act && xi > 0.0 && xi < 1.0 && 1.0 - y0 > 0.0 && 1.0 - y1 > 0.0;
@@ -1365,6 +1375,7 @@ __global__ void __launch_bounds__(128) k_terms(const double* __restrict__ p, lon
       } else {
         tb.bx[0 * c2 + ci] = bx[1][0];
         tb.bx[1 * c2 + ci] = bx[1][1];
+        tb.bx[2 * c2 + ci] = bx[1][2];
       }
     }
   }
@@ -1423,11 +1434,16 @@ __global__ void __launch_bounds__(128, ME_MINB) k_term_items(const double* __res
           tb.v[(NB + 1) * c + slot] = vS;
         } else {
           double vc[3];
-          isr_coll_set<BPID, T, 1>(kb, tb.bx[0 * c2 + ci], tb.bx[1 * c2 + ci], kp, 0, self, vc);
+          // only the spin-correlated Borns with a nonzero coefficient (flags from k_terms:
+          // 1 sector 1's, 2 sector 2's, 4 beams swapped so that sector 2's is gluon 0's)
+          const int fl = (int)tb.bx[2 * c2 + ci];
+          const bool sw = fl & 4;
+          isr_coll_set<BPID, T, 1>(kb, tb.bx[0 * c2 + ci], tb.bx[1 * c2 + ci], kp, 0, self, vc,
+                                   (fl & 1) || sw, (fl & 2) && !sw);
           tb.v[(NB + 2) * c + slot] = vc[0];
           if constexpr (BPID == P_GG_TT) {
-            tb.v[(NB + 3) * c + slot] = vc[1];
-            tb.v[(NB + 4) * c + slot] = vc[2];
+            if (fl & 1) tb.v[(NB + 3) * c + slot] = vc[1];
+            if (fl & 2) tb.v[(NB + 4) * c + slot] = sw ? vc[1] : vc[2];
           }
         }
       }
