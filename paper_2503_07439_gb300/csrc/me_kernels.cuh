@@ -712,7 +712,20 @@ __device__ __forceinline__ void isr_born_values(const IsrKin& f, const KParams& 
   double E[4];
   isr_eikonal_matrix<BPID>(f, kp, E);
   isr_soft_pair<BPID, T, LPE>(f.soft, E, kp, lane, mask, v[0], v[1]);
-  isr_coll_set<BPID, T, LPE>(f.coll, f.cphi, f.sphi, kp, lane, mask, v + 2);
+  // sector j's spin-correlated Born enters only where its collinear term is active (one
+  // sector at most for delta <= 1); where that is sector 2 alone, the beams are swapped
+  // (Bose symmetry of g g -> t tbar) so that every lane evaluates the gluon-0 block
+  const bool w0 = BPID == P_GG_TT && f.y[0] > 1.0 - kp.delta && f.cut_c[0];
+  const bool w1 = BPID == P_GG_TT && f.y[1] > 1.0 - kp.delta && f.cut_c[1];
+  const bool sw = w1 && !w0;
+  const r4<double> cb[4] = {sw ? f.coll[1] : f.coll[0], sw ? f.coll[0] : f.coll[1], f.coll[2], f.coll[3]};
+  isr_coll_set<BPID, T, LPE>(cb, f.cphi, f.sphi, kp, lane, mask, v + 2, w0 || sw, w1 && !sw);
+  if constexpr (BPID == P_GG_TT) {
+    if (sw) {
+      v[4] = v[3];
+      v[3] = 0.0;
+    }
+  }
 }
 
 // The Born |M|^2 of e+e- -> u ubar at kb (a final-state counterterm's Born).
@@ -1317,10 +1330,11 @@ __global__ void __launch_bounds__(128) k_terms(const double* __restrict__ p, lon
     const bool p0 = BPID == P_GG_TT && ab[3 % NBV] != 0.0, p1 = BPID == P_GG_TT && ab[4 % NBV] != 0.0;
     const bool swap = p1 && !p0;
 #pragma unroll
-    for (int l = 0; l < 4; ++l) {
-      kb[0][l] = f.soft[l];
-      kb[1][l] = f.coll[swap && l < 2 ? 1 - l : l];
-    }
+    for (int l = 0; l < 4; ++l) kb[0][l] = f.soft[l];
+    kb[1][0] = swap ? f.coll[1] : f.coll[0];
+    kb[1][1] = swap ? f.coll[0] : f.coll[1];
+    kb[1][2] = f.coll[2];
+    kb[1][3] = f.coll[3];
     bx[1][0] = f.cphi;
     bx[1][1] = f.sphi;
     bx[1][2] = (double)((p0 ? 1 : 0) | (p1 ? 2 : 0) | (swap ? 4 : 0));
