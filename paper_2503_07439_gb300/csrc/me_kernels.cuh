@@ -462,6 +462,14 @@ __device__ __forceinline__ r4<double> boost_by(const r4<double>& p, const r4<dou
   const double c = sgn * (e + p.e) / (Q.e + m);
   return r4<double>{e, p.x + c * Q.x, p.y + c * Q.y, p.z + c * Q.z};
 }
+// the same with 1 / (Q0 + M) given (several vectors boosted by one system)
+__device__ __forceinline__ r4<double> boost_by_r(const r4<double>& p, const r4<double>& Q, double inv_m,
+                                                 double inv_qm, double sgn) {
+  const double qp = Q.x * p.x + Q.y * p.y + Q.z * p.z;
+  const double e = (p.e * Q.e + sgn * qp) * inv_m;
+  const double c = sgn * (e + p.e) * inv_qm;
+  return r4<double>{e, p.x + c * Q.x, p.y + c * Q.y, p.z + c * Q.z};
+}
 
 __device__ __forceinline__ void unit3(const r4<double>& p, double& x, double& y, double& z) {
   const double a = rsqrt(p.x * p.x + p.y * p.y + p.z * p.z);
@@ -476,7 +484,7 @@ constexpr double CA_ = 3.0;
 
 // Initial-state FKS sectors (i = gluon leg 4, j = beam 0 or 1) of 2 -> Q Qbar g.
 struct IsrKin {
-  double xi, y[2], S[2], K, K0;
+  double xi, iz, y[2], S[2], K, K0;  // iz = 1 / (1 - xi)
   r4<double> soft[4];     // soft Born: beams, heavy pair at sqrt(s) along n*
   // collinear Born of sector 1: beam 1 scaled by z = 1 - xi.  That of sector 2 (beam 2
   // scaled) is the same 2 -> 2 configuration boosted along the beam axis, and everything
@@ -492,8 +500,8 @@ struct IsrKin {
 };
 
 __device__ __forceinline__ void isr_map(const r4<double>* k, double mass, IsrKin& o, const Cuts& cut) {
-  const double rs = k[0].e + k[1].e, s = rs * rs, is = 1.0 / s;
-  o.xi = 2.0 * k[4].e / rs;
+  const double rs = k[0].e + k[1].e, irs = 1.0 / rs, s = rs * rs, is = irs * irs;
+  o.xi = 2.0 * k[4].e * irs;
   unit3(k[4], o.qdir[0], o.qdir[1], o.qdir[2]);
   double b0[3], b1[3];
   unit3(k[0], b0[0], b0[1], b0[2]);
@@ -515,24 +523,25 @@ __device__ __forceinline__ void isr_map(const r4<double>* k, double mass, IsrKin
   double n[3];
   unit3(ks, n[0], n[1], n[2]);
   const double m4 = 4.0 * mass * mass;
-  const double beta = sqrt(1.0 - m4 * is);
+  const double b2 = 1.0 - m4 * is, ibeta = rsqrt(b2), beta = b2 * ibeta;
   o.soft[0] = k[0];
   o.soft[1] = k[1];
   const double e = 0.5 * rs, pa = 0.5 * rs * beta;
   o.soft[2] = r4<double>{e, pa * n[0], pa * n[1], pa * n[2]};
   o.soft[3] = r4<double>{e, -pa * n[0], -pa * n[1], -pa * n[2]};
   const double z = 1.0 - o.xi;
+  o.iz = 1.0 / z;
   const double sz = s * z, iM = rsqrt(sz), M = sz * iM;
-  const double bQ = sqrt(fmax(0.0, 1.0 - m4 * is / z));
+  const double bQ = sqrt(fmax(0.0, 1.0 - m4 * is * o.iz));
   const double eQ = 0.5 * M, pQ = 0.5 * M * bQ;
   const r4<double> tr{eQ, pQ * n[0], pQ * n[1], pQ * n[2]};
   const r4<double> tbr{eQ, -pQ * n[0], -pQ * n[1], -pQ * n[2]};
   o.coll[0] = scale(z, k[0]);
   o.coll[1] = k[1];
   const r4<double> Qc = o.coll[0] + o.coll[1];
-  const double Mc2 = mdot(Qc, Qc), iMc = rsqrt(Mc2);
-  o.coll[2] = boost_by(tr, Qc, iMc, Mc2 * iMc, 1.0);
-  o.coll[3] = boost_by(tbr, Qc, iMc, Mc2 * iMc, 1.0);
+  const double Mc2 = mdot(Qc, Qc), iMc = rsqrt(Mc2), iqm = 1.0 / (Qc.e + Mc2 * iMc);
+  o.coll[2] = boost_by_r(tr, Qc, iMc, iqm, 1.0);
+  o.coll[3] = boost_by_r(tbr, Qc, iMc, iqm, 1.0);
   o.cut_s = o.cut_c[0] = o.cut_c[1] = true;
   if (cut.mask) {
     o.cut_s = heavy_pass(o.soft[2], cut) && heavy_pass(o.soft[3], cut);
@@ -543,7 +552,7 @@ __device__ __forceinline__ void isr_map(const r4<double>* k, double mass, IsrKin
                  heavy_pass(boost_by(tbr, Q1, iM1, M12 * iM1, 1.0), cut);
   }
   constexpr double i64pi3 = 1.0 / (64.0 * PI * PI * PI);
-  o.K = s * bQ * i64pi3 / beta;
+  o.K = s * bQ * i64pi3 * ibeta;
   o.K0 = s * i64pi3;
 }
 
@@ -837,7 +846,7 @@ __device__ __forceinline__ RealSubOut real_sub_event(const double* __restrict__ 
     const double Bs = bv[1], Bc = bv[2];
     const double Bp[2] = {BPID == P_GG_TT ? bv[3 % RealLayout<PID>::NBV] : 0.0,
                           BPID == P_GG_TT ? bv[4 % RealLayout<PID>::NBV] : 0.0};
-    const double xi = f.xi, z = 1.0 - xi, iz = 1.0 / z, is2 = 2.0 / s;
+    const double xi = f.xi, z = 1.0 - xi, iz = f.iz, is2 = 2.0 / s;
     const double th_s = xi < kp.xi_cut && f.cut_s ? 1.0 : 0.0;
     // 1 / (xi^2 (1 - y_j) K) of both sectors from one reciprocal
     const double den0 = xi * xi * (1.0 - f.y[0]) * f.K, den1 = xi * xi * (1.0 - f.y[1]) * f.K;
@@ -1293,7 +1302,7 @@ __global__ void __launch_bounds__(128) k_terms(const double* __restrict__ p, lon
     xi = f.xi;
     y0 = f.y[0];
     y1 = f.y[1];
-    const double z = 1.0 - xi, iz = 1.0 / z, is2 = 2.0 / s;
+    const double z = 1.0 - xi, iz = f.iz, is2 = 2.0 / s;
     const double th_s = xi < kp.xi_cut && f.cut_s ? 1.0 : 0.0;
     const double den0 = xi * xi * (1.0 - f.y[0]) * f.K, den1 = xi * xi * (1.0 - f.y[1]) * f.K;
     const double rden = 1.0 / (den0 * den1);
