@@ -233,26 +233,18 @@ __global__ void __launch_bounds__(128, tree_min_blocks<PID, T>()) k_tree(const d
 //  2. lane w extends the quark line for the six orderings that start with gluon w,
 //     U(w) -> U(wx) -> U(wxy), for both top helicities, and writes the partial
 //     amplitudes of both antitop helicities into shared-memory rows;
-//  3. the colour sum of the warp's 32 rows (8 events x 4 heavy-pair helicities; lane
-//     4e + h holds helicity h of event e) on the tcgen05 tensor cores (me_tc.cuh): the
-//     lanes store their rows' bf16 terms into the CTA's operand tile and one lane issues
-//     the products into the warp's TMEM columns; each lane reads back its row of Z and
-//     forms J^dagger Z during the next block, after its currents (steps 1-4), so that
-//     the tensor core's latency is hidden behind them.
-// Everything a lane needs stays on chip, so the 5e5 flops of an event run from registers,
-// shared memory and TMEM.  In a warp that holds the end of the batch, events past it
-// compute a fixed finite configuration and are discarded, so every warp-wide step stays
-// converged; warps entirely past the end skip the blocks, and CTAs entirely past it
-// return before allocating TMEM.
+//  3. one warp-wide tensor-core colour sum (me_tc.cuh) takes the warp's 32 rows
+//     (8 events x 4 heavy-pair helicities): lane 4e + h receives helicity h of event e.
+// Everything a lane needs stays on chip, so the 5e5 flops of an event run from registers
+// and shared memory.  In a warp that holds the end of the batch, events past it compute
+// a fixed finite configuration and are discarded, so every warp-wide step stays
+// converged; warps entirely past the end return at once.
 constexpr int TC4_EV_FLOATS = 276;  // 34 four-vectors x 8 floats, padded so 8 events hit distinct banks
 constexpr int TC4_ROW = 25;         // floats per amplitude row (24 flows, padded)
 constexpr int TC4_WARP_FLOATS = 8 * TC4_EV_FLOATS + 2 * 32 * TC4_ROW;
-constexpr int TC4_SMEM_PER_WARP = TC4_WARP_FLOATS * 4;
+constexpr int TC4_SMEM_PER_WARP = TC4_WARP_FLOATS * 4 + TC_SMEM_PER_WARP;
 constexpr int TC4_THREADS = 128;
-// the CTA's tcgen05 operands, mbarriers and TMEM address first, then the warps' areas
-constexpr int TC4_SMEM = TC5_SMEM + (TC4_THREADS / 32) * TC4_SMEM_PER_WARP;
-static_assert(TC5_SMEM % 16 == 0 && TC4_SMEM_PER_WARP % 16 == 0, "16-byte aligned areas");
-static_assert(TC4_THREADS == 128, "the tcgen05 colour sum takes one 128-row tile per CTA");
+constexpr int TC4_SMEM = (TC4_THREADS / 32) * TC4_SMEM_PER_WARP;
 
 // J(xyz) representatives, slot t = 3 * (missing gluon) + (position of the middle gluon
 // among the three in increasing order); packed x | y << 4 | z << 8, x < z
@@ -313,21 +305,19 @@ __global__ void __launch_bounds__(TC4_THREADS, 2) k_tree_tc4(const double* __res
                                                              const int* __restrict__ idx, const int* __restrict__ count) {
   static_assert(LPE == 4, "four lanes per event");
   constexpr int PID = P_GG_TTGG;
-  extern __shared__ __align__(1024) unsigned char tc4_raw[];
+  extern __shared__ __align__(16) float tc4_smem[];
   const int warp = threadIdx.x >> 5, wl = threadIdx.x & 31;
-  const long nev = count ? (long)*count : n;
-  if ((long)blockIdx.x * blockDim.x / 4 >= nev) return;  // uniform over the CTA
-  // every thread of the CTA takes part in the TMEM allocation and its release
-  Tc5 tcs = tc5_setup(tc4_raw, kp.tab->C[PID]);
-  float* wsm = reinterpret_cast<float*>(tc4_raw + TC5_SMEM) + warp * (TC4_SMEM_PER_WARP / 4);
+  float* wsm = tc4_smem + warp * (TC4_SMEM_PER_WARP / 4);
   float* cur = wsm + (wl >> 2) * TC4_EV_FLOATS;         // this event's four-vectors
   float* are = wsm + 8 * TC4_EV_FLOATS;                 // amplitude rows, real parts [32][TC4_ROW]
   float* aim = are + 32 * TC4_ROW;                      // imaginary parts
+  unsigned char* stage = reinterpret_cast<unsigned char*>(wsm + TC4_WARP_FLOATS);
   const long gid = ((long)blockIdx.x * blockDim.x + threadIdx.x) / 4;
   const int lane = threadIdx.x & 3;
-  // a warp whose eight events all lie past the batch skips the blocks (every
-  // synchronisation in them is warp-wide), so a grid sized for a capacity costs little
-  const bool warp_live = ((long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u)) / 4 < nev;
+  const long nev = count ? (long)*count : n;
+  // a warp whose eight events all lie past the batch leaves together (every
+  // synchronisation below is warp-wide), so a grid sized for a capacity costs little
+  if (((long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u)) / 4 >= nev) return;
   const bool active = gid < nev;
   const long ev = active ? (idx ? (long)idx[gid] : gid) : 0;
   r4<double> k[6];
@@ -339,6 +329,7 @@ __global__ void __launch_bounds__(TC4_THREADS, 2) k_tree_tc4(const double* __res
 #pragma unroll
     for (int l = 0; l < 6; ++l) k[l] = r4<double>{d[l][0], d[l][1], d[l][2], d[l][3]};
   }
+  const TcColourB cb = tc_load_colour(kp.tab->C[PID]);
   const Kin<PID, float> K = prepare<PID, float>(k, kp.cp);
   const float g = (float)kp.cp.gs, mt = (float)kp.cp.mt;
   const r4<float>* q = K.q;
@@ -346,8 +337,7 @@ __global__ void __launch_bounds__(TC4_THREADS, 2) k_tree_tc4(const double* __res
   const c4<float> v[2] = {spinor_v_of(K.wtb, -1), spinor_v_of(K.wtb, 1)};
   constexpr int LEG[4] = {0, 1, 4, 5};
   float acc = 0.0f;
-  const int nblk = warp_live ? n_live_blocks<PID>() : 0;
-  for (int b = 0; b < nblk; ++b) {
+  for (int b = 0; b < n_live_blocks<PID>(); ++b) {
     const int hb = live_block_hel<PID>(b);
     // 1. polarisation of gluon `lane`
     st_c4(cur, lane, polvec_of(K.wg[lane], hel_of(hb, LEG[lane]), LEG[lane] >= 2));
@@ -390,12 +380,6 @@ __global__ void __launch_bounds__(TC4_THREADS, 2) k_tree_tc4(const double* __res
     // the quark lines only slash the 34 vectors against rows: convert them in place
     for (int sl = lane; sl < 34; sl += 4) slash_in_place(cur, sl);
     __syncwarp();
-    // the previous block's colour sum: its rows are still intact (step 5 rewrites them)
-    if (b > 0) {
-      const float sres = tc5_collect(are + wl * TC4_ROW, aim + wl * TC4_ROW, tcs);
-      if (active) acc += sres;
-      if (!tcs.ok) break;  // warp-uniform: the weight is NaN
-    }
     // 5. quark line for the orderings starting with gluon w = lane
     const int w = lane;
     for (int ht = 0; ht < 2; ++ht) {
@@ -445,11 +429,9 @@ __global__ void __launch_bounds__(TC4_THREADS, 2) k_tree_tc4(const double* __res
     cx<float> J[TC_NF];
 #pragma unroll
     for (int fl = 0; fl < TC_NF; ++fl) J[fl] = cx<float>{are[wl * TC4_ROW + fl], aim[wl * TC4_ROW + fl]};
-    tc5_issue(J, tcs);  // collected during the next block, while its currents are built
-  }
-  if (nblk > 0 && tcs.ok) {
-    const float sres = tc5_collect(are + wl * TC4_ROW, aim + wl * TC4_ROW, tcs);
+    const float sres = tc_colour_sum(J, cb, stage);
     if (active) acc += sres;
+    __syncwarp();
   }
   const double tot = 2.0 * (double)group_sum<4>(acc, group_mask<4>());
   if (active && lane == 0) {
@@ -462,7 +444,6 @@ __global__ void __launch_bounds__(TC4_THREADS, 2) k_tree_tc4(const double* __res
     }
     out[ev] = pass ? w8 * tot * kp.avg_inv * kp.nlo_factor : 0.0;
   }
-  tc5_teardown(tcs);
 }
 
 // ---------------------------------------------------------------- FKS kinematics (double)
